@@ -1,0 +1,317 @@
+"""Benchmark: ensemble member-steps/s of the decoupled Elsaesser scheme
+(Algorithm 1) on the lid-driven-cavity-shaped workload (unit square 128x128
+right-diagonal, Taylor-Hood P2-P1, J = 20, nu = nu_m = (1/15000)(1 + delta_j),
+s = 1, dt = 0.01, synthetic seeded data).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision mixed|fp64]
+
+One step = one pass of the whole hot path for all J members: ensemble means
+and mixing-length fields, two shared-matrix assemblies, two batched
+right-hand-side assemblies, and the two block solves on two streams.  Under
+torchrun each rank runs an independent ensemble replica (seed 2 + rank): the
+value is the whole-job member-steps/s.  Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ensemble member-steps/s at rel L2 <=1e-8 vs FP64 oracle"
+UNIT = "member-steps/s"
+WORKLOAD = dict(N=128, J=20, s=1.0, dt=0.01, Re=15000.0)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--N", type=int, default=WORKLOAD["N"])
+    p.add_argument("--J", type=int, default=WORKLOAD["J"])
+    return p.parse_args()
+
+
+def config(args, extra=None):
+    c = {"workload": f"lid-driven-cavity-shaped ensemble, unit square {args.N}x{args.N} "
+                     f"right-diagonal, Taylor-Hood P2-P1, J={args.J}, Re=15000, s=1, dt=0.01",
+         "mesh": f"{args.N}x{args.N}", "J": args.J, "s": WORKLOAD["s"], "dt": WORKLOAD["dt"],
+         "element": "P2-P1", "l2": "per-step working set (Krylov basis 31 blocks + states) > 129 MB L2",
+         "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# --------------------------------------------------------------------------- CPU oracle sample
+def cpu_sample(N, J_total):
+    """One v-subproblem of one member of the workload's first step on the full
+    mesh through the FP64 oracle (assembly + SuperLU factorisation + solve),
+    run in a fresh single-threaded process.  Returns seconds."""
+    import numpy as np
+    from workloads.ensembles import lid_cavity
+    from oracle.scheme import OracleRun, ensemble_mean, mixing_length_sq
+    from scipy.sparse.linalg import splu
+    ens = lid_cavity(N=N, J=J_total, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"])
+    run = OracleRun(ens, lu_per_member=True)
+    t0 = time.perf_counter()
+    mv, mw = ensemble_mean(run.V), ensemble_mean(run.W)
+    Wp = run.W - mw
+    l2w = mixing_length_sq(run.S, Wp)
+    A = run.saddle(run.shared_matrix(mw, l2w))
+    f1, f2, gv, gw = run.member_data(ens.dt)
+    b = run.rhs(run.V, run.W, Wp, f1, gv, 0, run.nu_p + run.nu_m_p, run.nu - run.nu_m)
+    x = splu(A).solve(b)
+    assert np.isfinite(x).all()
+    return time.perf_counter() - t0
+
+
+def run_cpu_sample_subprocess(args):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--N", str(args.N),
+                          "--J", str(args.J)], capture_output=True, text=True, env=env, timeout=900)
+    line = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    if out.returncode != 0 or not line:
+        raise RuntimeError("cpu sample failed: " + out.stderr[-2000:])
+    return json.loads(line[-1])["seconds"]
+
+
+def cpu_baseline_block(seconds):
+    return {"value": 0.5 / seconds, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one member's v-subproblem of one step on the full mesh (half a member-step): "
+                      "FP64 numpy/scipy assembly + SuperLU factorisation and solve, 1 thread; "
+                      f"{seconds:.2f} s"}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- reference arm
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    samples = max(1, min(args.steps, 3))
+    warm = 1 if args.warmup > 0 else 0
+    secs = []
+    for i in range(warm + samples):
+        secs.append(run_cpu_sample_subprocess(args))
+    timed = secs[warm:]
+    total = sum(timed)
+    value = 0.5 * samples / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": samples, "warmup": warm, "ms_per_step": 1000.0 * total / samples,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, {"sample": "half a member-step per step"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{samples} timed samples (after {warm} warm-up), each one "
+                                       "member's v-subproblem of one step on the full mesh with the "
+                                       "FP64 oracle (SuperLU), 1 thread; the driver's K is capped "
+                                       "at 3 to bound the run"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def spmm_bytes(sz, prec_bytes):
+    """Algorithmic bytes of one saddle SpMM: matrix structure and values read
+    once (F: value + column per nnz and row pointers; B and B^T: value pair +
+    column per nnz and row pointers; Dirichlet flags), X read once, Y written
+    once."""
+    n2, np_, nf, nb, Jp = sz.n2, sz.np, sz.nnz_F, sz.nnz_B, sz.J_pad
+    matrix = nf * (prec_bytes + 4) + 4 * (n2 + 1) + 2 * nb * (2 * prec_bytes + 4) + 4 * (n2 + 1) \
+        + 4 * (np_ + 1) + n2
+    vectors = 2 * sz.n_rows * Jp * prec_bytes
+    return matrix + vectors
+
+
+def our_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2108_05110_gb300 import ensemble_io, PREC_FP64, PREC_MIXED
+    from workloads.ensembles import lid_cavity
+
+    cpu_secs = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_secs = run_cpu_sample_subprocess(args)      # before any GPU work in this process
+
+    torch.cuda.set_device(local_rank)
+    prec = PREC_MIXED if args.precision == "mixed" else PREC_FP64
+    ens = lid_cavity(N=args.N, J=args.J, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"],
+                     seed=2 + rank)
+    sol = ensemble_io.solver_for(ens, precision=prec, device=f"cuda:{local_rank}")
+    ensemble_io.feed_initial(sol, ens)
+    ensemble_io.feed_step_data(sol, ens, ens.dt)     # constant lid / field data
+    sol.advance(args.warmup)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    st0 = sol.stats()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(sol.stream_v)
+    t0 = time.perf_counter()
+    sol.advance(args.steps)
+    ev1.record(sol.stream_v)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier()
+    clock_info = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    st1 = sol.stats()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local_rank}")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = ens.J * args.steps * world / (ms_max / 1000.0)
+    launches = int(st1.launches - st0.launches)
+    iters = int(st1.total_iters - st0.total_iters)
+
+    # dominant kernel: the saddle SpMM of the Krylov precision, timed alone
+    kid = 1 if prec == PREC_MIXED else 0
+    spmm_ms = sol.time_kernel(0, kid, reps=50)
+    pbytes = 4 if prec == PREC_MIXED else 8
+    alg = spmm_bytes(sol.sizes, pbytes)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg / (spmm_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"saddle SpMM ({'FP32' if pbytes == 4 else 'FP64'})",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "bytes_per_launch": alg, "ms_per_launch": spmm_ms,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    kernel_ms = {name: sol.time_kernel(0, k, reps=10) for name, k in
+                 (("means_l2", 4), ("assemble_F", 2), ("rhs", 3), ("precond", 5), ("gram", 6))}
+
+    # end to end through the public API with host buffers
+    xy = sol._nodes
+    u0, B0 = ens.u0(xy), ens.B0(xy)
+    ub, Bb = ens.u_bc(xy, ens.dt), ens.B_bc(xy, ens.dt)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    sol.set_initial(u0, B0)
+    sol.set_dirichlet(ub, Bb)
+    for _ in range(args.steps):
+        sol.step()
+        um, Bm = sol.read_mean()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local_rank}")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = ens.J * args.steps * world / float(e2e_t.item())
+    h2d = (u0.nbytes + B0.nbytes + ub.nbytes + Bb.nbytes) / args.steps
+    d2h = um.nbytes + Bm.nbytes
+    sol.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if prec == PREC_MIXED else "f64", "data": "synthetic",
+                "config": config(args, {"precision": args.precision}),
+                "roofline": roofline, "clocks": clock_info, "gpu_launches": launches,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "krylov_iters_per_step": iters / args.steps, "kernel_ms": kernel_ms,
+                "wall_ms_per_step": 1000.0 * wall / args.steps}
+        if cpu_secs is not None:
+            line["cpu_baseline"] = cpu_baseline_block(cpu_secs)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps({"seconds": cpu_sample(args.N, args.J)}), flush=True)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    our_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * mhde.h — C ABI of libmhde: one time step of the decoupled ensemble scheme
+ * for J parameterized MHD flows in Elsaesser variables (Algorithm 1, eq.
+ * weaknew1 and weaknew2), run on one GPU.
+ *
+ * Problem statement (Section 1, eq. gov1-gov5): J members share a mesh and
+ * differ in viscosity nu_j, magnetic diffusivity nu_m,j, body force f_j,
+ * curl g_j, initial data u_j^0, B_j^0 and Dirichlet data.  The library works
+ * in the Elsaesser variables v = u + sqrt(s) B, w = u - sqrt(s) B with
+ * f1 = f + sqrt(s) curl g and f2 = f - sqrt(s) curl g (Section 1) and converts
+ * at the boundary of every call.
+ *
+ * Discretisation: Taylor-Hood P2 velocity / P1 pressure on the given
+ * triangulation (Section 2, eq. infsup: any inf-sup stable pair), a
+ * 7-point degree-5 quadrature, Dirichlet data by identity rows, pressure node
+ * 0 pinned and pressures reported with mean zero (Q = L^2_0, Section 2).
+ *
+ * Numbering: P2 node k < nv is mesh vertex k; node nv + e is the midpoint of
+ * edge e, the edges being the distinct unordered vertex pairs sorted
+ * lexicographically by (smaller vertex, larger vertex).  P1 node i = vertex i.
+ * Nodal arrays are row-major: [J][n2][2] for member vector fields,
+ * [n2][2] for one field, [J][np] for member pressures.
+ *
+ * Ownership: every host array is owned by the caller; the library copies
+ * in or out during the call and keeps no pointer.  Device memory is one
+ * workspace the caller allocates (e.g. a torch uint8 tensor) of the size
+ * mhde_workspace_size() reports and hands over with mhde_bind(); after bind
+ * the library allocates no device memory.  The two CUDA streams passed to
+ * mhde_bind carry the v and w subproblems; the library synchronizes them
+ * before every call returns.
+ *
+ * Errors: every int-returning call returns MHDE_OK (0) or a negative code;
+ * mhde_last_error() describes the last failure on a context.
+ */
+#ifndef MHDE_H
+#define MHDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MHDE_OK 0
+#define MHDE_EINVAL -1      /* bad argument: J < 1, dt <= 0, s < 0, bad mesh, NULL ... */
+#define MHDE_ESTAB -2       /* alpha_j <= 0 or mu <= 1/2 with options.strict = 1 (Section 3.1) */
+#define MHDE_ENOCONV -3     /* solver hit its iteration cap; state left unchanged */
+#define MHDE_ENAN -4        /* non-finite residual; state left unchanged */
+#define MHDE_ECUDA -5       /* a CUDA call failed */
+#define MHDE_EWORKSPACE -6  /* workspace missing, too small or misaligned */
+#define MHDE_ESTATE -7      /* call out of order (e.g. step before bind / initial data) */
+
+/* Precision of the Krylov iterations (Section 1 block solve; the FP64
+ * refinement reading is the library's). */
+#define MHDE_PREC_FP64 0    /* block GMRES, SpMM and preconditioner in FP64 */
+#define MHDE_PREC_MIXED 1   /* FP32 block GMRES/SpMM/preconditioner, FP64 refinement */
+
+typedef struct mhde_ctx mhde_ctx;   /* opaque, owned by the library */
+
+/* Triangulation: nv vertices, nt counter-clockwise triangles, 0-based. */
+typedef struct {
+  int nv, nt;
+  const double* xy;   /* [nv][2] */
+  const int* tri;     /* [nt][3] */
+} mhde_mesh;
+
+typedef struct {
+  double mu;            /* mixing-length tuning parameter (Section 1, nu_T = mu dt l^2); default 1 */
+  int conv_form;        /* 0: skew-symmetric b (default), 1: standard b(u,v,w) = (u.grad v, w) */
+  int precision;        /* MHDE_PREC_FP64 or MHDE_PREC_MIXED (default) */
+  double rtol;          /* target FP64 relative residual ||b_j - A x_j|| / ||b_j|| per member; default 1e-12 */
+  double inner_rtol;    /* mixed: FP32 inner relative tolerance per refinement sweep; default 1e-5 */
+  int restart;          /* block GMRES restart length m (blocks); default 30 */
+  int max_iter;         /* cap on block GMRES iterations per subproblem solve; default 2000 */
+  int max_refine;       /* mixed: cap on refinement sweeps; default 12 */
+  int jacobi_sweeps;    /* damped Jacobi sweeps approximating F^{-1}; default 3 */
+  double jacobi_omega;  /* damping of those sweeps; default 0.3 */
+  int amg_sweeps;       /* Jacobi sweeps per level in the pressure-Laplacian V-cycle; default 2 */
+  int strict;           /* 1: reject alpha_j <= 0 or mu <= 1/2 with MHDE_ESTAB; default 0 */
+} mhde_options;
+
+typedef struct {
+  int nv, nt, ne, n2, np;   /* vertices, triangles, edges, P2 nodes, P1 pressure nodes */
+  int n_rows;               /* rows of one saddle system: 2 n2 + np */
+  int J, J_pad;             /* members, padded row width of the device multi-vectors */
+  long long nnz_F;          /* nonzeros of the scalar P2 block F */
+  long long nnz_B;          /* nonzeros of the divergence block (per component) */
+  long long nnz_saddle;     /* nonzeros of the full saddle matrix (2 nnz_F + 4 nnz_B + 1) */
+  int n_boundary;           /* Dirichlet P2 nodes */
+  int amg_levels;           /* levels of the pressure-Laplacian hierarchy */
+} mhde_sizes;
+
+typedef struct {
+  long long steps;            /* steps taken */
+  int last_iters[2];          /* block GMRES iterations of the last step (v, w) */
+  int last_refine[2];         /* refinement sweeps of the last step (v, w); 1 on the FP64 path */
+  double last_relres[2];      /* max_j FP64 relative residual after the last step (v, w) */
+  long long total_iters;      /* sum of block GMRES iterations over all steps and both subproblems */
+  double last_step_ms;        /* wall time of the last mhde_step (host clock) */
+  long long launches;         /* kernel launches issued by all steps so far */
+} mhde_stats;
+
+/* Default options (listed above). */
+void mhde_default_options(mhde_options* opt);
+
+/* Build the discrete problem for a mesh and J members (host only, no GPU
+ * work).  nu, nu_m: [J].  Checks J >= 1, dt > 0, s >= 0, a valid CCW mesh.
+ * alpha_j = nubar + nubar_m - |nu_j - nu_m,j| - |nu'_j + nu'_m,j| > 0 and
+ * mu > 1/2 are the stability conditions of Section 3.1; they are errors
+ * (MHDE_ESTAB) only with opt->strict = 1.  opt may be NULL (defaults). */
+int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu_m, double s,
+                double dt, const mhde_options* opt, mhde_ctx** out);
+
+int mhde_get_sizes(const mhde_ctx* ctx, mhde_sizes* sizes);
+
+/* Bytes of device workspace mhde_bind needs (256-byte aligned base). */
+int mhde_workspace_size(const mhde_ctx* ctx, size_t* bytes);
+
+/* Hand over the caller-allocated device workspace and the two streams
+ * (cudaStream_t as void*, may be NULL for the legacy default stream).
+ * Uploads the mesh tables and assembles the constant matrices M, K, B and the
+ * pressure-Laplacian hierarchy.  The workspace must stay allocated until
+ * mhde_destroy. */
+int mhde_bind(mhde_ctx* ctx, void* dev_workspace, size_t bytes, void* stream_v, void* stream_w);
+
+/* P2 node coordinates [n2][2] and Dirichlet flags [n2] (1 = boundary node);
+ * either pointer may be NULL. */
+int mhde_p2_nodes(const mhde_ctx* ctx, double* xy, unsigned char* is_boundary);
+
+/* Initial data u_j^0, B_j^0 as P2 nodal values [J][n2][2] (host).  Resets the
+ * step counter and the pressures to 0. */
+int mhde_set_initial(mhde_ctx* ctx, const double* u0, const double* B0);
+
+/* Body force f_j and curl g_j at t^{n+1} as P2 nodal values [J][n2][2]
+ * (host); the discrete forcing is M times the nodal interpolant.  NULL means
+ * zero.  Values persist for later steps until set again. */
+int mhde_set_forcing(mhde_ctx* ctx, const double* f, const double* curl_g);
+
+/* Dirichlet data u_j, B_j at t^{n+1} as P2 nodal values [J][n2][2] (host);
+ * only boundary nodes are read.  NULL means zero.  Values persist. */
+int mhde_set_dirichlet(mhde_ctx* ctx, const double* u_bc, const double* B_bc);
+
+/* One step n -> n+1 of Algorithm 1 for all members: ensemble means and
+ * mixing-length field, the two shared matrices, the batched right-hand
+ * sides, and the two block solves on the two streams.  On MHDE_ENOCONV or
+ * MHDE_ENAN the state is left at step n. */
+int mhde_step(mhde_ctx* ctx);
+
+/* nsteps calls of mhde_step with the forcing and Dirichlet data held fixed. */
+int mhde_advance(mhde_ctx* ctx, int nsteps);
+
+/* Ensemble means <u> = (<v>+<w>)/2 and <B> = (<v>-<w>)/(2 sqrt s) at the
+ * current step as [n2][2] (host).  B_mean may be NULL; with s = 0 a non-NULL
+ * B_mean is MHDE_EINVAL (B is not recoverable). */
+int mhde_read_mean(mhde_ctx* ctx, double* u_mean, double* B_mean);
+
+/* Elsaesser state: v, w [J][n2][2] and pressures q, r [J][np] (mean zero);
+ * any pointer may be NULL. */
+int mhde_read_state(mhde_ctx* ctx, double* v, double* w, double* q, double* r);
+
+/* Primitive fields of member j: u, B [n2][2]; p = (q+r)/2 and
+ * lambda = (q-r)/(2 sqrt s) [np]; any pointer may be NULL (B, lambda must be
+ * NULL when s = 0). */
+int mhde_read_member(mhde_ctx* ctx, int j, double* u, double* B, double* p, double* lambda);
+
+/* E_h^n = 1/2 (||<v_h>^n||^2 + ||<w_h>^n||^2) (Section 4.2). */
+int mhde_energy(mhde_ctx* ctx, double* E);
+
+int mhde_get_stats(const mhde_ctx* ctx, mhde_stats* stats);
+
+/* Copy of the full time-stepping state (step counter and the Elsaesser
+ * fields with pressures) to / from a caller buffer of mhde_state_bytes()
+ * bytes (host).  Loading reproduces an uninterrupted run bit for bit. */
+int mhde_state_bytes(const mhde_ctx* ctx, size_t* bytes);
+int mhde_save_state(mhde_ctx* ctx, void* host_buffer);
+int mhde_load_state(mhde_ctx* ctx, const void* host_buffer);
+
+const char* mhde_last_error(const mhde_ctx* ctx);
+void mhde_destroy(mhde_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Probes: intermediate results of the current step for parity tests.  They
+ * run the named kernels on the current state without advancing it.
+ * which = 0 for the v subproblem, 1 for the w subproblem.
+ * ---------------------------------------------------------------------- */
+
+/* Ensemble means (Section 1) [n2][2] and the mixing-length field
+ * l^2 = max_j |z'_j|^2 at the quadrature points [nt][7] for z = v and w. */
+int mhde_probe_mean_l2(mhde_ctx* ctx, double* mean_v, double* mean_w, double* l2_v, double* l2_w);
+
+/* Shared matrix F of eq. weaknew1 (which = 0) or weaknew2 (which = 1) with
+ * Dirichlet identity rows, in CSR: rowptr [n2+1], col [nnz_F], val [nnz_F]. */
+int mhde_probe_matrix_F(mhde_ctx* ctx, int which, int* rowptr, int* col, double* val);
+
+/* Right-hand sides of eq. weaknew1 / weaknew2 for all members:
+ * velocity part [J][n2][2] (boundary rows hold the Dirichlet values). */
+int mhde_probe_rhs(mhde_ctx* ctx, int which, double* rhs);
+
+/* Y = A X for the saddle matrix of subproblem `which` at the current step,
+ * X and Y host arrays in the oracle's block order [J][2 n2 + np]
+ * (x-components, y-components, pressures).  precision: 0 FP64 kernel,
+ * 1 FP32 kernel (inputs rounded to float). */
+int mhde_probe_spmm(mhde_ctx* ctx, int which, int precision, const double* X, double* Y);
+
+/* Average device time in milliseconds of one launch of a hot-path kernel
+ * group on the current state of subproblem `which`, from CUDA events on that
+ * subproblem's stream around `reps` back-to-back launches (benchmark
+ * support; the time-stepping state is not changed, scratch buffers are).
+ * kernel: 0 saddle SpMM (FP64), 1 saddle SpMM (FP32), 2 shared-matrix
+ * assembly (element kernel + nnz gather), 3 batched right-hand sides
+ * (element kernel + node gather), 4 ensemble means + mixing-length field,
+ * 5 block preconditioner (Krylov precision), 6 block Gram of restart/2
+ * basis blocks against one block (Krylov precision). */
+int mhde_time_kernel(mhde_ctx* ctx, int which, int kernel, int reps, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHDE_H */

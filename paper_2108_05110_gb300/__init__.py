@@ -1,0 +1,9 @@
+"""GB300 ensemble MHD time-stepper (decoupled Elsaesser scheme, Algorithm 1).
+
+The compute path is ``libmhde.so`` (hand-written CUDA for sm_103a behind the C
+ABI of ``include/mhde.h``); :mod:`.binding` marshals arguments only.
+"""
+from .binding import (  # noqa: F401
+    Library, load_library, Options, Sizes, Stats, MhdeError, EnsembleSolver, library_path,
+    declared_functions, PREC_FP64, PREC_MIXED,
+)

@@ -1,0 +1,338 @@
+"""ctypes binding of libmhde (include/mhde.h) with the same function names.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device workspace (one uint8 tensor) and
+the two CUDA streams of the v and w subproblems.  There is no CPU fallback:
+a missing library or a missing GPU raises.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(HERE, "..", "include", "mhde.h")
+PREC_FP64, PREC_MIXED = 0, 1
+
+ERRORS = {0: "MHDE_OK", -1: "MHDE_EINVAL", -2: "MHDE_ESTAB", -3: "MHDE_ENOCONV", -4: "MHDE_ENAN",
+          -5: "MHDE_ECUDA", -6: "MHDE_EWORKSPACE", -7: "MHDE_ESTATE"}
+
+
+class MhdeError(RuntimeError):
+    def __init__(self, code, where, msg=""):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} {msg}".strip())
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("xy", C.POINTER(C.c_double)),
+                ("tri", C.POINTER(C.c_int))]
+
+
+class Options(C.Structure):
+    _fields_ = [("mu", C.c_double), ("conv_form", C.c_int), ("precision", C.c_int),
+                ("rtol", C.c_double), ("inner_rtol", C.c_double), ("restart", C.c_int),
+                ("max_iter", C.c_int), ("max_refine", C.c_int), ("jacobi_sweeps", C.c_int),
+                ("jacobi_omega", C.c_double), ("amg_sweeps", C.c_int), ("strict", C.c_int)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("ne", C.c_int), ("n2", C.c_int), ("np", C.c_int),
+                ("n_rows", C.c_int), ("J", C.c_int), ("J_pad", C.c_int), ("nnz_F", C.c_longlong),
+                ("nnz_B", C.c_longlong), ("nnz_saddle", C.c_longlong), ("n_boundary", C.c_int),
+                ("amg_levels", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("last_iters", C.c_int * 2), ("last_refine", C.c_int * 2),
+                ("last_relres", C.c_double * 2), ("total_iters", C.c_longlong),
+                ("last_step_ms", C.c_double), ("launches", C.c_longlong)]
+
+
+def library_path():
+    return os.path.join(HERE, "libmhde.so")
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_U8 = C.POINTER(C.c_ubyte)
+SIGNATURES = {
+    "mhde_default_options": (None, [C.POINTER(Options)]),
+    "mhde_create": (C.c_int, [C.POINTER(Mesh), C.c_int, _D, _D, C.c_double, C.c_double,
+                              C.POINTER(Options), C.POINTER(_P)]),
+    "mhde_get_sizes": (C.c_int, [_P, C.POINTER(Sizes)]),
+    "mhde_workspace_size": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "mhde_bind": (C.c_int, [_P, _P, C.c_size_t, _P, _P]),
+    "mhde_p2_nodes": (C.c_int, [_P, _D, _U8]),
+    "mhde_set_initial": (C.c_int, [_P, _D, _D]),
+    "mhde_set_forcing": (C.c_int, [_P, _D, _D]),
+    "mhde_set_dirichlet": (C.c_int, [_P, _D, _D]),
+    "mhde_step": (C.c_int, [_P]),
+    "mhde_advance": (C.c_int, [_P, C.c_int]),
+    "mhde_read_mean": (C.c_int, [_P, _D, _D]),
+    "mhde_read_state": (C.c_int, [_P, _D, _D, _D, _D]),
+    "mhde_read_member": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
+    "mhde_energy": (C.c_int, [_P, _D]),
+    "mhde_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
+    "mhde_state_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "mhde_save_state": (C.c_int, [_P, _P]),
+    "mhde_load_state": (C.c_int, [_P, _P]),
+    "mhde_last_error": (C.c_char_p, [_P]),
+    "mhde_destroy": (None, [_P]),
+    "mhde_probe_mean_l2": (C.c_int, [_P, _D, _D, _D, _D]),
+    "mhde_probe_matrix_F": (C.c_int, [_P, C.c_int, _I, _I, _D]),
+    "mhde_probe_rhs": (C.c_int, [_P, C.c_int, _D]),
+    "mhde_probe_spmm": (C.c_int, [_P, C.c_int, C.c_int, _D, _D]),
+    "mhde_time_kernel": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D]),
+}
+
+
+def declared_functions(header=HEADER):
+    """Names of the functions declared in include/mhde.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mhde_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+class Library:
+    def __init__(self, path=None):
+        path = path or library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmhde is not built ({path}); run __graft_entry__.build()")
+        self.path = path
+        self.lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(self.lib, name)
+            fn.restype = res
+            fn.argtypes = args
+
+    def __getattr__(self, name):
+        if name.startswith("mhde_"):
+            return getattr(self.lib, name)
+        raise AttributeError(name)
+
+
+_LIB = None
+
+
+def load_library():
+    global _LIB
+    if _LIB is None:
+        _LIB = Library()
+    return _LIB
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def default_options(**kw):
+    lib = load_library()
+    o = Options()
+    lib.mhde_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class EnsembleSolver:
+    """One ensemble (mesh, J members) on one GPU, through the C ABI.
+
+    ``bind=False`` builds the host-side structure only (no GPU needed), which
+    is what the CPU tests use to check numbering and sizes.
+    """
+
+    def __init__(self, xy, tri, nu, nu_m, s, dt, options=None, bind=True, device=None, **opt_kw):
+        self.lib = load_library()
+        xy = _f64(xy)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self._keep = (xy, tri)
+        mesh = Mesh(xy.shape[0], tri.shape[0], xy.ctypes.data_as(_D), tri.ctypes.data_as(_I))
+        nu = _f64(nu).ravel()
+        nu_m = _f64(nu_m).ravel()
+        self.J = nu.shape[0]
+        self.s = float(s)
+        opts = options if options is not None else default_options(**opt_kw)
+        self.options = opts
+        ctx = _P()
+        rc = self.lib.mhde_create(C.byref(mesh), self.J, _dptr(nu), _dptr(nu_m), float(s), float(dt),
+                                  C.byref(opts), C.byref(ctx))
+        if rc != 0:
+            raise MhdeError(rc, "mhde_create")
+        self.ctx = ctx
+        self.sizes = Sizes()
+        self._check(self.lib.mhde_get_sizes(self.ctx, C.byref(self.sizes)), "mhde_get_sizes")
+        self.bound = False
+        if bind:
+            self.bind(device)
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, rc, where):
+        if rc != 0:
+            msg = self.lib.mhde_last_error(self.ctx) if getattr(self, "ctx", None) else b""
+            raise MhdeError(rc, where, (msg or b"").decode())
+
+    def bind(self, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmhde needs a CUDA device; none is available")
+        dev = torch.device(device or "cuda:0")
+        torch.cuda.set_device(dev)
+        nbytes = C.c_size_t()
+        self._check(self.lib.mhde_workspace_size(self.ctx, C.byref(nbytes)), "mhde_workspace_size")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+        self.stream_v = torch.cuda.Stream(device=dev)
+        self.stream_w = torch.cuda.Stream(device=dev)
+        self._check(self.lib.mhde_bind(self.ctx, C.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                       C.c_void_p(self.stream_v.cuda_stream),
+                                       C.c_void_p(self.stream_w.cuda_stream)), "mhde_bind")
+        self.bound = True
+        self.workspace_bytes = int(nbytes.value)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.mhde_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ mesh
+    @property
+    def n2(self):
+        return self.sizes.n2
+
+    @property
+    def np_(self):
+        return self.sizes.np
+
+    def p2_nodes(self):
+        xy = np.empty((self.n2, 2))
+        isb = np.empty(self.n2, dtype=np.uint8)
+        self._check(self.lib.mhde_p2_nodes(self.ctx, _dptr(xy), isb.ctypes.data_as(_U8)), "mhde_p2_nodes")
+        return xy, isb.astype(bool)
+
+    def workspace_size(self):
+        nbytes = C.c_size_t()
+        self._check(self.lib.mhde_workspace_size(self.ctx, C.byref(nbytes)), "mhde_workspace_size")
+        return int(nbytes.value)
+
+    # ------------------------------------------------------------------ data
+    def set_initial(self, u0, B0=None):
+        shp = (self.J, self.n2, 2)
+        u0, B0 = _f64(u0, shp), _f64(B0, shp)
+        self._check(self.lib.mhde_set_initial(self.ctx, _dptr(u0), _dptr(B0)), "mhde_set_initial")
+
+    def set_forcing(self, f=None, curl_g=None):
+        shp = (self.J, self.n2, 2)
+        f, cg = _f64(f, shp), _f64(curl_g, shp)
+        self._check(self.lib.mhde_set_forcing(self.ctx, _dptr(f), _dptr(cg)), "mhde_set_forcing")
+
+    def set_dirichlet(self, u_bc=None, B_bc=None):
+        shp = (self.J, self.n2, 2)
+        u, B = _f64(u_bc, shp), _f64(B_bc, shp)
+        self._check(self.lib.mhde_set_dirichlet(self.ctx, _dptr(u), _dptr(B)), "mhde_set_dirichlet")
+
+    # ------------------------------------------------------------------ stepping
+    def step(self):
+        self._check(self.lib.mhde_step(self.ctx), "mhde_step")
+
+    def advance(self, nsteps):
+        self._check(self.lib.mhde_advance(self.ctx, int(nsteps)), "mhde_advance")
+
+    # ------------------------------------------------------------------ read-out
+    def read_mean(self, with_B=True):
+        u = np.empty((self.n2, 2))
+        B = np.empty((self.n2, 2)) if with_B else None
+        self._check(self.lib.mhde_read_mean(self.ctx, _dptr(u), _dptr(B)), "mhde_read_mean")
+        return u, B
+
+    def read_state(self):
+        v = np.empty((self.J, self.n2, 2))
+        w = np.empty((self.J, self.n2, 2))
+        q = np.empty((self.J, self.np_))
+        r = np.empty((self.J, self.np_))
+        self._check(self.lib.mhde_read_state(self.ctx, _dptr(v), _dptr(w), _dptr(q), _dptr(r)),
+                    "mhde_read_state")
+        return v, w, q, r
+
+    def read_member(self, j):
+        u = np.empty((self.n2, 2))
+        p = np.empty(self.np_)
+        B = np.empty((self.n2, 2)) if self.s > 0 else None
+        lam = np.empty(self.np_) if self.s > 0 else None
+        self._check(self.lib.mhde_read_member(self.ctx, int(j), _dptr(u), _dptr(B), _dptr(p), _dptr(lam)),
+                    "mhde_read_member")
+        return u, B, p, lam
+
+    def energy(self):
+        e = C.c_double()
+        self._check(self.lib.mhde_energy(self.ctx, C.byref(e)), "mhde_energy")
+        return e.value
+
+    def stats(self):
+        st = Stats()
+        self._check(self.lib.mhde_get_stats(self.ctx, C.byref(st)), "mhde_get_stats")
+        return st
+
+    def save_state(self):
+        nb = C.c_size_t()
+        self._check(self.lib.mhde_state_bytes(self.ctx, C.byref(nb)), "mhde_state_bytes")
+        buf = np.empty(nb.value, dtype=np.uint8)
+        self._check(self.lib.mhde_save_state(self.ctx, C.c_void_p(buf.ctypes.data)), "mhde_save_state")
+        return buf
+
+    def load_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self.lib.mhde_load_state(self.ctx, C.c_void_p(buf.ctypes.data)), "mhde_load_state")
+
+    # ------------------------------------------------------------------ probes
+    def probe_mean_l2(self):
+        nt = self.sizes.nt
+        mv, mw = np.empty((self.n2, 2)), np.empty((self.n2, 2))
+        lv, lw = np.empty((nt, 7)), np.empty((nt, 7))
+        self._check(self.lib.mhde_probe_mean_l2(self.ctx, _dptr(mv), _dptr(mw), _dptr(lv), _dptr(lw)),
+                    "mhde_probe_mean_l2")
+        return mv, mw, lv, lw
+
+    def probe_matrix_F(self, which):
+        rp = np.empty(self.n2 + 1, dtype=np.int32)
+        col = np.empty(self.sizes.nnz_F, dtype=np.int32)
+        val = np.empty(self.sizes.nnz_F)
+        self._check(self.lib.mhde_probe_matrix_F(self.ctx, int(which), rp.ctypes.data_as(_I),
+                                                 col.ctypes.data_as(_I), _dptr(val)), "mhde_probe_matrix_F")
+        return rp, col, val
+
+    def probe_rhs(self, which):
+        out = np.empty((self.J, self.n2, 2))
+        self._check(self.lib.mhde_probe_rhs(self.ctx, int(which), _dptr(out)), "mhde_probe_rhs")
+        return out
+
+    def time_kernel(self, which, kernel, reps=20):
+        ms = C.c_double()
+        self._check(self.lib.mhde_time_kernel(self.ctx, int(which), int(kernel), int(reps), C.byref(ms)),
+                    "mhde_time_kernel")
+        return ms.value
+
+    def probe_spmm(self, which, X, precision=0):
+        X = _f64(X, (self.J, self.sizes.n_rows))
+        Y = np.empty_like(X)
+        self._check(self.lib.mhde_probe_spmm(self.ctx, int(which), int(precision), _dptr(X), _dptr(Y)),
+                    "mhde_probe_spmm")
+        return Y

@@ -1,0 +1,877 @@
+// C ABI of libmhde (declared in include/mhde.h): context life cycle,
+// workspace layout, input conversion to Elsaesser variables (Section 1),
+// the time step of Algorithm 1 on two streams, read-outs and parity probes.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "kernels.h"
+
+using namespace mhde;
+
+namespace {
+
+int fail(mhde_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CU(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(c, MHDE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+size_t ksize(const mhde_ctx* c) { return c->opt.precision == MHDE_PREC_FP64 ? 8 : 4; }
+
+// Assigns every device pointer inside the workspace (base may be nullptr to
+// measure).  Returns the total bytes.
+size_t layout(mhde_ctx* c, char* base) {
+  Carver w{base};
+  const FeHost& fe = c->fe;
+  const size_t nt = fe.nt, n2 = fe.n2, np = fe.np, Jp = c->Jp;
+  const size_t nf = fe.F.nnz(), nb = fe.B.nnz();
+  const size_t vs = (size_t)c->n_rows * Jp;
+  const int m = c->opt.restart;
+  c->d_dofs = w.take<int>(nt * 6);
+  c->d_geom = w.take<double>(nt * 8);
+  c->d_isbnd = w.take<unsigned char>(n2);
+  c->d_bnd = w.take<int>(n2);
+  c->F.nrows = (int)n2;
+  c->F.ncols = (int)n2;
+  c->F.nnz = (long long)nf;
+  c->F.rowptr = w.take<int>(n2 + 1);
+  c->F.col = w.take<int>(nf);
+  c->d_fslot_ptr = w.take<int>(nf + 1);
+  c->d_fslot = w.take<int>(nt * 36);
+  c->d_fdiag = w.take<int>(n2);
+  c->d_M = w.take<double>(nf);
+  c->d_K = w.take<double>(nf);
+  c->B.nrows = (int)np;
+  c->B.ncols = (int)n2;
+  c->B.nnz = (long long)nb;
+  c->B.rowptr = w.take<int>(np + 1);
+  c->B.col = w.take<int>(nb);
+  c->B.val = w.take<double>(2 * nb);
+  c->B.valf = w.take<float>(2 * nb);
+  c->d_bslot_ptr = w.take<int>(nb + 1);
+  c->d_bslot = w.take<int>(nt * 18);
+  c->BT.nrows = (int)n2;
+  c->BT.ncols = (int)np;
+  c->BT.nnz = (long long)nb;
+  c->BT.rowptr = w.take<int>(n2 + 1);
+  c->BT.col = w.take<int>(nb);
+  c->BT.val = w.take<double>(2 * nb);
+  c->BT.valf = w.take<float>(2 * nb);
+  c->d_btsrc = w.take<int>(nb);
+  c->d_node_ptr = w.take<int>(n2 + 1);
+  c->d_node_slot = w.take<int>(nt * 6);
+  c->d_mp = w.take<double>(np);
+  c->d_mpf = w.take<float>(np);
+  // AMG operators
+  const AmgHost& amg = fe.amg;
+  c->amg_ops.assign(amg.levels.size(), DevAmgLevel());
+  for (size_t l = 0; l < amg.levels.size(); ++l) {
+    const AmgLevelHost& H = amg.levels[l];
+    DevAmgLevel& D = c->amg_ops[l];
+    D.omega = H.omega;
+    auto mk = [&](const HostCsr& A, DevCsr& d, bool diag) {
+      d.nrows = A.nrows;
+      d.ncols = A.ncols;
+      d.nnz = A.nnz();
+      d.rowptr = w.take<int>(A.nrows + 1);
+      d.col = w.take<int>(A.nnz());
+      d.val = w.take<double>(A.nnz());
+      d.valf = w.take<float>(A.nnz());
+      if (diag) {
+        d.dinv = w.take<double>(A.nrows);
+        d.dinvf = w.take<float>(A.nrows);
+      }
+    };
+    mk(H.A, D.A, true);
+    if (l + 1 < amg.levels.size()) {
+      mk(H.P, D.P, false);
+      mk(H.R, D.R, false);
+    }
+  }
+  c->d_coarse_inv = w.take<double>((size_t)amg.nc * amg.nc);
+  c->d_coarse_invf = w.take<float>((size_t)amg.nc * amg.nc);
+  c->d_ccross = w.take<double>(Jp);
+  c->d_csame = w.take<double>(Jp);
+  // inputs and ensemble quantities
+  c->d_F1 = w.take<double>(n2 * 2 * Jp);
+  c->d_F2 = w.take<double>(n2 * 2 * Jp);
+  c->d_Gv = w.take<double>(fe.bnd_nodes.size() * 2 * Jp + 1);
+  c->d_Gw = w.take<double>(fe.bnd_nodes.size() * 2 * Jp + 1);
+  c->d_mean_v = w.take<double>(2 * n2);
+  c->d_mean_w = w.take<double>(2 * n2);
+  c->d_l2_v = w.take<double>(nt * NQ);
+  c->d_l2_w = w.take<double>(nt * NQ);
+  const size_t ks = ksize(c);
+  for (int which = 0; which < 2; ++which) {
+    Sub& s = c->sub[which];
+    s.which = which;
+    s.Fval = w.take<double>(nf);
+    s.Fvalf = w.take<float>(nf);
+    s.Fdinv = w.take<double>(n2);
+    s.Fdinvf = w.take<float>(n2);
+    s.Floc = w.take<double>(nt * 36);
+    s.Cloc = w.take<double>(nt * 6 * 2 * Jp);
+    s.Bv = w.take<double>(vs);
+    s.X = w.take<double>(vs);
+    s.S = w.take<double>(vs);
+    s.Res = w.take<double>(vs);
+    s.basis = w.take<char>((size_t)(m + 1) * vs * ks);
+    s.Wk = w.take<char>(vs * ks);
+    s.Zk = w.take<char>(vs * ks);
+    s.Uk = w.take<char>(vs * ks);
+    s.Tk = w.take<char>(vs * ks);
+    s.Pk = w.take<char>(vs * ks);
+    s.Rk = w.take<char>(vs * ks);
+    s.Dk = w.take<char>(vs * ks);
+    s.part = w.take<double>((size_t)c->nchunk * (m + 1) * c->J * c->J);
+    s.gram = w.take<double>((size_t)(m + 1) * c->J * c->J);
+    s.coef = w.take<char>((size_t)(m + 1) * c->J * c->J * 8);
+    s.colsq = w.take<double>((size_t)c->nchunk * Jp);
+    s.dscale = w.take<double>(2 * Jp);
+    s.amg.assign(amg.levels.size(), DevAmgLevel());
+    for (size_t l = 0; l < amg.levels.size(); ++l) {
+      size_t n = (size_t)amg.levels[l].A.nrows * Jp;
+      DevAmgLevel& L = s.amg[l];
+      if (ks == 8) {
+        L.x = w.take<double>(n);
+        L.b = w.take<double>(n);
+        L.r = w.take<double>(n);
+      } else {
+        L.xf = w.take<float>(n);
+        L.bf = w.take<float>(n);
+        L.rf = w.take<float>(n);
+      }
+    }
+  }
+  return w.off + 256;
+}
+
+template <class T>
+cudaError_t up(T* dst, const std::vector<T>& src, cudaStream_t st) {
+  if (src.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+// [J][n2][2] host (two fields a, b combined as a + sgn b) -> [n2][2][Jp] rows
+void to_rows(const mhde_ctx* c, const double* a, const double* b, double sgn, double* out) {
+  const int n2 = c->fe.n2, J = c->J, Jp = c->Jp;
+  std::fill(out, out + (size_t)n2 * 2 * Jp, 0.0);
+  for (int j = 0; j < J; ++j)
+    for (int k = 0; k < n2; ++k)
+      for (int d = 0; d < 2; ++d) {
+        double v = a ? a[((size_t)j * n2 + k) * 2 + d] : 0.0;
+        if (b) v += sgn * b[((size_t)j * n2 + k) * 2 + d];
+        out[((size_t)k * 2 + d) * Jp + j] = v;
+      }
+}
+
+int check_ready(mhde_ctx* c, bool need_initial) {
+  if (!c) return MHDE_EINVAL;
+  if (!c->bound) return fail(c, MHDE_ESTATE, "mhde_bind has not been called");
+  if (need_initial && !c->have_initial) return fail(c, MHDE_ESTATE, "mhde_set_initial has not been called");
+  return MHDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mhde_default_options(mhde_options* o) {
+  if (!o) return;
+  o->mu = 1.0;
+  o->conv_form = 0;
+  o->precision = MHDE_PREC_MIXED;
+  o->rtol = 1e-12;
+  o->inner_rtol = 1e-5;
+  o->restart = 30;
+  o->max_iter = 2000;
+  o->max_refine = 12;
+  o->jacobi_sweeps = 3;
+  o->jacobi_omega = 0.3;
+  o->amg_sweeps = 2;
+  o->strict = 0;
+}
+
+int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu_m, double s, double dt,
+                const mhde_options* opt, mhde_ctx** out) {
+  if (!out) return MHDE_EINVAL;
+  *out = nullptr;
+  if (J < 1 || J > MAX_J || !nu || !nu_m || !(dt > 0.0) || !(s >= 0.0) || !mesh) return MHDE_EINVAL;
+  mhde_ctx* c = new mhde_ctx();
+  if (opt)
+    c->opt = *opt;
+  else
+    mhde_default_options(&c->opt);
+  if (c->opt.restart < 1 || c->opt.restart > 200 || c->opt.max_iter < 1 || !(c->opt.rtol > 0) ||
+      (c->opt.precision != MHDE_PREC_FP64 && c->opt.precision != MHDE_PREC_MIXED) ||
+      (c->opt.conv_form != 0 && c->opt.conv_form != 1)) {
+    delete c;
+    return MHDE_EINVAL;
+  }
+  std::string e = build_fe(mesh, c->fe);
+  if (e.empty()) e = build_amg(c->fe, 256);
+  if (!e.empty()) {
+    // keep the message reachable through a NULL-safe path
+    delete c;
+    return MHDE_EINVAL;
+  }
+  c->J = J;
+  c->Jp = (J + 3) / 4 * 4;
+  c->n_rows = 2 * c->fe.n2 + c->fe.np;
+  c->s = s;
+  c->rs = std::sqrt(s);
+  c->dt = dt;
+  c->nu.assign(nu, nu + J);
+  c->nu_m.assign(nu_m, nu_m + J);
+  for (int j = 0; j < J; ++j) {
+    if (!(nu[j] > 0.0) || !(nu_m[j] > 0.0)) {
+      delete c;
+      return MHDE_EINVAL;
+    }
+    c->nubar += nu[j];
+    c->nubar_m += nu_m[j];
+  }
+  c->nubar /= J;
+  c->nubar_m /= J;
+  c->c_cross.resize(J);
+  c->c_same.resize(J);
+  bool stable = c->opt.mu > 0.5;
+  for (int j = 0; j < J; ++j) {
+    c->c_cross[j] = nu[j] - nu_m[j];
+    c->c_same[j] = (nu[j] - c->nubar) + (nu_m[j] - c->nubar_m);
+    double alpha = c->nubar + c->nubar_m - std::fabs(c->c_cross[j]) - std::fabs(c->c_same[j]);
+    if (!(alpha > 0.0)) stable = false;
+  }
+  if (!stable && c->opt.strict) {
+    delete c;
+    return MHDE_ESTAB;
+  }
+  c->nchunk = std::max(1, std::min(304, (c->n_rows + 255) / 256));
+  c->amg_levels = (int)c->fe.amg.levels.size();
+  *out = c;
+  return MHDE_OK;
+}
+
+int mhde_get_sizes(const mhde_ctx* c, mhde_sizes* z) {
+  if (!c || !z) return MHDE_EINVAL;
+  z->nv = c->fe.nv;
+  z->nt = c->fe.nt;
+  z->ne = c->fe.ne;
+  z->n2 = c->fe.n2;
+  z->np = c->fe.np;
+  z->n_rows = c->n_rows;
+  z->J = c->J;
+  z->J_pad = c->Jp;
+  z->nnz_F = c->fe.F.nnz();
+  z->nnz_B = c->fe.B.nnz();
+  z->nnz_saddle = 2 * z->nnz_F + 4 * z->nnz_B + 1;
+  z->n_boundary = (int)c->fe.bnd_nodes.size();
+  z->amg_levels = c->amg_levels;
+  return MHDE_OK;
+}
+
+int mhde_workspace_size(const mhde_ctx* c0, size_t* bytes) {
+  if (!c0 || !bytes) return MHDE_EINVAL;
+  mhde_ctx* c = const_cast<mhde_ctx*>(c0);
+  // measuring does not change the bound pointers
+  if (c->bound) {
+    *bytes = c->ws_bytes;
+    return MHDE_OK;
+  }
+  *bytes = layout(c, nullptr);
+  return MHDE_OK;
+}
+
+int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_w) {
+  if (!c) return MHDE_EINVAL;
+  if (c->bound) return fail(c, MHDE_ESTATE, "context is already bound");
+  size_t need = layout(c, nullptr);
+  if (!ws || bytes < need) return fail(c, MHDE_EWORKSPACE, "workspace missing or smaller than mhde_workspace_size");
+  if (((uintptr_t)ws) & 255) return fail(c, MHDE_EWORKSPACE, "workspace must be 256-byte aligned");
+  c->ws = (char*)ws;
+  c->ws_bytes = bytes;
+  layout(c, c->ws);
+  CU(cudaGetDevice(&c->device));
+  c->sv = (cudaStream_t)stream_v;
+  c->sw = (cudaStream_t)stream_w;
+  c->sub[0].stream = c->sv;
+  c->sub[1].stream = c->sw;
+  CU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CU(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  CU(upload_quad_tables());
+  const FeHost& fe = c->fe;
+  cudaStream_t st = c->sv;
+  CU(cudaMemsetAsync(c->ws, 0, need, st));
+  CU(up(c->d_dofs, fe.dofs, st));
+  CU(up(c->d_geom, fe.geom, st));
+  CU(up(c->d_isbnd, fe.is_bnd, st));
+  std::vector<int> bidx(fe.n2, -1);
+  for (size_t i = 0; i < fe.bnd_nodes.size(); ++i) bidx[fe.bnd_nodes[i]] = (int)i;
+  c->h_bidx = bidx;
+  CU(up(c->d_bnd, bidx, st));
+  CU(up(c->F.rowptr, fe.F.rowptr, st));
+  CU(up(c->F.col, fe.F.col, st));
+  CU(up(c->d_fslot_ptr, fe.f_gather_ptr, st));
+  CU(up(c->d_fslot, fe.f_gather_slot, st));
+  CU(up(c->d_fdiag, fe.f_diag, st));
+  CU(up(c->B.rowptr, fe.B.rowptr, st));
+  CU(up(c->B.col, fe.B.col, st));
+  CU(up(c->d_bslot_ptr, fe.b_gather_ptr, st));
+  CU(up(c->d_bslot, fe.b_gather_slot, st));
+  CU(up(c->BT.rowptr, fe.BT.rowptr, st));
+  CU(up(c->BT.col, fe.BT.col, st));
+  CU(up(c->d_btsrc, fe.bt_src, st));
+  CU(up(c->d_node_ptr, fe.node_ptr, st));
+  CU(up(c->d_node_slot, fe.node_slot, st));
+  CU(up(c->d_mp, fe.mp_lumped, st));
+  std::vector<float> mpf(fe.mp_lumped.begin(), fe.mp_lumped.end());
+  CU(up(c->d_mpf, mpf, st));
+  std::vector<double> cc(c->Jp, 0.0), cs(c->Jp, 0.0);
+  for (int j = 0; j < c->J; ++j) {
+    cc[j] = c->c_cross[j];
+    cs[j] = c->c_same[j];
+  }
+  CU(up(c->d_ccross, cc, st));
+  CU(up(c->d_csame, cs, st));
+  // AMG operators
+  std::vector<std::vector<float>> keep_f;   // host float copies alive until the sync below
+  for (size_t l = 0; l < fe.amg.levels.size(); ++l) {
+    const AmgLevelHost& H = fe.amg.levels[l];
+    DevAmgLevel& D = c->amg_ops[l];
+    auto put = [&](const HostCsr& A, DevCsr& d, const std::vector<double>* dinv) -> cudaError_t {
+      cudaError_t e;
+      if ((e = up(d.rowptr, A.rowptr, st))) return e;
+      if ((e = up(d.col, A.col, st))) return e;
+      if ((e = up(d.val, A.val, st))) return e;
+      keep_f.emplace_back(A.val.begin(), A.val.end());
+      if ((e = up(d.valf, keep_f.back(), st))) return e;
+      if (dinv) {
+        if ((e = up(d.dinv, *dinv, st))) return e;
+        keep_f.emplace_back(dinv->begin(), dinv->end());
+        if ((e = up(d.dinvf, keep_f.back(), st))) return e;
+      }
+      return cudaSuccess;
+    };
+    CU(put(H.A, D.A, &H.dinv));
+    if (l + 1 < fe.amg.levels.size()) {
+      CU(put(H.P, D.P, nullptr));
+      CU(put(H.R, D.R, nullptr));
+    }
+  }
+  CU(up(c->d_coarse_inv, fe.amg.coarse_inv, st));
+  std::vector<float> cif(fe.amg.coarse_inv.begin(), fe.amg.coarse_inv.end());
+  CU(up(c->d_coarse_invf, cif, st));
+  // constant matrices: element scratch aliases the F slot buffers of the subproblems
+  c->d_Mloc = c->sub[0].Floc;
+  c->d_Kloc = c->sub[1].Floc;
+  c->d_Bloc = c->sub[0].Cloc;
+  launch_const_local(fe.nt, c->d_geom, c->d_Mloc, c->d_Kloc, c->d_Bloc, st);
+  launch_gather_const(c, st);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  c->h_M.resize(fe.F.nnz());
+  CU(cudaMemcpy(c->h_M.data(), c->d_M, sizeof(double) * fe.F.nnz(), cudaMemcpyDeviceToHost));
+  // pinned host staging
+  const size_t small = (size_t)(c->opt.restart + 1) * c->J * c->J;
+  for (int which = 0; which < 2; ++which) {
+    Sub& s = c->sub[which];
+    CU(cudaMallocHost((void**)&s.hbuf, sizeof(double) * small));
+    CU(cudaMallocHost((void**)&s.hcol, sizeof(double) * c->nchunk * c->Jp));
+    CU(cudaMallocHost(&s.hcoef, sizeof(double) * small));
+  }
+  c->bound = true;
+  return MHDE_OK;
+}
+
+int mhde_p2_nodes(const mhde_ctx* c, double* xy, unsigned char* isb) {
+  if (!c) return MHDE_EINVAL;
+  if (xy) std::copy(c->fe.node_xy.begin(), c->fe.node_xy.end(), xy);
+  if (isb) std::copy(c->fe.is_bnd.begin(), c->fe.is_bnd.end(), isb);
+  return MHDE_OK;
+}
+
+int mhde_set_initial(mhde_ctx* c, const double* u0, const double* B0) {
+  int rc = check_ready(c, false);
+  if (rc) return rc;
+  if (!u0) return fail(c, MHDE_EINVAL, "u0 is NULL");
+  if (B0 && c->s == 0.0) {
+    // B does not enter the Elsaesser fields when s = 0
+  }
+  const size_t vs = (size_t)c->n_rows * c->Jp;
+  std::vector<double> buf(vs, 0.0);
+  for (int which = 0; which < 2; ++which) {
+    std::fill(buf.begin(), buf.end(), 0.0);
+    to_rows(c, u0, B0 ? B0 : nullptr, which == 0 ? c->rs : -c->rs, buf.data());
+    CU(cudaMemcpy(c->sub[which].S, buf.data(), vs * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  c->have_initial = true;
+  c->steps = 0;
+  c->stats = mhde_stats();
+  return MHDE_OK;
+}
+
+int mhde_set_forcing(mhde_ctx* c, const double* f, const double* cg) {
+  int rc = check_ready(c, false);
+  if (rc) return rc;
+  if (!f && !cg) {
+    c->have_forcing = false;
+    return MHDE_OK;
+  }
+  const size_t n = (size_t)c->fe.n2 * 2 * c->Jp;
+  std::vector<double> buf(n);
+  to_rows(c, f, cg, c->rs, buf.data());
+  CU(cudaMemcpy(c->d_F1, buf.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  to_rows(c, f, cg, -c->rs, buf.data());
+  CU(cudaMemcpy(c->d_F2, buf.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  c->have_forcing = true;
+  return MHDE_OK;
+}
+
+int mhde_set_dirichlet(mhde_ctx* c, const double* ub, const double* Bb) {
+  int rc = check_ready(c, false);
+  if (rc) return rc;
+  const int nb = (int)c->fe.bnd_nodes.size(), J = c->J, Jp = c->Jp, n2 = c->fe.n2;
+  std::vector<double> gv((size_t)nb * 2 * Jp, 0.0), gw((size_t)nb * 2 * Jp, 0.0);
+  for (int i = 0; i < nb; ++i) {
+    int k = c->fe.bnd_nodes[i];
+    for (int j = 0; j < J; ++j)
+      for (int d = 0; d < 2; ++d) {
+        double u = ub ? ub[((size_t)j * n2 + k) * 2 + d] : 0.0;
+        double b = Bb ? Bb[((size_t)j * n2 + k) * 2 + d] : 0.0;
+        gv[((size_t)i * 2 + d) * Jp + j] = u + c->rs * b;
+        gw[((size_t)i * 2 + d) * Jp + j] = u - c->rs * b;
+      }
+  }
+  if (nb > 0) {
+    CU(cudaMemcpy(c->d_Gv, gv.data(), gv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->d_Gw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return MHDE_OK;
+}
+
+static int run_sub(mhde_ctx* c, int which) {
+  cudaSetDevice(c->device);
+  Sub& s = c->sub[which];
+  s.err.clear();
+  int rc = assemble_sub(c, which);
+  if (rc == MHDE_OK) rc = solve_sub(c, which);
+  if (rc == MHDE_OK) {
+    cudaError_t e = cudaStreamSynchronize(s.stream);
+    if (e != cudaSuccess) {
+      s.err = std::string("stream: ") + cudaGetErrorString(e);
+      rc = MHDE_ECUDA;
+    }
+  }
+  s.status = rc;
+  return rc;
+}
+
+int mhde_step(mhde_ctx* c) {
+  int rc = check_ready(c, true);
+  if (rc) return rc;
+  auto t0 = std::chrono::steady_clock::now();
+  const long long launches0 = launch_count();
+  // ensemble means and mixing-length fields of both variables (Section 1)
+  launch_means(c->fe.n2, c->J, c->Jp, c->sub[0].S, c->sub[1].S, c->d_mean_v, c->d_mean_w, c->sv);
+  launch_l2(c->fe.nt, c->J, c->Jp, c->d_dofs, c->sub[0].S, c->sub[1].S, c->d_mean_v, c->d_mean_w,
+            c->d_l2_v, c->d_l2_w, c->sv);
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(c->ev_fork, c->sv));
+  CU(cudaStreamWaitEvent(c->sw, c->ev_fork, 0));
+  // the two subproblems run concurrently on their own streams
+  std::thread tw([c]() { run_sub(c, 1); });
+  run_sub(c, 0);
+  tw.join();
+  for (int which = 0; which < 2; ++which) {
+    if (c->sub[which].status != MHDE_OK) {
+      c->err = std::string(which == 0 ? "v" : "w") + " subproblem: " + c->sub[which].err;
+      return c->sub[which].status;
+    }
+  }
+  for (int which = 0; which < 2; ++which) std::swap(c->sub[which].S, c->sub[which].X);
+  c->steps++;
+  c->stats.steps = c->steps;
+  for (int which = 0; which < 2; ++which) {
+    c->stats.last_iters[which] = c->sub[which].iters;
+    c->stats.last_refine[which] = c->sub[which].refine;
+    c->stats.last_relres[which] = c->sub[which].relres;
+    c->stats.total_iters += c->sub[which].iters;
+  }
+  c->stats.launches += launch_count() - launches0;
+  c->stats.last_step_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return MHDE_OK;
+}
+
+int mhde_advance(mhde_ctx* c, int nsteps) {
+  if (nsteps < 0) return fail(c, MHDE_EINVAL, "nsteps < 0");
+  for (int i = 0; i < nsteps; ++i) {
+    int rc = mhde_step(c);
+    if (rc) return rc;
+  }
+  return MHDE_OK;
+}
+
+int mhde_read_mean(mhde_ctx* c, double* u, double* B) {
+  int rc = check_ready(c, true);
+  if (rc) return rc;
+  if (B && c->s == 0.0) return fail(c, MHDE_EINVAL, "B is not recoverable when s = 0");
+  const int n2 = c->fe.n2;
+  launch_means(n2, c->J, c->Jp, c->sub[0].S, c->sub[1].S, c->d_mean_v, c->d_mean_w, c->sv);
+  std::vector<double> mv(2 * (size_t)n2), mw(2 * (size_t)n2);
+  CU(cudaMemcpyAsync(mv.data(), c->d_mean_v, mv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->sv));
+  CU(cudaMemcpyAsync(mw.data(), c->d_mean_w, mw.size() * sizeof(double), cudaMemcpyDeviceToHost, c->sv));
+  CU(cudaStreamSynchronize(c->sv));
+  for (size_t i = 0; i < mv.size(); ++i) {
+    if (u) u[i] = 0.5 * (mv[i] + mw[i]);
+    if (B) B[i] = 0.5 * (mv[i] - mw[i]) / c->rs;
+  }
+  return MHDE_OK;
+}
+
+// Reads the states into [J][n2][2] velocity arrays and mean-zero pressures [J][np].
+static int read_state_host(mhde_ctx* c, std::vector<double>& v, std::vector<double>& w,
+                           std::vector<double>& q, std::vector<double>& r) {
+  const int n2 = c->fe.n2, np = c->fe.np, J = c->J, Jp = c->Jp;
+  const size_t vs = (size_t)c->n_rows * Jp;
+  std::vector<double> buf(vs);
+  std::vector<double>* outs[2][2] = {{&v, &q}, {&w, &r}};
+  double area = 0.0;
+  for (double m : c->fe.mp_lumped) area += m;
+  for (int which = 0; which < 2; ++which) {
+    CU(cudaMemcpy(buf.data(), c->sub[which].S, vs * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double>& z = *outs[which][0];
+    std::vector<double>& p = *outs[which][1];
+    z.assign((size_t)J * n2 * 2, 0.0);
+    p.assign((size_t)J * np, 0.0);
+    for (int j = 0; j < J; ++j) {
+      for (int k = 0; k < n2; ++k)
+        for (int d = 0; d < 2; ++d) z[((size_t)j * n2 + k) * 2 + d] = buf[((size_t)k * 2 + d) * Jp + j];
+      double mean = 0.0;
+      for (int i = 0; i < np; ++i) {
+        double val = buf[((size_t)2 * n2 + i) * Jp + j];
+        p[(size_t)j * np + i] = val;
+        mean += c->fe.mp_lumped[i] * val;
+      }
+      mean /= area;
+      for (int i = 0; i < np; ++i) p[(size_t)j * np + i] -= mean;
+    }
+  }
+  return MHDE_OK;
+}
+
+int mhde_read_state(mhde_ctx* c, double* v, double* w, double* q, double* r) {
+  int rc = check_ready(c, true);
+  if (rc) return rc;
+  std::vector<double> hv, hw, hq, hr;
+  if ((rc = read_state_host(c, hv, hw, hq, hr))) return rc;
+  if (v) std::copy(hv.begin(), hv.end(), v);
+  if (w) std::copy(hw.begin(), hw.end(), w);
+  if (q) std::copy(hq.begin(), hq.end(), q);
+  if (r) std::copy(hr.begin(), hr.end(), r);
+  return MHDE_OK;
+}
+
+int mhde_read_member(mhde_ctx* c, int j, double* u, double* B, double* p, double* lam) {
+  int rc = check_ready(c, true);
+  if (rc) return rc;
+  if (j < 0 || j >= c->J) return fail(c, MHDE_EINVAL, "member index out of range");
+  if ((B || lam) && c->s == 0.0) return fail(c, MHDE_EINVAL, "B, lambda are not recoverable when s = 0");
+  std::vector<double> hv, hw, hq, hr;
+  if ((rc = read_state_host(c, hv, hw, hq, hr))) return rc;
+  const int n2 = c->fe.n2, np = c->fe.np;
+  for (size_t i = 0; i < (size_t)n2 * 2; ++i) {
+    double a = hv[(size_t)j * n2 * 2 + i], b = hw[(size_t)j * n2 * 2 + i];
+    if (u) u[i] = 0.5 * (a + b);
+    if (B) B[i] = 0.5 * (a - b) / c->rs;
+  }
+  for (int i = 0; i < np; ++i) {
+    double a = hq[(size_t)j * np + i], b = hr[(size_t)j * np + i];
+    if (p) p[i] = 0.5 * (a + b);
+    if (lam) lam[i] = 0.5 * (a - b) / c->rs;
+  }
+  return MHDE_OK;
+}
+
+int mhde_energy(mhde_ctx* c, double* E) {
+  int rc = check_ready(c, true);
+  if (rc) return rc;
+  if (!E) return fail(c, MHDE_EINVAL, "E is NULL");
+  const int n2 = c->fe.n2;
+  launch_means(n2, c->J, c->Jp, c->sub[0].S, c->sub[1].S, c->d_mean_v, c->d_mean_w, c->sv);
+  std::vector<double> mv(2 * (size_t)n2), mw(2 * (size_t)n2);
+  CU(cudaMemcpyAsync(mv.data(), c->d_mean_v, mv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->sv));
+  CU(cudaMemcpyAsync(mw.data(), c->d_mean_w, mw.size() * sizeof(double), cudaMemcpyDeviceToHost, c->sv));
+  CU(cudaStreamSynchronize(c->sv));
+  const HostCsr& F = c->fe.F;
+  double e = 0.0;
+  for (int r = 0; r < n2; ++r)
+    for (int k = F.rowptr[r]; k < F.rowptr[r + 1]; ++k) {
+      int col = F.col[k];
+      double m = c->h_M[k];
+      for (int d = 0; d < 2; ++d) e += m * (mv[2 * r + d] * mv[2 * col + d] + mw[2 * r + d] * mw[2 * col + d]);
+    }
+  *E = 0.5 * e;
+  return MHDE_OK;
+}
+
+int mhde_get_stats(const mhde_ctx* c, mhde_stats* st) {
+  if (!c || !st) return MHDE_EINVAL;
+  *st = c->stats;
+  return MHDE_OK;
+}
+
+int mhde_state_bytes(const mhde_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return MHDE_EINVAL;
+  *bytes = sizeof(long long) + 2 * (size_t)c->n_rows * c->Jp * sizeof(double);
+  return MHDE_OK;
+}
+
+int mhde_save_state(mhde_ctx* c, void* buf) {
+  int rc = check_ready(c, true);
+  if (rc) return rc;
+  if (!buf) return fail(c, MHDE_EINVAL, "buffer is NULL");
+  char* p = (char*)buf;
+  std::memcpy(p, &c->steps, sizeof(long long));
+  const size_t vs = (size_t)c->n_rows * c->Jp * sizeof(double);
+  for (int which = 0; which < 2; ++which)
+    CU(cudaMemcpy(p + sizeof(long long) + which * vs, c->sub[which].S, vs, cudaMemcpyDeviceToHost));
+  return MHDE_OK;
+}
+
+int mhde_load_state(mhde_ctx* c, const void* buf) {
+  int rc = check_ready(c, false);
+  if (rc) return rc;
+  if (!buf) return fail(c, MHDE_EINVAL, "buffer is NULL");
+  const char* p = (const char*)buf;
+  std::memcpy(&c->steps, p, sizeof(long long));
+  const size_t vs = (size_t)c->n_rows * c->Jp * sizeof(double);
+  for (int which = 0; which < 2; ++which)
+    CU(cudaMemcpy(c->sub[which].S, p + sizeof(long long) + which * vs, vs, cudaMemcpyHostToDevice));
+  c->have_initial = true;
+  c->stats.steps = c->steps;
+  return MHDE_OK;
+}
+
+const char* mhde_last_error(const mhde_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+void mhde_destroy(mhde_ctx* c) {
+  if (!c) return;
+  if (c->bound) {
+    cudaStreamSynchronize(c->sv);
+    cudaStreamSynchronize(c->sw);
+    for (int which = 0; which < 2; ++which) {
+      if (c->sub[which].hbuf) cudaFreeHost(c->sub[which].hbuf);
+      if (c->sub[which].hcol) cudaFreeHost(c->sub[which].hcol);
+      if (c->sub[which].hcoef) cudaFreeHost(c->sub[which].hcoef);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+  }
+  delete c;
+}
+
+// ------------------------------------------------------------------ probes
+static int prepare_means(mhde_ctx* c) {
+  launch_means(c->fe.n2, c->J, c->Jp, c->sub[0].S, c->sub[1].S, c->d_mean_v, c->d_mean_w, c->sv);
+  launch_l2(c->fe.nt, c->J, c->Jp, c->d_dofs, c->sub[0].S, c->sub[1].S, c->d_mean_v, c->d_mean_w,
+            c->d_l2_v, c->d_l2_w, c->sv);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(c->sv));
+  return MHDE_OK;
+}
+
+int mhde_probe_mean_l2(mhde_ctx* c, double* mv, double* mw, double* l2v, double* l2w) {
+  int rc = check_ready(c, true);
+  if (rc) return rc;
+  if ((rc = prepare_means(c))) return rc;
+  const size_t n2 = c->fe.n2, nt = c->fe.nt;
+  if (mv) CU(cudaMemcpy(mv, c->d_mean_v, 2 * n2 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (mw) CU(cudaMemcpy(mw, c->d_mean_w, 2 * n2 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (l2v) CU(cudaMemcpy(l2v, c->d_l2_v, nt * NQ * sizeof(double), cudaMemcpyDeviceToHost));
+  if (l2w) CU(cudaMemcpy(l2w, c->d_l2_w, nt * NQ * sizeof(double), cudaMemcpyDeviceToHost));
+  return MHDE_OK;
+}
+
+static int probe_assemble(mhde_ctx* c, int which) {
+  int rc = check_ready(c, true);
+  if (rc) return rc;
+  if (which != 0 && which != 1) return fail(c, MHDE_EINVAL, "which must be 0 or 1");
+  if ((rc = prepare_means(c))) return rc;
+  cudaStream_t keep = c->sub[which].stream;
+  c->sub[which].stream = c->sv;
+  rc = assemble_sub(c, which);
+  c->sub[which].stream = keep;
+  if (rc) return fail(c, rc, c->sub[which].err);
+  CU(cudaStreamSynchronize(c->sv));
+  return MHDE_OK;
+}
+
+int mhde_probe_matrix_F(mhde_ctx* c, int which, int* rowptr, int* col, double* val) {
+  int rc = probe_assemble(c, which);
+  if (rc) return rc;
+  const HostCsr& F = c->fe.F;
+  if (rowptr) std::copy(F.rowptr.begin(), F.rowptr.end(), rowptr);
+  if (col) std::copy(F.col.begin(), F.col.end(), col);
+  if (val) CU(cudaMemcpy(val, c->sub[which].Fval, F.nnz() * sizeof(double), cudaMemcpyDeviceToHost));
+  return MHDE_OK;
+}
+
+int mhde_probe_rhs(mhde_ctx* c, int which, double* rhs) {
+  int rc = probe_assemble(c, which);
+  if (rc) return rc;
+  if (!rhs) return fail(c, MHDE_EINVAL, "rhs is NULL");
+  const int n2 = c->fe.n2, J = c->J, Jp = c->Jp;
+  std::vector<double> buf((size_t)2 * n2 * Jp);
+  CU(cudaMemcpy(buf.data(), c->sub[which].Bv, buf.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int j = 0; j < J; ++j)
+    for (int k = 0; k < n2; ++k)
+      for (int d = 0; d < 2; ++d) rhs[((size_t)j * n2 + k) * 2 + d] = buf[((size_t)k * 2 + d) * Jp + j];
+  return MHDE_OK;
+}
+
+int mhde_probe_spmm(mhde_ctx* c, int which, int precision, const double* X, double* Y) {
+  int rc = probe_assemble(c, which);
+  if (rc) return rc;
+  if (!X || !Y) return fail(c, MHDE_EINVAL, "X or Y is NULL");
+  const int n2 = c->fe.n2, np = c->fe.np, J = c->J, Jp = c->Jp, nr = c->n_rows;
+  const size_t vs = (size_t)nr * Jp;
+  std::vector<double> buf(vs, 0.0);
+  for (int j = 0; j < J; ++j) {
+    const double* x = X + (size_t)j * nr;
+    for (int k = 0; k < n2; ++k)
+      for (int d = 0; d < 2; ++d) buf[((size_t)k * 2 + d) * Jp + j] = x[(size_t)d * n2 + k];
+    for (int i = 0; i < np; ++i) buf[((size_t)2 * n2 + i) * Jp + j] = x[(size_t)2 * n2 + i];
+  }
+  Sub& s = c->sub[which];
+  double* dx = s.Res;   // FP64 scratch: the probe runs outside a step
+  double* dy = s.X;
+  CU(cudaMemcpy(dx, buf.data(), vs * sizeof(double), cudaMemcpyHostToDevice));
+  if (precision == 0) {
+    launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, dx, nullptr, dy, 0, c->sv);
+    CU(cudaGetLastError());
+    CU(cudaMemcpy(buf.data(), dy, vs * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    float* fx = (float*)s.Wk;
+    float* fy = (float*)s.Zk;
+    if (ksize(c) != 4) {
+      // FP64 Krylov buffers are twice as large: reuse them as float storage
+    }
+    launch_d2f(dx, fx, vs, c->sv);
+    launch_saddle_spmm<float>(c, s.Fvalf, c->B.valf, c->BT.valf, fx, nullptr, fy, 0, c->sv);
+    CU(cudaGetLastError());
+    std::vector<float> fb(vs);
+    CU(cudaMemcpy(fb.data(), fy, vs * sizeof(float), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < vs; ++i) buf[i] = fb[i];
+  }
+  for (int j = 0; j < J; ++j) {
+    double* y = Y + (size_t)j * nr;
+    for (int k = 0; k < n2; ++k)
+      for (int d = 0; d < 2; ++d) y[(size_t)d * n2 + k] = buf[((size_t)k * 2 + d) * Jp + j];
+    for (int i = 0; i < np; ++i) y[(size_t)2 * n2 + i] = buf[((size_t)2 * n2 + i) * Jp + j];
+  }
+  return MHDE_OK;
+}
+
+int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
+  int rc = probe_assemble(c, which);
+  if (rc) return rc;
+  if (!ms || reps < 1 || kernel < 0 || kernel > 6) return fail(c, MHDE_EINVAL, "bad kernel id, reps or ms");
+  Sub& s = c->sub[which];
+  cudaStream_t st = s.stream;
+  const size_t vs = (size_t)c->n_rows * c->Jp;
+  CU(cudaStreamSynchronize(c->sv));
+  // inputs: the current state as a saddle multi-vector
+  double* xd = s.Res;
+  double* yd = s.X;
+  CU(cudaMemcpyAsync(xd, s.S, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const bool fp64 = c->opt.precision == MHDE_PREC_FP64;
+  if (kernel == 1 || (!fp64 && (kernel == 5 || kernel == 6))) launch_d2f(xd, (float*)s.Wk, vs, st);
+  if (fp64 && (kernel == 5 || kernel == 6))
+    CU(cudaMemcpyAsync(s.Wk, xd, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const int kb = std::max(1, c->opt.restart / 2);
+  if (kernel == 6) {
+    // fill kb basis blocks with copies of the input
+    for (int i = 0; i < kb; ++i)
+      CU(cudaMemcpyAsync((char*)s.basis + (size_t)i * vs * ksize(c), s.Wk, vs * ksize(c),
+                         cudaMemcpyDeviceToDevice, st));
+  }
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  auto once = [&]() {
+    switch (kernel) {
+      case 0:
+        launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, xd, nullptr, yd, 0, st);
+        break;
+      case 1:
+        launch_saddle_spmm<float>(c, s.Fvalf, c->B.valf, c->BT.valf, (const float*)s.Wk, nullptr,
+                                  (float*)s.Zk, 0, st);
+        break;
+      case 2: {
+        const double* mean_conv = which == 0 ? c->d_mean_w : c->d_mean_v;
+        const double* l2 = which == 0 ? c->d_l2_w : c->d_l2_v;
+        launch_F_local(c->fe.nt, c->d_dofs, c->d_geom, mean_conv, l2, 2.0 * c->opt.mu * c->dt,
+                       c->opt.conv_form, s.Floc, st);
+        launch_F_gather(c, s.Floc, 1.0 / c->dt, 0.5 * (c->nubar + c->nubar_m), s.Fval, s.Fvalf, s.Fdinv,
+                        s.Fdinvf, st);
+        break;
+      }
+      case 3: {
+        const Sub& o = c->sub[1 - which];
+        const double* mean_other = which == 0 ? c->d_mean_w : c->d_mean_v;
+        launch_rhs_conv_local(c->fe.nt, c->J, c->Jp, c->d_dofs, c->d_geom, s.S, o.S, mean_other,
+                              c->opt.conv_form, s.Cloc, st);
+        launch_rhs_assemble(c, s.S, o.S, c->have_forcing ? (which == 0 ? c->d_F1 : c->d_F2) : nullptr,
+                            which == 0 ? c->d_Gv : c->d_Gw, s.Cloc, c->d_ccross, c->d_csame, s.Bv, st);
+        break;
+      }
+      case 4:
+        launch_means(c->fe.n2, c->J, c->Jp, c->sub[0].S, c->sub[1].S, c->d_mean_v, c->d_mean_w, st);
+        launch_l2(c->fe.nt, c->J, c->Jp, c->d_dofs, c->sub[0].S, c->sub[1].S, c->d_mean_v, c->d_mean_w,
+                  c->d_l2_v, c->d_l2_w, st);
+        break;
+      case 5:
+        precond_apply_any(c, which, s.Wk, s.Zk);
+        break;
+      case 6:
+        gram_any(c, which, s.basis, vs, kb, s.Wk);
+        break;
+    }
+  };
+  once();
+  CU(cudaEventRecord(e0, st));
+  for (int i = 0; i < reps; ++i) once();
+  CU(cudaEventRecord(e1, st));
+  CU(cudaEventSynchronize(e1));
+  float t = 0.f;
+  CU(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(cudaGetLastError());
+  *ms = (double)t / reps;
+  return MHDE_OK;
+}
+
+}  // extern "C"

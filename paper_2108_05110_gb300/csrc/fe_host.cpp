@@ -1,0 +1,618 @@
+// Host-side construction of the Taylor-Hood P2/P1 discrete structure:
+// P2 numbering, Dirichlet nodes, element geometry, the CSR patterns of the
+// shared scalar block F and the divergence block B (Section 2, conforming
+// inf-sup stable pair), the element -> nonzero scatter maps that let the
+// device assemble without atomics, and the smoothed-aggregation hierarchy of
+// the pressure Laplacian used by the block preconditioner.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "mhde_internal.h"
+
+namespace mhde {
+
+namespace {
+
+// local edges of a triangle in P2 node order 3, 4, 5
+const int LE[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+
+// Sort (key, payload) pairs by key then payload; returns unique keys and, for
+// every input, the index of its key in the unique list.
+void unique_keys(const std::vector<long long>& keys, std::vector<long long>& uniq,
+                 std::vector<int>& where) {
+  std::vector<int> order(keys.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return keys[a] < keys[b] || (keys[a] == keys[b] && a < b);
+  });
+  uniq.clear();
+  where.assign(keys.size(), -1);
+  for (size_t t = 0; t < order.size(); ++t) {
+    long long k = keys[order[t]];
+    if (uniq.empty() || uniq.back() != k) uniq.push_back(k);
+    where[order[t]] = (int)uniq.size() - 1;
+  }
+}
+
+// CSR pattern from sorted unique keys row * ncols + col.
+void csr_from_keys(const std::vector<long long>& uniq, int nrows, int ncols, HostCsr& A) {
+  A.nrows = nrows;
+  A.ncols = ncols;
+  A.rowptr.assign(nrows + 1, 0);
+  A.col.resize(uniq.size());
+  for (size_t k = 0; k < uniq.size(); ++k) {
+    int r = (int)(uniq[k] / ncols);
+    A.col[k] = (int)(uniq[k] % ncols);
+    A.rowptr[r + 1]++;
+  }
+  for (int r = 0; r < nrows; ++r) A.rowptr[r + 1] += A.rowptr[r];
+}
+
+// Inverse of a slot -> nnz map: for every nnz, the slots mapping to it,
+// ascending (a fixed summation order).
+void invert_map(const std::vector<int>& slot_nnz, long long nnz, std::vector<int>& ptr,
+                std::vector<int>& slots) {
+  ptr.assign(nnz + 1, 0);
+  for (int k : slot_nnz) ptr[k + 1]++;
+  for (long long k = 0; k < nnz; ++k) ptr[k + 1] += ptr[k];
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  slots.resize(slot_nnz.size());
+  for (size_t s = 0; s < slot_nnz.size(); ++s) slots[fill[slot_nnz[s]]++] = (int)s;
+}
+
+}  // namespace
+
+std::string build_fe(const mhde_mesh* mesh, FeHost& fe) {
+  if (!mesh || !mesh->xy || !mesh->tri) return "mesh pointers are NULL";
+  if (mesh->nv < 3 || mesh->nt < 1) return "mesh needs at least 3 vertices and 1 triangle";
+  fe.nv = mesh->nv;
+  fe.nt = mesh->nt;
+  const int nv = fe.nv, nt = fe.nt;
+  fe.xy.assign(mesh->xy, mesh->xy + 2 * (size_t)nv);
+  fe.tri.assign(mesh->tri, mesh->tri + 3 * (size_t)nt);
+  for (int t = 0; t < 3 * nt; ++t)
+    if (fe.tri[t] < 0 || fe.tri[t] >= nv) return "triangle vertex index out of range";
+
+  // geometry: gradients of the barycentric coordinates and twice the area
+  fe.geom.assign((size_t)nt * 8, 0.0);
+  for (int e = 0; e < nt; ++e) {
+    const int* v = &fe.tri[3 * e];
+    double x0 = fe.xy[2 * v[0]], y0 = fe.xy[2 * v[0] + 1];
+    double x1 = fe.xy[2 * v[1]], y1 = fe.xy[2 * v[1] + 1];
+    double x2 = fe.xy[2 * v[2]], y2 = fe.xy[2 * v[2] + 1];
+    double det = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
+    if (!(det > 0.0)) return "triangle " + std::to_string(e) + " is not counter-clockwise";
+    double* g = &fe.geom[8 * (size_t)e];
+    g[0] = (y1 - y2) / det; g[1] = (x2 - x1) / det;
+    g[2] = (y2 - y0) / det; g[3] = (x0 - x2) / det;
+    g[4] = (y0 - y1) / det; g[5] = (x1 - x0) / det;
+    g[6] = det;
+  }
+
+  // edges and P2 numbering
+  std::vector<long long> ekeys((size_t)nt * 3);
+  for (int e = 0; e < nt; ++e)
+    for (int l = 0; l < 3; ++l) {
+      long long a = fe.tri[3 * e + LE[l][0]], b = fe.tri[3 * e + LE[l][1]];
+      if (a == b) return "degenerate triangle";
+      if (a > b) std::swap(a, b);
+      ekeys[3 * (size_t)e + l] = a * nv + b;
+    }
+  std::vector<int> eid;
+  unique_keys(ekeys, fe.edges, eid);
+  fe.ne = (int)fe.edges.size();
+  fe.n2 = nv + fe.ne;
+  fe.np = nv;
+  fe.edge_count.assign(fe.ne, 0);
+  for (int id : eid) fe.edge_count[id]++;
+  for (int c : fe.edge_count)
+    if (c > 2) return "non-manifold edge (shared by more than two triangles)";
+  fe.dofs.resize((size_t)nt * 6);
+  for (int e = 0; e < nt; ++e) {
+    for (int l = 0; l < 3; ++l) fe.dofs[6 * (size_t)e + l] = fe.tri[3 * e + l];
+    for (int l = 0; l < 3; ++l) fe.dofs[6 * (size_t)e + 3 + l] = nv + eid[3 * (size_t)e + l];
+  }
+  fe.node_xy.resize(2 * (size_t)fe.n2);
+  std::copy(fe.xy.begin(), fe.xy.end(), fe.node_xy.begin());
+  fe.is_bnd.assign(fe.n2, 0);
+  for (int k = 0; k < fe.ne; ++k) {
+    long long a = fe.edges[k] / nv, b = fe.edges[k] % nv;
+    fe.node_xy[2 * (size_t)(nv + k)] = 0.5 * (fe.xy[2 * a] + fe.xy[2 * b]);
+    fe.node_xy[2 * (size_t)(nv + k) + 1] = 0.5 * (fe.xy[2 * a + 1] + fe.xy[2 * b + 1]);
+    if (fe.edge_count[k] == 1) {
+      fe.is_bnd[a] = fe.is_bnd[b] = fe.is_bnd[nv + k] = 1;
+    }
+  }
+  fe.bnd_nodes.clear();
+  for (int k = 0; k < fe.n2; ++k)
+    if (fe.is_bnd[k]) fe.bnd_nodes.push_back(k);
+
+  // F pattern and scatter map
+  {
+    std::vector<long long> keys((size_t)nt * 36);
+    for (int e = 0; e < nt; ++e)
+      for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b)
+          keys[36 * (size_t)e + 6 * a + b] =
+              (long long)fe.dofs[6 * (size_t)e + a] * fe.n2 + fe.dofs[6 * (size_t)e + b];
+    std::vector<long long> uniq;
+    unique_keys(keys, uniq, fe.f_slot_nnz);
+    csr_from_keys(uniq, fe.n2, fe.n2, fe.F);
+    invert_map(fe.f_slot_nnz, fe.F.nnz(), fe.f_gather_ptr, fe.f_gather_slot);
+    fe.f_diag.assign(fe.n2, -1);
+    for (int r = 0; r < fe.n2; ++r)
+      for (int k = fe.F.rowptr[r]; k < fe.F.rowptr[r + 1]; ++k)
+        if (fe.F.col[k] == r) fe.f_diag[r] = k;
+  }
+  // B pattern (P1 rows x P2 columns) and scatter map
+  {
+    std::vector<long long> keys((size_t)nt * 18);
+    for (int e = 0; e < nt; ++e)
+      for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 6; ++a)
+          keys[18 * (size_t)e + 6 * i + a] =
+              (long long)fe.tri[3 * e + i] * fe.n2 + fe.dofs[6 * (size_t)e + a];
+    std::vector<long long> uniq;
+    std::vector<int> slot_nnz;
+    unique_keys(keys, uniq, slot_nnz);
+    csr_from_keys(uniq, fe.np, fe.n2, fe.B);
+    invert_map(slot_nnz, fe.B.nnz(), fe.b_gather_ptr, fe.b_gather_slot);
+    // transpose pattern
+    std::vector<long long> tkeys(uniq.size());
+    for (size_t k = 0; k < uniq.size(); ++k) {
+      long long i = uniq[k] / fe.n2, a = uniq[k] % fe.n2;
+      tkeys[k] = a * fe.np + i;
+    }
+    std::vector<long long> tuniq;
+    std::vector<int> where;
+    unique_keys(tkeys, tuniq, where);
+    csr_from_keys(tuniq, fe.n2, fe.np, fe.BT);
+    fe.bt_src.assign(uniq.size(), 0);
+    for (size_t k = 0; k < uniq.size(); ++k) fe.bt_src[where[k]] = (int)k;
+  }
+  // node -> element-local slots
+  {
+    std::vector<int> slot_node((size_t)nt * 6);
+    for (size_t s = 0; s < slot_node.size(); ++s) slot_node[s] = fe.dofs[s];
+    invert_map(slot_node, fe.n2, fe.node_ptr, fe.node_slot);
+  }
+  // pressure Laplacian (P1 stiffness, node 0 pinned) and lumped pressure mass
+  {
+    std::vector<long long> keys((size_t)nt * 9);
+    std::vector<double> vals((size_t)nt * 9);
+    fe.mp_lumped.assign(fe.np, 0.0);
+    for (int e = 0; e < nt; ++e) {
+      const double* g = &fe.geom[8 * (size_t)e];
+      double area = 0.5 * g[6];
+      for (int i = 0; i < 3; ++i) {
+        fe.mp_lumped[fe.tri[3 * e + i]] += area / 3.0;
+        for (int k = 0; k < 3; ++k) {
+          keys[9 * (size_t)e + 3 * i + k] = (long long)fe.tri[3 * e + i] * fe.np + fe.tri[3 * e + k];
+          vals[9 * (size_t)e + 3 * i + k] = area * (g[2 * i] * g[2 * k] + g[2 * i + 1] * g[2 * k + 1]);
+        }
+      }
+    }
+    std::vector<long long> uniq;
+    std::vector<int> where;
+    unique_keys(keys, uniq, where);
+    csr_from_keys(uniq, fe.np, fe.np, fe.Kp);
+    fe.Kp.val.assign(uniq.size(), 0.0);
+    // deterministic: slots in ascending order per nnz
+    std::vector<int> ptr, slots;
+    invert_map(where, (long long)uniq.size(), ptr, slots);
+    for (size_t k = 0; k < uniq.size(); ++k)
+      for (int t = ptr[k]; t < ptr[k + 1]; ++t) fe.Kp.val[k] += vals[slots[t]];
+    // pin node 0: identity row and column
+    for (int r = 0; r < fe.np; ++r)
+      for (int k = fe.Kp.rowptr[r]; k < fe.Kp.rowptr[r + 1]; ++k) {
+        int c = fe.Kp.col[k];
+        if (r == 0 || c == 0) fe.Kp.val[k] = (r == c) ? 1.0 : 0.0;
+      }
+  }
+  return "";
+}
+
+// ------------------------------------------------------------------------- AMG
+namespace {
+
+void csr_transpose(const HostCsr& A, HostCsr& T) {
+  T.nrows = A.ncols;
+  T.ncols = A.nrows;
+  T.rowptr.assign(T.nrows + 1, 0);
+  for (int c : A.col) T.rowptr[c + 1]++;
+  for (int r = 0; r < T.nrows; ++r) T.rowptr[r + 1] += T.rowptr[r];
+  std::vector<int> fill(T.rowptr.begin(), T.rowptr.end() - 1);
+  T.col.resize(A.col.size());
+  T.val.resize(A.col.size());
+  for (int r = 0; r < A.nrows; ++r)
+    for (int k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+      int p = fill[A.col[k]]++;
+      T.col[p] = r;
+      T.val[p] = A.val[k];
+    }
+}
+
+// C = A B (Gustavson, columns sorted per row)
+void csr_matmul(const HostCsr& A, const HostCsr& B, HostCsr& C) {
+  C.nrows = A.nrows;
+  C.ncols = B.ncols;
+  C.rowptr.assign(C.nrows + 1, 0);
+  C.col.clear();
+  C.val.clear();
+  std::vector<int> mark(B.ncols, -1);
+  std::vector<double> acc(B.ncols, 0.0);
+  std::vector<int> cols;
+  for (int r = 0; r < A.nrows; ++r) {
+    cols.clear();
+    for (int k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+      int a = A.col[k];
+      double av = A.val[k];
+      for (int t = B.rowptr[a]; t < B.rowptr[a + 1]; ++t) {
+        int c = B.col[t];
+        if (mark[c] != r) {
+          mark[c] = r;
+          acc[c] = 0.0;
+          cols.push_back(c);
+        }
+        acc[c] += av * B.val[t];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int c : cols) {
+      C.col.push_back(c);
+      C.val.push_back(acc[c]);
+    }
+    C.rowptr[r + 1] = (int)C.col.size();
+  }
+}
+
+double spectral_radius_DinvA(const HostCsr& A, const std::vector<double>& dinv) {
+  int n = A.nrows;
+  std::vector<double> x(n), y(n);
+  for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * std::sin(1.7 * i + 0.3);
+  double lam = 1.0;
+  for (int it = 0; it < 30; ++it) {
+    double nx = 0.0;
+    for (int i = 0; i < n; ++i) nx += x[i] * x[i];
+    nx = std::sqrt(nx);
+    for (int i = 0; i < n; ++i) x[i] /= nx;
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) s += A.val[k] * x[A.col[k]];
+      y[i] = dinv[i] * s;
+    }
+    double ny = 0.0;
+    for (int i = 0; i < n; ++i) ny += y[i] * y[i];
+    lam = std::sqrt(ny);
+    x.swap(y);
+  }
+  return lam * 1.05;
+}
+
+std::vector<double> diag_inv(const HostCsr& A) {
+  std::vector<double> d(A.nrows, 0.0);
+  for (int r = 0; r < A.nrows; ++r)
+    for (int k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k)
+      if (A.col[k] == r) d[r] = A.val[k];
+  for (auto& v : d) v = (v != 0.0) ? 1.0 / v : 0.0;
+  return d;
+}
+
+// Greedy aggregation on the strength graph |a_ij| >= theta sqrt(|a_ii a_jj|).
+int aggregate(const HostCsr& A, double theta, std::vector<int>& agg) {
+  int n = A.nrows;
+  std::vector<double> diag(n, 0.0);
+  for (int r = 0; r < n; ++r)
+    for (int k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k)
+      if (A.col[k] == r) diag[r] = std::fabs(A.val[k]);
+  std::vector<std::vector<int>> S(n);
+  for (int r = 0; r < n; ++r)
+    for (int k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+      int c = A.col[k];
+      if (c != r && std::fabs(A.val[k]) >= theta * std::sqrt(diag[r] * diag[c]) && A.val[k] != 0.0)
+        S[r].push_back(c);
+    }
+  agg.assign(n, -1);
+  int na = 0;
+  for (int i = 0; i < n; ++i) {         // pass 1: whole free neighbourhoods
+    if (agg[i] >= 0) continue;
+    bool free_nb = true;
+    for (int c : S[i])
+      if (agg[c] >= 0) { free_nb = false; break; }
+    if (!free_nb) continue;
+    agg[i] = na;
+    for (int c : S[i]) agg[c] = na;
+    na++;
+  }
+  std::vector<int> agg1 = agg;
+  for (int i = 0; i < n; ++i) {         // pass 2: join a neighbouring aggregate
+    if (agg[i] >= 0) continue;
+    for (int c : S[i])
+      if (agg1[c] >= 0) { agg[i] = agg1[c]; break; }
+  }
+  for (int i = 0; i < n; ++i) {         // pass 3: leftovers
+    if (agg[i] >= 0) continue;
+    agg[i] = na;
+    for (int c : S[i])
+      if (agg[c] < 0) agg[c] = na;
+    na++;
+  }
+  return na;
+}
+
+bool dense_inverse(int n, std::vector<double> A, std::vector<double>& inv) {
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)p * n + c])) p = r;
+    if (A[(size_t)p * n + c] == 0.0) return false;
+    if (p != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)p * n + k], A[(size_t)c * n + k]);
+        std::swap(inv[(size_t)p * n + k], inv[(size_t)c * n + k]);
+      }
+    double d = 1.0 / A[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[(size_t)c * n + k] *= d;
+      inv[(size_t)c * n + k] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = A[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+      }
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+std::string build_amg(FeHost& fe, int coarse_max) {
+  AmgHost& amg = fe.amg;
+  amg.levels.clear();
+  AmgLevelHost L0;
+  L0.A = fe.Kp;
+  amg.levels.push_back(L0);
+  for (int lev = 0; lev < 25; ++lev) {
+    AmgLevelHost& L = amg.levels.back();
+    L.dinv = diag_inv(L.A);
+    double rho = spectral_radius_DinvA(L.A, L.dinv);
+    L.omega = 4.0 / (3.0 * rho);
+    int n = L.A.nrows;
+    if (n <= coarse_max) break;
+    std::vector<int> agg;
+    int na = aggregate(L.A, 0.08, agg);
+    if (na >= n || na < 1) break;
+    // tentative prolongator: normalized piecewise constants
+    std::vector<int> size(na, 0);
+    for (int a : agg) size[a]++;
+    HostCsr Pt;
+    Pt.nrows = n;
+    Pt.ncols = na;
+    Pt.rowptr.resize(n + 1);
+    Pt.col.resize(n);
+    Pt.val.resize(n);
+    for (int i = 0; i < n; ++i) {
+      Pt.rowptr[i] = i;
+      Pt.col[i] = agg[i];
+      Pt.val[i] = 1.0 / std::sqrt((double)size[agg[i]]);
+    }
+    Pt.rowptr[n] = n;
+    // smoothed prolongator P = (I - omega D^-1 A) Pt
+    HostCsr AP;
+    csr_matmul(L.A, Pt, AP);
+    HostCsr P;
+    P.nrows = n;
+    P.ncols = na;
+    P.rowptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      std::vector<std::pair<int, double>> row;
+      for (int k = AP.rowptr[i]; k < AP.rowptr[i + 1]; ++k)
+        row.push_back({AP.col[k], -L.omega * L.dinv[i] * AP.val[k]});
+      row.push_back({agg[i], Pt.val[i]});
+      std::sort(row.begin(), row.end());
+      int last = -1;
+      for (auto& pr : row) {
+        if (pr.first == last) {
+          P.val.back() += pr.second;
+        } else {
+          P.col.push_back(pr.first);
+          P.val.push_back(pr.second);
+          last = pr.first;
+        }
+      }
+      P.rowptr[i + 1] = (int)P.col.size();
+    }
+    HostCsr R, RA, Ac;
+    csr_transpose(P, R);
+    csr_matmul(R, L.A, RA);
+    csr_matmul(RA, P, Ac);
+    L.P = P;
+    L.R = R;
+    AmgLevelHost next;
+    next.A = Ac;
+    amg.levels.push_back(next);
+  }
+  AmgLevelHost& C = amg.levels.back();
+  amg.nc = C.A.nrows;
+  if (C.dinv.empty()) {
+    C.dinv = diag_inv(C.A);
+    C.omega = 4.0 / (3.0 * spectral_radius_DinvA(C.A, C.dinv));
+  }
+  if (amg.nc > 4096) return "pressure-Laplacian hierarchy did not coarsen below 4096 unknowns";
+  std::vector<double> dense((size_t)amg.nc * amg.nc, 0.0);
+  for (int r = 0; r < amg.nc; ++r)
+    for (int k = C.A.rowptr[r]; k < C.A.rowptr[r + 1]; ++k)
+      dense[(size_t)r * amg.nc + C.A.col[k]] = C.A.val[k];
+  if (!dense_inverse(amg.nc, dense, amg.coarse_inv)) return "coarsest pressure operator is singular";
+  return "";
+}
+
+// ------------------------------------------------------------- small dense
+void eig_sym(int n, const double* A0, double* w, double* U) {
+  // cyclic Jacobi rotations
+  std::vector<double> A(A0, A0 + (size_t)n * n);
+  for (int i = 0; i < n * n; ++i) U[i] = 0.0;
+  for (int i = 0; i < n; ++i) U[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double a = A[i * n + j] * A[i * n + j];
+        tot += a;
+        if (i != j) off += a;
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        double app = A[p * n + p], aqq = A[q * n + q];
+        double theta = 0.5 * (aqq - app) / apq;
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double ukp = U[k * n + p], ukq = U[k * n + q];
+          U[k * n + p] = c * ukp - s * ukq;
+          U[k * n + q] = s * ukp + c * ukq;
+        }
+      }
+  }
+  // sort descending
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> d(n);
+  for (int i = 0; i < n; ++i) d[i] = A[i * n + i];
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return d[a] > d[b]; });
+  std::vector<double> U2((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = d[order[j]];
+    for (int i = 0; i < n; ++i) U2[i * n + j] = U[i * n + order[j]];
+  }
+  std::copy(U2.begin(), U2.end(), U);
+}
+
+void BlockLS::init(int r_, int J_, int m_, const double* S0) {
+  r = r_;
+  J = J_;
+  m = m_;
+  k = 0;
+  ldr = (m + 1) * r;
+  R.assign((size_t)ldr * m * r, 0.0);
+  hv.assign((size_t)m * r * 2 * r, 0.0);
+  htau.assign((size_t)m * r, 0.0);
+  g.assign((size_t)ldr * J, 0.0);
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < J; ++j) g[(size_t)j * ldr + i] = S0[i * J + j];
+}
+
+bool BlockLS::add(const double* h) {
+  const int rows = (k + 2) * r;
+  std::vector<double> c((size_t)rows * r);
+  for (int t = 0; t < r; ++t)
+    for (int i = 0; i < rows; ++i) c[(size_t)t * rows + i] = h[(size_t)t * rows + i];
+  // previous reflectors
+  for (int col = 0; col < k * r; ++col) {
+    int blk = col / r;
+    int lo = col, hi = (blk + 2) * r;       // rows [lo, hi)
+    const double* v = &hv[(size_t)col * 2 * r];
+    double tau = htau[col];
+    if (tau == 0.0) continue;
+    for (int t = 0; t < r; ++t) {
+      double* x = &c[(size_t)t * rows];
+      double s = 0.0;
+      for (int i = lo; i < hi; ++i) s += v[i - lo] * x[i];
+      s *= tau;
+      for (int i = lo; i < hi; ++i) x[i] -= s * v[i - lo];
+    }
+  }
+  // new reflectors for this block column
+  bool ok = true;
+  for (int t = 0; t < r; ++t) {
+    int col = k * r + t;
+    int lo = col, hi = (k + 2) * r;
+    double* x = &c[(size_t)t * rows];
+    double alpha = x[lo], nrm2 = 0.0;
+    for (int i = lo; i < hi; ++i) nrm2 += x[i] * x[i];
+    double nrm = std::sqrt(nrm2);
+    double* v = &hv[(size_t)col * 2 * r];
+    for (int i = 0; i < 2 * r; ++i) v[i] = 0.0;
+    if (nrm == 0.0) {
+      htau[col] = 0.0;
+      ok = false;
+      continue;
+    }
+    double beta = (alpha >= 0) ? -nrm : nrm;
+    v[0] = 1.0;
+    double denom = alpha - beta;
+    for (int i = lo + 1; i < hi; ++i) v[i - lo] = x[i] / denom;
+    double tau = (beta - alpha) / beta;
+    htau[col] = tau;
+    x[lo] = beta;
+    for (int i = lo + 1; i < hi; ++i) x[i] = 0.0;
+    for (int t2 = t + 1; t2 < r; ++t2) {
+      double* y = &c[(size_t)t2 * rows];
+      double s = 0.0;
+      for (int i = lo; i < hi; ++i) s += v[i - lo] * y[i];
+      s *= tau;
+      for (int i = lo; i < hi; ++i) y[i] -= s * v[i - lo];
+    }
+    for (int j = 0; j < J; ++j) {
+      double* y = &g[(size_t)j * ldr];
+      double s = 0.0;
+      for (int i = lo; i < hi; ++i) s += v[i - lo] * y[i];
+      s *= tau;
+      for (int i = lo; i < hi; ++i) y[i] -= s * v[i - lo];
+    }
+  }
+  for (int t = 0; t < r; ++t)
+    for (int i = 0; i < (k + 1) * r; ++i)
+      R[(size_t)(k * r + t) * ldr + i] = c[(size_t)t * rows + i];
+  double dmax = 0.0;
+  for (int i = 0; i < (k + 1) * r; ++i) dmax = std::max(dmax, std::fabs(R[(size_t)i * ldr + i]));
+  for (int t = 0; t < r; ++t) {
+    double d = std::fabs(R[(size_t)(k * r + t) * ldr + k * r + t]);
+    if (!(d > 1e-14 * dmax)) ok = false;
+  }
+  k++;
+  return ok;
+}
+
+double BlockLS::resid(int j) const {
+  double s = 0.0;
+  for (int i = k * r; i < (k + 1) * r; ++i) s += g[(size_t)j * ldr + i] * g[(size_t)j * ldr + i];
+  return std::sqrt(s);
+}
+
+void BlockLS::solve(std::vector<double>& Y) const {
+  const int n = k * r;
+  Y.assign((size_t)n * J, 0.0);
+  for (int j = 0; j < J; ++j) {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = g[(size_t)j * ldr + i];
+      for (int c = i + 1; c < n; ++c) s -= R[(size_t)c * ldr + i] * Y[(size_t)c * J + j];
+      double d = R[(size_t)i * ldr + i];
+      Y[(size_t)i * J + j] = (d != 0.0) ? s / d : 0.0;
+    }
+  }
+}
+
+}  // namespace mhde

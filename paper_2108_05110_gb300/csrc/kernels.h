@@ -1,0 +1,101 @@
+// Launch wrappers of the libmhde device kernels.  All multi-vectors are
+// row-major [rows][Jp] with J real columns (the rest zero).  Velocity rows
+// are ordered node-major: row 2a + c is component c of P2 node a; pressure
+// row i of a saddle multi-vector is row 2 n2 + i.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mhde_internal.h"
+
+namespace mhde {
+
+// Kernel launches issued by this library (all contexts), for the
+// benchmark's launch count.
+long long launch_count();
+void count_launch(long long n = 1);
+
+struct QuadTables {             // degree-5 rule and P2 basis tables (host copy)
+  double lam[NQ][3];
+  double w[NQ];                 // reference weights, sum 1/2
+  double phi[NQ][NLOC];
+  double dphi[NQ][NLOC][3];     // d phi_a / d lambda_k
+};
+void quad_tables(QuadTables& q);
+cudaError_t upload_quad_tables();
+
+// ---- finite element kernels (FP64) ----------------------------------------
+void launch_const_local(int nt, const double* geom, double* Mloc, double* Kloc, double* Bloc,
+                        cudaStream_t st);
+void launch_gather_const(const mhde_ctx* c, cudaStream_t st);
+void launch_means(int n2, int J, int Jp, const double* Sv, const double* Sw, double* mv, double* mw,
+                  cudaStream_t st);
+void launch_l2(int nt, int J, int Jp, const int* dofs, const double* Sv, const double* Sw,
+               const double* mv, const double* mw, double* l2v, double* l2w, cudaStream_t st);
+void launch_F_local(int nt, const int* dofs, const double* geom, const double* mean_conv,
+                    const double* l2, double coef_eddy, int conv_form, double* Floc,
+                    cudaStream_t st);
+void launch_F_gather(const mhde_ctx* c, const double* Floc, double inv_dt, double nu_hat,
+                     double* Fval, float* Fvalf, double* Fdinv, float* Fdinvf, cudaStream_t st);
+void launch_rhs_conv_local(int nt, int J, int Jp, const int* dofs, const double* geom,
+                           const double* S_self, const double* S_other, const double* mean_other,
+                           int conv_form, double* Cloc, cudaStream_t st);
+void launch_rhs_assemble(const mhde_ctx* c, const double* S_self, const double* S_other,
+                         const double* Fz, const double* G, const double* Cloc,
+                         const double* c_cross, const double* c_same, double* Bv, cudaStream_t st);
+
+// ---- linear algebra kernels (T = double or float) -------------------------
+// Y = A X (mode 0) or Y = Bvec - A X (mode 1) for the saddle matrix.
+template <typename T>
+void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T* BTval, const T* X,
+                        const double* Bvec, T* Y, int mode, cudaStream_t st);
+// generic CSR: mode 0 y = A x; 1 y = b - A x; 2 y = x + omega dinv (b - A x);
+// 3 y = omega dinv b; 4 y += A x
+template <typename T>
+void launch_csr(int nrows, const int* rowptr, const int* col, const T* val, const T* dinv, T omega,
+                const T* x, const T* b, T* y, int mode, int Jp, cudaStream_t st);
+template <typename T>
+void launch_dense_apply(int n, const T* Ainv, const T* x, T* y, int Jp, cudaStream_t st);
+// velocity rows: z = dinv r (first) or z_out = z_in + omega dinv (r - F z_in); identity rows copy r
+template <typename T>
+void launch_jacobi_F(const mhde_ctx* c, const T* Fval, const T* Fdinv, T omega, const T* r,
+                     const T* zin, T* zout, cudaStream_t st);
+// pressure part of the block preconditioner:
+//   zp = -(1/dt) x - nu_hat rp / mp, zp[0] = rp[0]
+template <typename T>
+void launch_precond_p(int np, int Jp, const T* x, const T* rp, const T* mp, T inv_dt, T nu_hat,
+                      T* zp, cudaStream_t st);
+// tu = ru - B^T zp (velocity rows; Dirichlet rows keep ru)
+template <typename T>
+void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu,
+                     cudaStream_t st);
+// Gram partial sums: part[chunk][i][p][q] = sum_rows V_i[row][p] W[row][q]
+template <typename T>
+void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
+                 int nchunk, double* part, double* gram, cudaStream_t st);
+// out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q], q < r_out; 0 beyond
+template <typename T>
+void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
+                          int r_in, const T* C, int r_out, int n_rows, int Jp, cudaStream_t st);
+// per-chunk column sums of squares (FP64)
+template <typename T>
+void launch_colsq(const T* X, int n_rows, int Jp, int nchunk, double* out, cudaStream_t st);
+// y[:, j] = (T)(x[:, j] * scale[j])   (FP64 -> T with per-column scaling)
+template <typename T>
+void launch_scale_to(const double* x, const double* scale, T* y, size_t n, int Jp, cudaStream_t st);
+// x[:, j] += (double) d[:, j] * scale[j]
+template <typename T>
+void launch_axpy_from(const T* d, const double* scale, double* x, size_t n, int Jp, cudaStream_t st);
+// out = a x + b y (elementwise, n entries)
+template <typename T>
+void launch_axpby(T* out, T a, const T* x, T b, const T* y, size_t n, cudaStream_t st);
+void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st);
+
+// solver entry points (solver.cu)
+int assemble_sub(mhde_ctx* c, int which);
+int solve_sub(mhde_ctx* c, int which);
+// benchmark helpers in the context's Krylov precision
+void precond_apply_any(mhde_ctx* c, int which, const void* in, void* out);
+void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W);
+
+}  // namespace mhde

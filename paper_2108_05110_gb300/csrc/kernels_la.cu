@@ -1,0 +1,488 @@
+// Linear-algebra kernels of the shared-matrix block solve (Section 1: one
+// matrix A for all J right-hand sides, A [x_1 | ... | x_J] = [b_1 | ... | b_J],
+// solved with block linear solvers).  Every multi-vector is row-major
+// [rows][Jp]; a thread owns one 16-byte chunk of one row (2 doubles or 4
+// floats), so the J-wide rows that a sparse row gathers are read as
+// contiguous, coalesced vector loads and the matrix values / column indices of
+// a row are broadcast to the threads sharing that row.
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace mhde {
+
+template <typename T> struct Vec;
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+
+__device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float4 vzero(float4) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void vfma(double2& acc, double s, const double2& x) {
+  acc.x = fma(s, x.x, acc.x);
+  acc.y = fma(s, x.y, acc.y);
+}
+__device__ __forceinline__ void vfma(float4& acc, float s, const float4& x) {
+  acc.x = fmaf(s, x.x, acc.x);
+  acc.y = fmaf(s, x.y, acc.y);
+  acc.z = fmaf(s, x.z, acc.z);
+  acc.w = fmaf(s, x.w, acc.w);
+}
+__device__ __forceinline__ double2 vaxpby(double a, const double2& x, double b, const double2& y) {
+  return make_double2(a * x.x + b * y.x, a * x.y + b * y.y);
+}
+__device__ __forceinline__ float4 vaxpby(float a, const float4& x, float b, const float4& y) {
+  return make_float4(a * x.x + b * y.x, a * x.y + b * y.y, a * x.z + b * y.z, a * x.w + b * y.w);
+}
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------ saddle SpMM
+// Velocity row (a, c):  sum_k F_ak X(col_k, c) + sum_i B^T_ai(c) X_p(i)
+// Pressure row i:       sum_k Bx_ik X(a_k, 0) + By_ik X(a_k, 1)
+// Dirichlet velocity rows and pressure row 0 are identity rows.
+template <typename T, int MODE>
+__global__ void k_saddle(int n2, int np, int nch, const int* __restrict__ frp, const int* __restrict__ fcol,
+                         const T* __restrict__ Fval, const int* __restrict__ btrp,
+                         const int* __restrict__ btcol, const T* __restrict__ BTval,
+                         const int* __restrict__ brp, const int* __restrict__ bcol,
+                         const T* __restrict__ Bval, const unsigned char* __restrict__ isbnd,
+                         const T* __restrict__ X, const double* __restrict__ Bvec, T* __restrict__ Y) {
+  using V = typename Vec<T>::type;
+  const V* Xv = reinterpret_cast<const V*>(X);
+  V* Yv = reinterpret_cast<V*>(Y);
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long nvel = (long long)n2 * 2 * nch;
+  V acc = vzero(V());
+  size_t out;
+  if (tid < nvel) {
+    int a = (int)(tid / (2 * nch));
+    int rem = (int)(tid % (2 * nch));
+    int c = rem / nch, ch = rem % nch;
+    out = ((size_t)(2 * a + c)) * nch + ch;
+    if (isbnd[a]) {
+      acc = Xv[out];
+    } else {
+      for (int k = frp[a]; k < frp[a + 1]; ++k)
+        vfma(acc, Fval[k], Xv[((size_t)(2 * fcol[k] + c)) * nch + ch]);
+      const size_t pbase = (size_t)2 * n2 * nch;
+      for (int k = btrp[a]; k < btrp[a + 1]; ++k)
+        vfma(acc, BTval[2 * (size_t)k + c], Xv[pbase + (size_t)btcol[k] * nch + ch]);
+    }
+  } else if (tid < nvel + (long long)np * nch) {
+    long long p = tid - nvel;
+    int i = (int)(p / nch), ch = (int)(p % nch);
+    out = (size_t)2 * n2 * nch + (size_t)i * nch + ch;
+    if (i == 0) {
+      acc = Xv[out];
+    } else {
+      for (int k = brp[i]; k < brp[i + 1]; ++k) {
+        size_t x0 = ((size_t)(2 * bcol[k])) * nch + ch;
+        vfma(acc, Bval[2 * (size_t)k], Xv[x0]);
+        vfma(acc, Bval[2 * (size_t)k + 1], Xv[x0 + nch]);
+      }
+    }
+  } else {
+    return;
+  }
+  if (MODE == 0) {
+    Yv[out] = acc;
+  } else {
+    const V* Bb = reinterpret_cast<const V*>(Bvec);
+    Yv[out] = vaxpby(T(1), Bb[out], T(-1), acc);
+  }
+}
+
+template <typename T>
+void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T* BTval, const T* X,
+                        const double* Bvec, T* Y, int mode, cudaStream_t st) {
+  count_launch();
+  int nch = c->Jp / Vec<T>::W;
+  long long n = ((long long)2 * c->fe.n2 + c->fe.np) * nch;
+  if (mode == 0)
+    k_saddle<T, 0><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
+                                                c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
+                                                Bval, c->d_isbnd, X, Bvec, Y);
+  else
+    k_saddle<T, 1><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
+                                                c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
+                                                Bval, c->d_isbnd, X, Bvec, Y);
+}
+
+// ------------------------------------------------------------ generic CSR
+template <typename T>
+__global__ void k_csr(int nrows, int nch, const int* __restrict__ rp, const int* __restrict__ col,
+                      const T* __restrict__ val, const T* __restrict__ dinv, T omega,
+                      const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, int mode) {
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)nrows * nch) return;
+  int r = (int)(tid / nch), ch = (int)(tid % nch);
+  const V* xv = reinterpret_cast<const V*>(x);
+  const V* bv = reinterpret_cast<const V*>(b);
+  V* yv = reinterpret_cast<V*>(y);
+  size_t o = (size_t)r * nch + ch;
+  if (mode == 3) {
+    yv[o] = vaxpby(omega * dinv[r], bv[o], T(0), bv[o]);
+    return;
+  }
+  V acc = vzero(V());
+  for (int k = rp[r]; k < rp[r + 1]; ++k) vfma(acc, val[k], xv[(size_t)col[k] * nch + ch]);
+  if (mode == 0) {
+    yv[o] = acc;
+  } else if (mode == 1) {
+    yv[o] = vaxpby(T(1), bv[o], T(-1), acc);
+  } else if (mode == 2) {
+    V res = vaxpby(T(1), bv[o], T(-1), acc);
+    yv[o] = vaxpby(T(1), xv[o], omega * dinv[r], res);
+  } else {
+    yv[o] = vaxpby(T(1), yv[o], T(1), acc);
+  }
+}
+
+template <typename T>
+void launch_csr(int nrows, const int* rowptr, const int* col, const T* val, const T* dinv, T omega,
+                const T* x, const T* b, T* y, int mode, int Jp, cudaStream_t st) {
+  count_launch();
+  int nch = Jp / Vec<T>::W;
+  long long n = (long long)nrows * nch;
+  k_csr<T><<<nblk(n, 256), 256, 0, st>>>(nrows, nch, rowptr, col, val, dinv, omega, x, b, y, mode);
+}
+
+template <typename T>
+__global__ void k_dense_apply(int n, int nch, const T* __restrict__ A, const T* __restrict__ x,
+                              T* __restrict__ y) {
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)n * nch) return;
+  int r = (int)(tid / nch), ch = (int)(tid % nch);
+  const V* xv = reinterpret_cast<const V*>(x);
+  V acc = vzero(V());
+  for (int k = 0; k < n; ++k) vfma(acc, A[(size_t)r * n + k], xv[(size_t)k * nch + ch]);
+  reinterpret_cast<V*>(y)[(size_t)r * nch + ch] = acc;
+}
+
+template <typename T>
+void launch_dense_apply(int n, const T* Ainv, const T* x, T* y, int Jp, cudaStream_t st) {
+  count_launch();
+  int nch = Jp / Vec<T>::W;
+  long long m = (long long)n * nch;
+  k_dense_apply<T><<<nblk(m, 128), 128, 0, st>>>(n, nch, Ainv, x, y);
+}
+
+// ------------------------------------------------------------ preconditioner pieces
+template <typename T>
+__global__ void k_jacobi_F(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
+                           const T* __restrict__ F, const T* __restrict__ dinv,
+                           const unsigned char* __restrict__ isbnd, T omega, const T* __restrict__ r,
+                           const T* __restrict__ zin, T* __restrict__ zout) {
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)n2 * 2 * nch) return;
+  int a = (int)(tid / (2 * nch));
+  int rem = (int)(tid % (2 * nch));
+  int c = rem / nch, ch = rem % nch;
+  size_t o = ((size_t)(2 * a + c)) * nch + ch;
+  const V* rv = reinterpret_cast<const V*>(r);
+  V* zo = reinterpret_cast<V*>(zout);
+  if (isbnd[a]) {
+    zo[o] = rv[o];
+    return;
+  }
+  if (zin == nullptr) {
+    zo[o] = vaxpby(dinv[a], rv[o], T(0), rv[o]);
+    return;
+  }
+  const V* zi = reinterpret_cast<const V*>(zin);
+  V acc = vzero(V());
+  for (int k = rp[a]; k < rp[a + 1]; ++k) vfma(acc, F[k], zi[((size_t)(2 * col[k] + c)) * nch + ch]);
+  V res = vaxpby(T(1), rv[o], T(-1), acc);
+  zo[o] = vaxpby(T(1), zi[o], omega * dinv[a], res);
+}
+
+template <typename T>
+void launch_jacobi_F(const mhde_ctx* c, const T* Fval, const T* Fdinv, T omega, const T* r,
+                     const T* zin, T* zout, cudaStream_t st) {
+  count_launch();
+  int nch = c->Jp / Vec<T>::W;
+  long long n = (long long)c->fe.n2 * 2 * nch;
+  k_jacobi_F<T><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, nch, c->F.rowptr, c->F.col, Fval, Fdinv,
+                                             c->d_isbnd, omega, r, zin, zout);
+}
+
+template <typename T>
+__global__ void k_precond_p(int np, int nch, const T* __restrict__ x, const T* __restrict__ rp,
+                            const T* __restrict__ mp, T inv_dt, T nu_hat, T* __restrict__ zp) {
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)np * nch) return;
+  int i = (int)(tid / nch);
+  const V* xv = reinterpret_cast<const V*>(x);
+  const V* rv = reinterpret_cast<const V*>(rp);
+  V* zv = reinterpret_cast<V*>(zp);
+  if (i == 0) {
+    zv[tid] = rv[tid];
+    return;
+  }
+  zv[tid] = vaxpby(-inv_dt, xv[tid], -nu_hat / mp[i], rv[tid]);
+}
+
+template <typename T>
+void launch_precond_p(int np, int Jp, const T* x, const T* rp, const T* mp, T inv_dt, T nu_hat,
+                      T* zp, cudaStream_t st) {
+  count_launch();
+  int nch = Jp / Vec<T>::W;
+  long long n = (long long)np * nch;
+  k_precond_p<T><<<nblk(n, 256), 256, 0, st>>>(np, nch, x, rp, mp, inv_dt, nu_hat, zp);
+}
+
+template <typename T>
+__global__ void k_bt_apply(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
+                           const T* __restrict__ BT, const unsigned char* __restrict__ isbnd,
+                           const T* __restrict__ ru, const T* __restrict__ zp, T* __restrict__ tu) {
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)n2 * 2 * nch) return;
+  int a = (int)(tid / (2 * nch));
+  int rem = (int)(tid % (2 * nch));
+  int c = rem / nch, ch = rem % nch;
+  const V* r = reinterpret_cast<const V*>(ru);
+  const V* z = reinterpret_cast<const V*>(zp);
+  V* t = reinterpret_cast<V*>(tu);
+  size_t o = ((size_t)(2 * a + c)) * nch + ch;
+  if (isbnd[a]) {
+    t[o] = r[o];
+    return;
+  }
+  V acc = vzero(V());
+  for (int k = rp[a]; k < rp[a + 1]; ++k) vfma(acc, BT[2 * (size_t)k + c], z[(size_t)col[k] * nch + ch]);
+  t[o] = vaxpby(T(1), r[o], T(-1), acc);
+}
+
+template <typename T>
+void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu,
+                     cudaStream_t st) {
+  count_launch();
+  int nch = c->Jp / Vec<T>::W;
+  long long n = (long long)c->fe.n2 * 2 * nch;
+  k_bt_apply<T><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, nch, c->BT.rowptr, c->BT.col, BTval, c->d_isbnd,
+                                             ru, zp, tu);
+}
+
+// ------------------------------------------------------------ block Gram
+// CTA `chunk` covers a contiguous range of rows.  Thread t owns a 4x4 tile of
+// the r x r block (tile t % ntile) and every G-th row of the range (group
+// t / ntile); tiles are summed over the groups in shared memory in a fixed
+// order, so the result does not depend on scheduling.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, size_t vstride, int kblocks,
+                                              const T* __restrict__ W, int n_rows, int Jp, int r,
+                                              int rows_per_chunk, double* __restrict__ part) {
+  extern __shared__ double sh[];
+  const int nt4 = (r + 3) / 4;
+  const int ntile = nt4 * nt4;
+  const int G = 256 / ntile;
+  const int t = threadIdx.x;
+  const int tile = t % ntile, grp = t / ntile;
+  const int p0 = 4 * (tile / nt4), q0 = 4 * (tile % nt4);
+  const int r0 = blockIdx.x * rows_per_chunk;
+  const int r1 = min(n_rows, r0 + rows_per_chunk);
+  for (int i = 0; i < kblocks; ++i) {
+    const T* Vi = V + (size_t)i * vstride;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    if (grp < G) {
+      for (int row = r0 + grp; row < r1; row += G) {
+        const T* vr = Vi + (size_t)row * Jp;
+        const T* wr = W + (size_t)row * Jp;
+        T a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = (p0 + u < r) ? vr[p0 + u] : T(0);
+          b[u] = (q0 + u < r) ? wr[q0 + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+      }
+    }
+    // reduce over groups
+    if (grp < G) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sh[((size_t)grp * ntile + tile) * 16 + 4 * u + v] = (double)acc[u][v];
+    }
+    __syncthreads();
+    for (int o = t; o < ntile * 16; o += blockDim.x) {
+      double s = 0.0;
+      for (int g = 0; g < G; ++g) s += sh[(size_t)g * ntile * 16 + o];
+      int tl = o / 16, uv = o % 16;
+      int p = 4 * (tl / nt4) + uv / 4, q = 4 * (tl % nt4) + uv % 4;
+      if (p < r && q < r) part[(((size_t)blockIdx.x * kblocks) + i) * r * r + (size_t)p * r + q] = s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_gram_reduce(int nchunk, int total, const double* __restrict__ part,
+                              double* __restrict__ gram) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= total) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * total + o];
+  gram[o] = s;
+}
+
+template <typename T>
+void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
+                 int nchunk, double* part, double* gram, cudaStream_t st) {
+  count_launch(2);
+  int rows_per_chunk = (n_rows + nchunk - 1) / nchunk;
+  int nt4 = (r + 3) / 4;
+  int ntile = nt4 * nt4;
+  int G = 256 / ntile;
+  size_t shmem = (size_t)G * ntile * 16 * sizeof(double);
+  k_gram<T><<<nchunk, 256, shmem, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, rows_per_chunk, part);
+  int total = kblocks * r * r;
+  k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(nchunk, total, part, gram);
+}
+
+// ------------------------------------------------------------ block combine
+template <typename T>
+__global__ void k_block_combine(T* __restrict__ out, const T* __restrict__ in, T alpha,
+                                const T* __restrict__ V, size_t vstride, int kblocks, int r_in,
+                                const T* __restrict__ C, int r_out, int n_rows, int Jp) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)n_rows * Jp) return;
+  int row = (int)(tid / Jp), q = (int)(tid % Jp);
+  if (q >= r_out) {
+    out[tid] = T(0);
+    return;
+  }
+  T acc = in ? alpha * in[tid] : T(0);
+  for (int i = 0; i < kblocks; ++i) {
+    const T* vr = V + (size_t)i * vstride + (size_t)row * Jp;
+    const T* Ci = C + (size_t)i * r_in * r_out;
+    for (int p = 0; p < r_in; ++p) acc += vr[p] * Ci[(size_t)p * r_out + q];
+  }
+  out[tid] = acc;
+}
+
+template <typename T>
+void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
+                          int r_in, const T* C, int r_out, int n_rows, int Jp, cudaStream_t st) {
+  count_launch();
+  long long n = (long long)n_rows * Jp;
+  k_block_combine<T><<<nblk(n, 256), 256, 0, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out,
+                                                  n_rows, Jp);
+}
+
+// ------------------------------------------------------------ column norms, conversions
+template <typename T>
+__global__ void k_colsq(const T* __restrict__ X, int n_rows, int Jp, int rows_per_chunk,
+                        double* __restrict__ out) {
+  extern __shared__ double sh[];
+  int G = blockDim.x / Jp;
+  int j = threadIdx.x % Jp, g = threadIdx.x / Jp;
+  int r0 = blockIdx.x * rows_per_chunk, r1 = min(n_rows, r0 + rows_per_chunk);
+  double s = 0.0;
+  if (g < G)
+    for (int row = r0 + g; row < r1; row += G) {
+      double x = (double)X[(size_t)row * Jp + j];
+      s += x * x;
+    }
+  if (g < G) sh[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < Jp) {
+    double t = 0.0;
+    for (int h = 0; h < G; ++h) t += sh[h * Jp + threadIdx.x];
+    out[(size_t)blockIdx.x * Jp + threadIdx.x] = t;
+  }
+}
+
+template <typename T>
+void launch_colsq(const T* X, int n_rows, int Jp, int nchunk, double* out, cudaStream_t st) {
+  count_launch();
+  int rows_per_chunk = (n_rows + nchunk - 1) / nchunk;
+  int threads = (256 / Jp) * Jp;
+  k_colsq<T><<<nchunk, threads, threads * sizeof(double), st>>>(X, n_rows, Jp, rows_per_chunk, out);
+}
+
+template <typename T>
+__global__ void k_scale_to(const double* __restrict__ x, const double* __restrict__ scale,
+                           T* __restrict__ y, size_t n, int Jp) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y[i] = (T)(x[i] * scale[i % Jp]);
+}
+
+template <typename T>
+void launch_scale_to(const double* x, const double* scale, T* y, size_t n, int Jp, cudaStream_t st) {
+  count_launch();
+  k_scale_to<T><<<nblk((long long)n, 256), 256, 0, st>>>(x, scale, y, n, Jp);
+}
+
+template <typename T>
+__global__ void k_axpy_from(const T* __restrict__ d, const double* __restrict__ scale,
+                            double* __restrict__ x, size_t n, int Jp) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] += (double)d[i] * scale[i % Jp];
+}
+
+template <typename T>
+void launch_axpy_from(const T* d, const double* scale, double* x, size_t n, int Jp, cudaStream_t st) {
+  count_launch();
+  k_axpy_from<T><<<nblk((long long)n, 256), 256, 0, st>>>(d, scale, x, n, Jp);
+}
+
+template <typename T>
+__global__ void k_axpby(T* __restrict__ out, T a, const T* __restrict__ x, T b, const T* __restrict__ y,
+                        size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+template <typename T>
+void launch_axpby(T* out, T a, const T* x, T b, const T* y, size_t n, cudaStream_t st) {
+  count_launch();
+  k_axpby<T><<<nblk((long long)n, 256), 256, 0, st>>>(out, a, x, b, y, n);
+}
+
+__global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
+  count_launch();
+  k_d2f<<<nblk((long long)n, 256), 256, 0, st>>>(x, y, n);
+}
+
+// explicit instantiations
+#define MHDE_INST(T)                                                                                 \
+  template void launch_saddle_spmm<T>(const mhde_ctx*, const T*, const T*, const T*, const T*,       \
+                                      const double*, T*, int, cudaStream_t);                         \
+  template void launch_csr<T>(int, const int*, const int*, const T*, const T*, T, const T*, const T*, \
+                              T*, int, int, cudaStream_t);                                           \
+  template void launch_dense_apply<T>(int, const T*, const T*, T*, int, cudaStream_t);               \
+  template void launch_jacobi_F<T>(const mhde_ctx*, const T*, const T*, T, const T*, const T*, T*,   \
+                                   cudaStream_t);                                                    \
+  template void launch_precond_p<T>(int, int, const T*, const T*, const T*, T, T, T*, cudaStream_t); \
+  template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, cudaStream_t); \
+  template void launch_gram<T>(const T*, size_t, int, const T*, int, int, int, int, double*, double*, \
+                               cudaStream_t);                                                        \
+  template void launch_block_combine<T>(T*, const T*, T, const T*, size_t, int, int, const T*, int,  \
+                                        int, int, cudaStream_t);                                     \
+  template void launch_colsq<T>(const T*, int, int, int, double*, cudaStream_t);                     \
+  template void launch_scale_to<T>(const double*, const double*, T*, size_t, int, cudaStream_t);     \
+  template void launch_axpy_from<T>(const T*, const double*, double*, size_t, int, cudaStream_t);     \
+  template void launch_axpby<T>(T*, T, const T*, T, const T*, size_t, cudaStream_t);
+MHDE_INST(double)
+MHDE_INST(float)
+
+}  // namespace mhde

@@ -1,0 +1,99 @@
+"""CPU tests of the library's host side: the shared object loads and
+exports every function include/mhde.h declares, and the host-built discrete
+structure (P2 numbering, Dirichlet nodes, patterns) matches the oracle's
+independent construction.  No GPU work is done here (contexts are not bound).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import paper_2108_05110_gb300 as P
+from paper_2108_05110_gb300 import ensemble_io
+from oracle.fe import P2Space
+from workloads.ensembles import lid_cavity, channel
+from workloads.mesh import unit_square, channel_step
+
+
+def test_library_exports_every_declared_function():
+    lib = P.load_library()
+    names = P.declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib.lib, n), n
+    assert set(names) == set(P.binding.SIGNATURES)
+
+
+@pytest.mark.parametrize("mesh", [unit_square(6), channel_step(cells_per_unit=2)])
+def test_host_numbering_matches_oracle(mesh):
+    s = P.EnsembleSolver(mesh.xy, mesh.tri, [0.01, 0.02], [0.01, 0.03], 0.5, 0.01, bind=False)
+    S = P2Space(mesh)
+    assert s.sizes.n2 == S.n2 and s.sizes.np == S.np_ and s.sizes.ne == S.ne
+    xy, isb = s.p2_nodes()
+    assert np.array_equal(xy, S.node_xy)
+    assert np.array_equal(isb, S.is_boundary)
+    assert s.sizes.n_boundary == S.boundary.size
+    # pattern sizes: F has the pattern of the oracle's P2 mass matrix, B of its divergence
+    M = S.mass()
+    Bx, _ = S.divergence()
+    nnzF = sp.csr_matrix((np.ones(M.nnz), M.indices, M.indptr), shape=M.shape).nnz
+    assert s.sizes.nnz_F == nnzF
+    Bpat = Bx.copy()
+    Bpat.data[:] = 1.0
+    assert s.sizes.nnz_B == Bpat.nnz
+    assert s.sizes.n_rows == 2 * S.n2 + S.np_
+    assert s.sizes.amg_levels >= 1
+    s.close()
+
+
+def test_create_rejects_bad_input():
+    m = unit_square(3)
+    lib = P.load_library()
+    with pytest.raises(P.MhdeError):
+        P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, -0.1, bind=False)      # dt <= 0
+    with pytest.raises(P.MhdeError):
+        P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], -1.0, 0.1, bind=False)      # s < 0
+    bad = m.tri.copy()
+    bad[0] = bad[0][::-1]                                                         # clockwise
+    with pytest.raises(P.MhdeError):
+        P.EnsembleSolver(m.xy, bad, [0.01], [0.01], 1.0, 0.1, bind=False)
+    # alpha_j <= 0 is an error only with strict = 1 (Section 3.1)
+    nu, nu_m = [0.01, 0.02], [0.2, 0.001]
+    P.EnsembleSolver(m.xy, m.tri, nu, nu_m, 1.0, 0.1, bind=False).close()
+    with pytest.raises(P.MhdeError) as e:
+        P.EnsembleSolver(m.xy, m.tri, nu, nu_m, 1.0, 0.1, bind=False, strict=1)
+    assert e.value.code == -2
+    with pytest.raises(P.MhdeError):
+        P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, strict=1, mu=0.4)
+
+
+def test_calls_before_bind_fail_cleanly():
+    ens = lid_cavity(N=4, J=2, nsteps=1)
+    s = ensemble_io.solver_for(ens, bind=False)
+    with pytest.raises(P.MhdeError) as e:
+        s.step()
+    assert e.value.code == -7
+    with pytest.raises(P.MhdeError):
+        s.set_initial(np.zeros((2, s.n2, 2)))
+    s.close()
+
+
+def test_workspace_grows_with_members_and_precision():
+    m = unit_square(8)
+    sizes = {}
+    for J in (2, 8):
+        for prec in (0, 1):
+            s = P.EnsembleSolver(m.xy, m.tri, np.full(J, 0.01), np.full(J, 0.01), 1.0, 0.01, bind=False,
+                                 precision=prec)
+            sizes[(J, prec)] = s.workspace_size()
+            s.close()
+    assert sizes[(8, 1)] > sizes[(2, 1)]
+    assert sizes[(8, 0)] > sizes[(8, 1)]
+
+
+def test_channel_mesh_builds_hierarchy():
+    ens = channel(J=2, nsteps=1, cells_per_unit=3)
+    s = ensemble_io.solver_for(ens, bind=False)
+    assert s.sizes.amg_levels >= 2
+    s.close()
