@@ -73,7 +73,7 @@ typedef struct {
   double inner_rtol;    /* mixed: FP32 inner relative tolerance per refinement sweep; default 1e-5 */
   int restart;          /* block GMRES restart length m (blocks); default 30 */
   int max_iter;         /* cap on block GMRES iterations per subproblem solve; default 2000 */
-  int max_refine;       /* mixed: cap on refinement sweeps; default 12 */
+  int max_refine;       /* cap on FP64 refinement sweeps (one block GMRES cycle each); default 60 */
   int jacobi_sweeps;    /* damped Jacobi sweeps approximating F^{-1}; default 3 */
   double jacobi_omega;  /* damping of those sweeps; default 0.3 */
   int amg_sweeps;       /* Jacobi sweeps per level in the pressure-Laplacian V-cycle; default 2 */

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <thread>
 
@@ -146,7 +147,7 @@ size_t layout(mhde_ctx* c, char* base) {
     s.Dk = w.take<char>(vs * ks);
     s.part = w.take<double>((size_t)c->nchunk * (m + 1) * c->J * c->J);
     s.gram = w.take<double>((size_t)(m + 1) * c->J * c->J);
-    s.coef = w.take<char>((size_t)(m + 1) * c->J * c->J * 8);
+    s.coef = w.take<char>(4 * (size_t)(m + 1) * c->J * c->J * 8);
     s.colsq = w.take<double>((size_t)c->nchunk * Jp);
     s.dscale = w.take<double>(2 * Jp);
     s.amg.assign(amg.levels.size(), DevAmgLevel());
@@ -206,7 +207,7 @@ void mhde_default_options(mhde_options* o) {
   o->inner_rtol = 1e-5;
   o->restart = 30;
   o->max_iter = 2000;
-  o->max_refine = 12;
+  o->max_refine = 60;
   o->jacobi_sweeps = 3;
   o->jacobi_omega = 0.3;
   o->amg_sweeps = 2;
@@ -268,6 +269,10 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
     return MHDE_ESTAB;
   }
   c->nchunk = std::max(1, std::min(304, (c->n_rows + 255) / 256));
+  const char* tr = std::getenv("MHDE_TRACE");
+  c->trace = tr && tr[0] == '1';
+  const char* gr = std::getenv("MHDE_GRAPHS");
+  c->use_graphs = !(gr && gr[0] == '0');
   c->amg_levels = (int)c->fe.amg.levels.size();
   *out = c;
   return MHDE_OK;
@@ -398,7 +403,7 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
     Sub& s = c->sub[which];
     CU(cudaMallocHost((void**)&s.hbuf, sizeof(double) * small));
     CU(cudaMallocHost((void**)&s.hcol, sizeof(double) * c->nchunk * c->Jp));
-    CU(cudaMallocHost(&s.hcoef, sizeof(double) * small));
+    CU(cudaMallocHost(&s.hcoef, 4 * sizeof(double) * small));
   }
   c->bound = true;
   return MHDE_OK;
@@ -682,6 +687,7 @@ void mhde_destroy(mhde_ctx* c) {
     cudaStreamSynchronize(c->sv);
     cudaStreamSynchronize(c->sw);
     for (int which = 0; which < 2; ++which) {
+      for (auto& kv : c->sub[which].prec_graphs) cudaGraphExecDestroy(kv.second.first);
       if (c->sub[which].hbuf) cudaFreeHost(c->sub[which].hbuf);
       if (c->sub[which].hcol) cudaFreeHost(c->sub[which].hcol);
       if (c->sub[which].hcoef) cudaFreeHost(c->sub[which].hcoef);
@@ -767,10 +773,12 @@ int mhde_probe_spmm(mhde_ctx* c, int which, int precision, const double* X, doub
   Sub& s = c->sub[which];
   double* dx = s.Res;   // FP64 scratch: the probe runs outside a step
   double* dy = s.X;
+  CU(cudaStreamSynchronize(c->sv));
   CU(cudaMemcpy(dx, buf.data(), vs * sizeof(double), cudaMemcpyHostToDevice));
   if (precision == 0) {
     launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, dx, nullptr, dy, 0, c->sv);
     CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->sv));
     CU(cudaMemcpy(buf.data(), dy, vs * sizeof(double), cudaMemcpyDeviceToHost));
   } else {
     float* fx = (float*)s.Wk;
@@ -781,6 +789,7 @@ int mhde_probe_spmm(mhde_ctx* c, int which, int precision, const double* X, doub
     launch_d2f(dx, fx, vs, c->sv);
     launch_saddle_spmm<float>(c, s.Fvalf, c->B.valf, c->BT.valf, fx, nullptr, fy, 0, c->sv);
     CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->sv));
     std::vector<float> fb(vs);
     CU(cudaMemcpy(fb.data(), fy, vs * sizeof(float), cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < vs; ++i) buf[i] = fb[i];

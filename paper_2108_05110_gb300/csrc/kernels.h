@@ -14,6 +14,7 @@ namespace mhde {
 // benchmark's launch count.
 long long launch_count();
 void count_launch(long long n = 1);
+void set_capturing(bool on);   // launches issued while capturing a graph are not counted
 
 struct QuadTables {             // degree-5 rule and P2 basis tables (host copy)
   double lam[NQ][3];
@@ -77,6 +78,10 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
                           int r_in, const T* C, int r_out, int n_rows, int Jp, cudaStream_t st);
+// out[row][q] = (T) sum_p X[row][p] C[p][q], q < r (0 beyond); X, C (J x r) in FP64
+template <typename T>
+void launch_combine_from_f64(T* out, const double* X, const double* C, int J, int r, int n_rows, int Jp,
+                             cudaStream_t st);
 // per-chunk column sums of squares (FP64)
 template <typename T>
 void launch_colsq(const T* X, int n_rows, int Jp, int nchunk, double* out, cudaStream_t st);

@@ -16,8 +16,12 @@
 namespace mhde {
 
 static std::atomic<long long> g_launches{0};
+static thread_local bool g_capturing = false;
 long long launch_count() { return g_launches.load(); }
-void count_launch(long long n) { g_launches += n; }
+void count_launch(long long n) {
+  if (!g_capturing) g_launches += n;
+}
+void set_capturing(bool on) { g_capturing = on; }
 
 __constant__ double c_lam[NQ][3];
 __constant__ double c_w[NQ];

@@ -5,6 +5,7 @@
 // floats), so the J-wide rows that a sparse row gathers are read as
 // contiguous, coalesced vector loads and the matrix values / column indices of
 // a row are broadcast to the threads sharing that row.
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.h"
@@ -269,15 +270,22 @@ void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp
 }
 
 // ------------------------------------------------------------ block Gram
-// CTA `chunk` covers a contiguous range of rows.  Thread t owns a 4x4 tile of
-// the r x r block (tile t % ntile) and every G-th row of the range (group
-// t / ntile); tiles are summed over the groups in shared memory in a fixed
-// order, so the result does not depend on scheduling.
+// CTA `chunk` covers a contiguous range of rows.  For every basis block i the
+// CTA streams 64-row tiles of V_i and W (contiguous in memory) into shared
+// memory; thread t owns a 4x4 tile of the r x r block (tile t % ntile) and
+// every G-th row of the staged tile (group t / ntile).  Partial tiles are
+// summed over the groups in a fixed order, so the result does not depend on
+// scheduling.
+constexpr int GRAM_TR = 64;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, size_t vstride, int kblocks,
                                               const T* __restrict__ W, int n_rows, int Jp, int r,
                                               int rows_per_chunk, double* __restrict__ part) {
-  extern __shared__ double sh[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Vs = reinterpret_cast<T*>(smem_raw);
+  T* Ws = Vs + GRAM_TR * Jp;
+  double* red = reinterpret_cast<double*>(Ws + GRAM_TR * Jp);
   const int nt4 = (r + 3) / 4;
   const int ntile = nt4 * nt4;
   const int G = 256 / ntile;
@@ -293,36 +301,47 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, size_t vs
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-    if (grp < G) {
-      for (int row = r0 + grp; row < r1; row += G) {
-        const T* vr = Vi + (size_t)row * Jp;
-        const T* wr = W + (size_t)row * Jp;
-        T a[4], b[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          a[u] = (p0 + u < r) ? vr[p0 + u] : T(0);
-          b[u] = (q0 + u < r) ? wr[q0 + u] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    for (int tr0 = r0; tr0 < r1; tr0 += GRAM_TR) {
+      const int nr = min(GRAM_TR, r1 - tr0);
+      const int nel = nr * Jp;            // contiguous elements of the tile
+      const T* vsrc = Vi + (size_t)tr0 * Jp;
+      const T* wsrc = W + (size_t)tr0 * Jp;
+      for (int e = t; e < nel; e += blockDim.x) {
+        Vs[e] = vsrc[e];
+        Ws[e] = wsrc[e];
       }
+      __syncthreads();
+      if (grp < G) {
+        for (int row = grp; row < nr; row += G) {
+          const T* vr = Vs + row * Jp;
+          const T* wr = Ws + row * Jp;
+          T a[4], b[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            a[u] = vr[p0 + u];
+            b[u] = wr[q0 + u];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+      }
+      __syncthreads();
     }
-    // reduce over groups
     if (grp < G) {
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) sh[((size_t)grp * ntile + tile) * 16 + 4 * u + v] = (double)acc[u][v];
+        for (int v = 0; v < 4; ++v) red[((size_t)grp * ntile + tile) * 16 + 4 * u + v] = (double)acc[u][v];
     }
     __syncthreads();
     for (int o = t; o < ntile * 16; o += blockDim.x) {
-      double s = 0.0;
-      for (int g = 0; g < G; ++g) s += sh[(size_t)g * ntile * 16 + o];
+      double sum = 0.0;
+      for (int g = 0; g < G; ++g) sum += red[(size_t)g * ntile * 16 + o];
       int tl = o / 16, uv = o % 16;
       int p = 4 * (tl / nt4) + uv / 4, q = 4 * (tl % nt4) + uv % 4;
-      if (p < r && q < r) part[(((size_t)blockIdx.x * kblocks) + i) * r * r + (size_t)p * r + q] = s;
+      if (p < r && q < r) part[(((size_t)blockIdx.x * kblocks) + i) * r * r + (size_t)p * r + q] = sum;
     }
     __syncthreads();
   }
@@ -338,47 +357,156 @@ __global__ void k_gram_reduce(int nchunk, int total, const double* __restrict__ 
 }
 
 template <typename T>
-void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
-                 int nchunk, double* part, double* gram, cudaStream_t st) {
-  count_launch(2);
-  int rows_per_chunk = (n_rows + nchunk - 1) / nchunk;
+static size_t gram_smem(int Jp, int r) {
   int nt4 = (r + 3) / 4;
   int ntile = nt4 * nt4;
   int G = 256 / ntile;
-  size_t shmem = (size_t)G * ntile * 16 * sizeof(double);
+  return 2 * (size_t)GRAM_TR * Jp * sizeof(T) + (size_t)G * ntile * 16 * sizeof(double);
+}
+
+template <typename T>
+void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
+                 int nchunk, double* part, double* gram, cudaStream_t st) {
+  count_launch(2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    attr_set = true;
+  }
+  int rows_per_chunk = (n_rows + nchunk - 1) / nchunk;
+  size_t shmem = gram_smem<T>(Jp, r);
   k_gram<T><<<nchunk, 256, shmem, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, rows_per_chunk, part);
   int total = kblocks * r * r;
   k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(nchunk, total, part, gram);
 }
 
 // ------------------------------------------------------------ block combine
-template <typename T>
-__global__ void k_block_combine(T* __restrict__ out, const T* __restrict__ in, T alpha,
-                                const T* __restrict__ V, size_t vstride, int kblocks, int r_in,
-                                const T* __restrict__ C, int r_out, int n_rows, int Jp) {
-  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= (long long)n_rows * Jp) return;
-  int row = (int)(tid / Jp), q = (int)(tid % Jp);
-  if (q >= r_out) {
-    out[tid] = T(0);
-    return;
+// out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q].
+// One thread per row keeps the QMAX output columns in registers; the
+// coefficient blocks are staged in shared memory in groups that fit 48 KB and
+// read as broadcast vector loads.
+template <typename T, int QMAX>
+__global__ void __launch_bounds__(128) k_block_combine(T* __restrict__ out, const T* __restrict__ in, T alpha,
+                                                       const T* __restrict__ V, size_t vstride, int kblocks,
+                                                       int r_in, const T* __restrict__ C, int r_out,
+                                                       int n_rows, int Jp, int kgroup) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Cs = reinterpret_cast<T*>(smem_raw);           // [kgroup * r_in][QMAX]
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  T acc[QMAX];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) acc[q] = T(0);
+  for (int i0 = 0; i0 < kblocks; i0 += kgroup) {
+    const int nb = min(kgroup, kblocks - i0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * r_in * QMAX; e += blockDim.x) {
+      int q = e % QMAX, pi = e / QMAX;             // pi = ib * r_in + p
+      int ib = pi / r_in, p = pi % r_in;
+      Cs[e] = (q < r_out) ? C[((size_t)(i0 + ib) * r_in + p) * r_out + q] : T(0);
+    }
+    __syncthreads();
+    if (row < n_rows) {
+      for (int ib = 0; ib < nb; ++ib) {
+        const T* vr = V + (size_t)(i0 + ib) * vstride + (size_t)row * Jp;
+        const T* cb = Cs + (size_t)ib * r_in * QMAX;
+        for (int p = 0; p < r_in; ++p) {
+          const T v = vr[p];
+          const T* cp = cb + p * QMAX;
+#pragma unroll
+          for (int q = 0; q < QMAX; ++q) acc[q] += v * cp[q];
+        }
+      }
+    }
   }
-  T acc = in ? alpha * in[tid] : T(0);
-  for (int i = 0; i < kblocks; ++i) {
-    const T* vr = V + (size_t)i * vstride + (size_t)row * Jp;
-    const T* Ci = C + (size_t)i * r_in * r_out;
-    for (int p = 0; p < r_in; ++p) acc += vr[p] * Ci[(size_t)p * r_out + q];
-  }
-  out[tid] = acc;
+  if (row >= n_rows) return;
+  T* orow = out + (size_t)row * Jp;
+  const T* irow = in ? in + (size_t)row * Jp : nullptr;
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q)
+    if (q < Jp) orow[q] = (q < r_out) ? (irow ? alpha * irow[q] : T(0)) + acc[q] : T(0);
+  for (int q = QMAX; q < Jp; ++q) orow[q] = T(0);
+}
+
+template <typename T, int QMAX>
+static void combine_q(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
+                      const T* C, int r_out, int n_rows, int Jp, cudaStream_t st) {
+  const size_t per_block = (size_t)r_in * QMAX * sizeof(T);
+  int kgroup = (int)std::max<size_t>(1, (48 * 1024) / std::max<size_t>(per_block, 1));
+  kgroup = std::min(kgroup, std::max(kblocks, 1));
+  size_t shmem = (size_t)kgroup * per_block;
+  k_block_combine<T, QMAX><<<nblk(n_rows, 128), 128, shmem, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C,
+                                                                  r_out, n_rows, Jp, kgroup);
 }
 
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
                           int r_in, const T* C, int r_out, int n_rows, int Jp, cudaStream_t st) {
   count_launch();
-  long long n = (long long)n_rows * Jp;
-  k_block_combine<T><<<nblk(n, 256), 256, 0, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out,
-                                                  n_rows, Jp);
+  if (r_out <= 4)
+    combine_q<T, 4>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+  else if (r_out <= 8)
+    combine_q<T, 8>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+  else if (r_out <= 16)
+    combine_q<T, 16>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+  else if (r_out <= 24)
+    combine_q<T, 24>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+  else if (r_out <= 32)
+    combine_q<T, 32>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+  else if (r_out <= 48)
+    combine_q<T, 48>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+  else
+    combine_q<T, 64>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+}
+
+// out[row][q] = (T) sum_p X[row][p] C[p][q] for q < r (0 beyond), X and C in FP64:
+// the first Krylov block built from the FP64 residual.
+template <typename T, int QMAX>
+__global__ void __launch_bounds__(128) k_combine_from_f64(T* __restrict__ out, const double* __restrict__ X,
+                                                          const double* __restrict__ C, int J, int r,
+                                                          int n_rows, int Jp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Cs = reinterpret_cast<double*>(smem_raw);   // [J][QMAX]
+  for (int e = threadIdx.x; e < J * QMAX; e += blockDim.x) {
+    int q = e % QMAX, p = e / QMAX;
+    Cs[e] = q < r ? C[(size_t)p * r + q] : 0.0;
+  }
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_rows) return;
+  double acc[QMAX];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) acc[q] = 0.0;
+  const double* xr = X + (size_t)row * Jp;
+  for (int p = 0; p < J; ++p) {
+    const double v = xr[p];
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) acc[q] += v * Cs[p * QMAX + q];
+  }
+  T* orow = out + (size_t)row * Jp;
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q)
+    if (q < Jp) orow[q] = q < r ? (T)acc[q] : T(0);
+  for (int q = QMAX; q < Jp; ++q) orow[q] = T(0);
+}
+
+template <typename T>
+void launch_combine_from_f64(T* out, const double* X, const double* C, int J, int r, int n_rows, int Jp,
+                             cudaStream_t st) {
+  count_launch();
+#define MHDE_CF(Q)                                                                                     \
+  k_combine_from_f64<T, Q><<<nblk(n_rows, 128), 128, (size_t)J * Q * sizeof(double), st>>>(out, X, C, J, r, \
+                                                                                           n_rows, Jp)
+  if (r <= 8)
+    MHDE_CF(8);
+  else if (r <= 16)
+    MHDE_CF(16);
+  else if (r <= 24)
+    MHDE_CF(24);
+  else if (r <= 32)
+    MHDE_CF(32);
+  else
+    MHDE_CF(64);
+#undef MHDE_CF
 }
 
 // ------------------------------------------------------------ column norms, conversions
@@ -481,7 +609,9 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
   template void launch_colsq<T>(const T*, int, int, int, double*, cudaStream_t);                     \
   template void launch_scale_to<T>(const double*, const double*, T*, size_t, int, cudaStream_t);     \
   template void launch_axpy_from<T>(const T*, const double*, double*, size_t, int, cudaStream_t);     \
-  template void launch_axpby<T>(T*, T, const T*, T, const T*, size_t, cudaStream_t);
+  template void launch_axpby<T>(T*, T, const T*, T, const T*, size_t, cudaStream_t);               \
+  template void launch_combine_from_f64<T>(T*, const double*, const double*, int, int, int, int,     \
+                                           cudaStream_t);
 MHDE_INST(double)
 MHDE_INST(float)
 

@@ -5,6 +5,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -151,6 +153,8 @@ struct Sub {                       // one subproblem (v: which = 0, w: which = 1
   double* hbuf = nullptr;          // pinned host mirror of gram [m+1][J][J]
   double* hcol = nullptr;          // pinned host column norms [nchunk][Jp]
   std::vector<DevAmgLevel> amg;    // per-subproblem AMG work vectors (shared operators)
+  // captured preconditioner graphs keyed by (input, output) device pointers
+  std::map<std::pair<const void*, const void*>, std::pair<cudaGraphExec_t, long long>> prec_graphs;
   // stats
   int iters = 0, refine = 0;
   double relres = 0.0;
@@ -222,6 +226,8 @@ struct mhde_ctx {
   double* d_ccross = nullptr;          // [Jp] nu_j - nu_m,j
   double* d_csame = nullptr;           // [Jp] nu'_j + nu'_m,j
   int device = 0;
+  bool trace = false;                  // MHDE_TRACE=1: per-sweep residuals on stderr
+  bool use_graphs = true;              // MHDE_GRAPHS=0 disables graph capture
   mhde::Sub sub[2];
   std::vector<int> h_bidx;             // boundary index of every P2 node (host copy)
   std::vector<double> h_M;             // mass matrix values (host copy, for the energy)

@@ -11,6 +11,7 @@
 // M_p the lumped pressure mass.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "kernels.h"
@@ -39,7 +40,7 @@ template <> struct Prec<double> {
   static double* b(DevAmgLevel& L) { return L.b; }
   static double* r(DevAmgLevel& L) { return L.r; }
   static const double* cinv(const mhde_ctx* c) { return c->d_coarse_inv; }
-  static constexpr double thresh = 1e-26;
+  static constexpr double thresh = 1e-22;
 };
 template <> struct Prec<float> {
   static const float* F(const Sub& s) { return s.Fvalf; }
@@ -53,7 +54,7 @@ template <> struct Prec<float> {
   static float* b(DevAmgLevel& L) { return L.bf; }
   static float* r(DevAmgLevel& L) { return L.rf; }
   static const float* cinv(const mhde_ctx* c) { return c->d_coarse_invf; }
-  static constexpr double thresh = 1e-11;
+  static constexpr double thresh = 1e-9;
 };
 
 // ------------------------------------------------------------------ preconditioner
@@ -101,7 +102,7 @@ static void vcycle(const mhde_ctx* c, Sub& s, int l, const T* b, T* x) {
 }
 
 template <typename T>
-static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out) {
+static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out) {
   const int Jp = c->Jp;
   const size_t poff = (size_t)2 * c->fe.n2 * Jp;
   cudaStream_t st = s.stream;
@@ -123,6 +124,43 @@ static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out) {
     std::swap(cur, other);
   }
   if (cur != out) cudaMemcpyAsync(out, cur, poff * sizeof(T), cudaMemcpyDeviceToDevice, st);
+}
+
+// The preconditioner is a fixed sequence of ~30 small kernels whose pointers
+// and scalars do not change for the lifetime of the context (matrix values are
+// read at execution time), so each (in, out) pair is captured once into a
+// CUDA graph and replayed.
+template <typename T>
+static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out) {
+  if (!c->use_graphs) {
+    apply_prec_raw<T>(c, s, in, out);
+    return;
+  }
+  auto key = std::make_pair((const void*)in, (const void*)out);
+  auto it = s.prec_graphs.find(key);
+  if (it == s.prec_graphs.end()) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      apply_prec_raw<T>(c, s, in, out);
+      return;
+    }
+    set_capturing(true);
+    apply_prec_raw<T>(c, s, in, out);
+    set_capturing(false);
+    size_t nodes = 0;
+    if (cudaStreamEndCapture(s.stream, &g) != cudaSuccess || cudaGraphGetNodes(g, nullptr, &nodes) != cudaSuccess ||
+        cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      apply_prec_raw<T>(c, s, in, out);
+      return;
+    }
+    cudaGraphDestroy(g);
+    it = s.prec_graphs.emplace(key, std::make_pair(ge, (long long)nodes)).first;
+  }
+  cudaGraphLaunch(it->second.first, s.stream);
+  count_launch(it->second.second);
 }
 
 // ------------------------------------------------------------------ small helpers
@@ -151,16 +189,18 @@ static int gram_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int 
   return MHDE_OK;
 }
 
-// Upload coefficients (host doubles) to the device coefficient buffer in T.
+// Upload coefficients (host doubles, converted to T) into staging slot
+// `slot` (0..3) of the pinned host buffer and of the device coefficient
+// buffer, without synchronizing: a slot is rewritten only after a later
+// host synchronization (gram_host / col_norms) has drained the stream.
 template <typename T>
-static int upload_coef(const mhde_ctx* c, Sub& s, const std::vector<double>& h, T** dev) {
-  T* hc = (T*)s.hcoef;
+static T* upload_coef(const mhde_ctx* c, Sub& s, const std::vector<double>& h, int slot) {
+  const size_t cap = (size_t)(c->opt.restart + 1) * c->J * c->J;
+  T* hc = reinterpret_cast<T*>(reinterpret_cast<double*>(s.hcoef) + (size_t)slot * cap);
+  T* dc = reinterpret_cast<T*>(reinterpret_cast<char*>(s.coef) + (size_t)slot * cap * sizeof(double));
   for (size_t i = 0; i < h.size(); ++i) hc[i] = (T)h[i];
-  SCU(cudaMemcpyAsync(s.coef, hc, sizeof(T) * h.size(), cudaMemcpyHostToDevice, s.stream));
-  // the host staging buffer is reused by the next upload: wait for this copy
-  SCU(cudaStreamSynchronize(s.stream));
-  *dev = (T*)s.coef;
-  return MHDE_OK;
+  cudaMemcpyAsync(dc, hc, sizeof(T) * h.size(), cudaMemcpyHostToDevice, s.stream);
+  return dc;
 }
 
 // SVQB normalisation of an r-column Gram matrix G: keeps eigen-directions
@@ -185,102 +225,78 @@ static int svqb(int r, const std::vector<double>& G, double thresh, std::vector<
 }
 
 // ------------------------------------------------------------------ block GMRES
-// Solves A D = R0 (both [n_rows][Jp] in T, J columns) to relative residual
-// tol per column (columns of R0 have unit norm or are zero); D in s.Dk.
+// One cycle of right-preconditioned block GMRES for A D = R, where the first
+// basis block V_0 = Res C0 is built from the FP64 residual (C0: J x r, FP64)
+// and R = V_0 S0 (S0: r x J) are the unit-scaled columns of the residual.
+// Stops when every column's residual estimate is <= tol, at m blocks, at a
+// (numerically) rank-deficient new block, or after maxit iterations.  The
+// correction D = P^{-1} V Y is left in s.Dk (Krylov precision).
 template <typename T>
-static int block_gmres(mhde_ctx* c, Sub& s, double tol, int maxit, int& used) {
+static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const std::vector<double>& S0,
+                       int r, double tol, int maxit, int& used) {
   const int J = c->J, Jp = c->Jp, m = c->opt.restart;
   const size_t vs = (size_t)c->n_rows * Jp;
   cudaStream_t st = s.stream;
   T* Vb = (T*)s.basis;
-  T* R0 = (T*)s.Rk;
   T* D = (T*)s.Dk;
   T* Wk = (T*)s.Wk;
   T* Zk = (T*)s.Zk;
-  T* Uk = (T*)s.Uk;
   const double thresh = Prec<T>::thresh;
-  SCU(cudaMemsetAsync(D, 0, vs * sizeof(T), st));
-  // Rcur = R0 initially, kept in Uk between cycles
-  SCU(cudaMemcpyAsync(Uk, R0, vs * sizeof(T), cudaMemcpyDeviceToDevice, st));
   used = 0;
-  std::vector<double> G, Tm, Sm, H, Y;
-  BlockLS ls;
   int rc;
-  while (used < maxit) {
-    // block normalisation of the current residual
-    if ((rc = gram_host<T>(c, s, Uk, 0, 1, Uk, J, G))) return rc;
-    int r = svqb(J, G, thresh, Tm, Sm);
-    if (r == 0) return MHDE_OK;          // zero residual
-    // early exit if the current residual already meets the tolerance
-    {
-      double worst = 0.0;
-      for (int j = 0; j < J; ++j) worst = std::max(worst, std::sqrt(std::max(G[(size_t)j * J + j], 0.0)));
-      if (worst <= tol) return MHDE_OK;
+  double* dC0 = upload_coef<double>(c, s, C0, 3);
+  launch_combine_from_f64<T>(Vb, s.Res, dC0, J, r, c->n_rows, Jp, st);
+  BlockLS ls;
+  ls.init(r, J, m, S0.data());
+  std::vector<double> G, H, Y, Hsum;
+  int k = 0;
+  for (; k < m && used < maxit; ++k) {
+    T* Vk = Vb + (size_t)k * vs;
+    apply_prec<T>(c, s, Vk, Zk);
+    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk, nullptr, Wk, 0, st);
+    // block classical Gram-Schmidt, twice
+    Hsum.assign((size_t)(k + 1) * r * r, 0.0);
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wk, r, H))) return rc;
+      for (size_t t = 0; t < H.size(); ++t) Hsum[t] += H[t];
+      for (auto& v : H) v = -v;
+      T* dc = upload_coef<T>(c, s, H, pass);
+      launch_block_combine<T>(Wk, Wk, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Jp, st);
     }
-    T* dc;
-    if ((rc = upload_coef<T>(c, s, Tm, &dc))) return rc;
-    launch_block_combine<T>(Vb, nullptr, T(0), Uk, 0, 1, J, dc, r, c->n_rows, Jp, st);
-    ls.init(r, J, m, Sm.data());
-    int k = 0;
-    bool done = false;
-    for (; k < m && used < maxit; ++k) {
-      T* Vk = Vb + (size_t)k * vs;
-      apply_prec<T>(c, s, Vk, Zk);
-      launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk, nullptr, Wk, 0, st);
-      // block classical Gram-Schmidt, twice
-      std::vector<double> Hsum((size_t)(k + 1) * r * r, 0.0);
-      for (int pass = 0; pass < 2; ++pass) {
-        if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wk, r, H))) return rc;
-        for (size_t t = 0; t < H.size(); ++t) Hsum[t] += H[t];
-        for (auto& v : H) v = -v;
-        if ((rc = upload_coef<T>(c, s, H, &dc))) return rc;
-        launch_block_combine<T>(Wk, Wk, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Jp, st);
-      }
-      // normalise the new block
-      if ((rc = gram_host<T>(c, s, Wk, 0, 1, Wk, r, G))) return rc;
-      std::vector<double> Tn, Sn;
-      int rk = svqb(r, G, thresh, Tn, Sn);
-      bool breakdown = rk < r;
-      // block column of the Hessenberg matrix, column-major ((k+2) r) x r
-      const int rows = (k + 2) * r;
-      std::vector<double> hcol((size_t)rows * r, 0.0);
-      for (int i = 0; i <= k; ++i)
-        for (int p = 0; p < r; ++p)
-          for (int q = 0; q < r; ++q)
-            hcol[(size_t)q * rows + i * r + p] = Hsum[(size_t)i * r * r + (size_t)p * r + q];
-      if (!breakdown) {
-        for (int p = 0; p < r; ++p)
-          for (int q = 0; q < r; ++q) hcol[(size_t)q * rows + (k + 1) * r + p] = Sn[(size_t)p * r + q];
-        if ((rc = upload_coef<T>(c, s, Tn, &dc))) return rc;
-        launch_block_combine<T>(Vb + (size_t)(k + 1) * vs, nullptr, T(0), Wk, 0, 1, r, dc, r, c->n_rows,
-                                Jp, st);
-      }
-      bool ok = ls.add(hcol.data());
-      used++;
-      double worst = 0.0;
-      for (int j = 0; j < J; ++j) worst = std::max(worst, ls.resid(j));
-      if (!std::isfinite(worst)) {
-        s.err = "non-finite Krylov residual";
-        return MHDE_ENAN;
-      }
-      if (worst <= tol || breakdown || !ok) {
-        done = worst <= tol || breakdown;
-        k++;
-        break;
-      }
+    // normalise the new block (SVQB)
+    if ((rc = gram_host<T>(c, s, Wk, 0, 1, Wk, r, G))) return rc;
+    std::vector<double> Tn, Sn;
+    int rk = svqb(r, G, thresh, Tn, Sn);
+    bool breakdown = rk < r;
+    const int rows = (k + 2) * r;
+    std::vector<double> hcol((size_t)rows * r, 0.0);
+    for (int i = 0; i <= k; ++i)
+      for (int p = 0; p < r; ++p)
+        for (int q = 0; q < r; ++q)
+          hcol[(size_t)q * rows + i * r + p] = Hsum[(size_t)i * r * r + (size_t)p * r + q];
+    if (!breakdown) {
+      for (int p = 0; p < r; ++p)
+        for (int q = 0; q < r; ++q) hcol[(size_t)q * rows + (k + 1) * r + p] = Sn[(size_t)p * r + q];
+      T* dc = upload_coef<T>(c, s, Tn, 2);
+      launch_block_combine<T>(Vb + (size_t)(k + 1) * vs, nullptr, T(0), Wk, 0, 1, r, dc, r, c->n_rows, Jp, st);
     }
-    // solution of this cycle: D += P^{-1} (V Y)
-    ls.solve(Y);
-    // Y is (k r) x J row-major: block i is rows i r .. (i+1) r - 1
-    if ((rc = upload_coef<T>(c, s, Y, &dc))) return rc;
-    launch_block_combine<T>(Wk, nullptr, T(0), Vb, vs, k, r, dc, J, c->n_rows, Jp, st);
-    apply_prec<T>(c, s, Wk, Zk);
-    launch_axpby<T>(D, T(1), D, T(1), Zk, vs, st);          // D += P^{-1} V Y
-    if (done) return MHDE_OK;
-    // restart from the true residual of the correction equation: R0 - A D
-    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), D, nullptr, Wk, 0, st);
-    launch_axpby<T>(Uk, T(1), R0, T(-1), Wk, vs, st);
+    bool ok = ls.add(hcol.data());
+    used++;
+    double worst = 0.0;
+    for (int j = 0; j < J; ++j) worst = std::max(worst, ls.resid(j));
+    if (!std::isfinite(worst)) {
+      s.err = "non-finite Krylov residual";
+      return MHDE_ENAN;
+    }
+    if (worst <= tol || breakdown || !ok) {
+      k++;
+      break;
+    }
   }
+  ls.solve(Y);
+  T* dc = upload_coef<T>(c, s, Y, 3);
+  launch_block_combine<T>(Wk, nullptr, T(0), Vb, vs, k, r, dc, J, c->n_rows, Jp, st);
+  apply_prec<T>(c, s, Wk, D);
   return MHDE_OK;
 }
 
@@ -307,20 +323,23 @@ template <typename T>
 static int solve_sub_t(mhde_ctx* c, int which) {
   Sub& s = c->sub[which];
   cudaStream_t st = s.stream;
+  const int J = c->J;
   const size_t vs = (size_t)c->n_rows * c->Jp;
   int rc;
   SCU(cudaMemcpyAsync(s.X, s.S, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  std::vector<double> bn, rn;
+  std::vector<double> bn, G, Gs, Tm, Sm, C0;
   if ((rc = col_norms<double>(c, s, s.Bv, bn))) return rc;
   s.iters = 0;
   s.refine = 0;
   const bool fp64 = std::is_same<T, double>::value;
-  std::vector<double> scale(c->Jp, 0.0), unscale(c->Jp, 0.0);
+  std::vector<double> rn(J), sc(J), unscale(c->Jp, 0.0);
   for (;;) {
+    // FP64 residual and its Gram matrix (column norms on the diagonal)
     launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, s.X, s.Bv, s.Res, 1, st);
-    if ((rc = col_norms<double>(c, s, s.Res, rn))) return rc;
+    if ((rc = gram_host<double>(c, s, s.Res, 0, 1, s.Res, J, G))) return rc;
     double worst = 0.0, min_target = 1.0;
-    for (int j = 0; j < c->J; ++j) {
+    for (int j = 0; j < J; ++j) {
+      rn[j] = std::sqrt(std::max(G[(size_t)j * J + j], 0.0));
       double ref = bn[j] > 0.0 ? bn[j] : 1.0;
       double rel = rn[j] / ref;
       if (!std::isfinite(rel)) {
@@ -331,25 +350,32 @@ static int solve_sub_t(mhde_ctx* c, int which) {
       if (rn[j] > 0.0) min_target = std::min(min_target, c->opt.rtol * ref / rn[j]);
     }
     s.relres = worst;
+    if (c->trace)
+      std::fprintf(stderr, "[mhde] sub %d sweep %d iters %d relres %.3e\n", which, s.refine, s.iters, worst);
     if (worst <= c->opt.rtol) return MHDE_OK;
-    if (s.refine >= (fp64 ? std::max(c->opt.max_refine, 4) : c->opt.max_refine) ||
-        s.iters >= c->opt.max_iter) {
+    if (s.refine >= c->opt.max_refine || s.iters >= c->opt.max_iter) {
       s.err = "solver did not reach rtol (relres " + std::to_string(worst) + ")";
       return MHDE_ENOCONV;
     }
-    double tol_in = fp64 ? std::max(0.3 * min_target, 1e-15) : std::max(c->opt.inner_rtol, 0.3 * min_target);
-    for (int j = 0; j < c->Jp; ++j) {
-      scale[j] = (j < c->J && rn[j] > 0.0) ? 1.0 / rn[j] : 0.0;
-      unscale[j] = (j < c->J) ? rn[j] : 0.0;
-    }
-    SCU(cudaMemcpyAsync(s.dscale, scale.data(), sizeof(double) * c->Jp, cudaMemcpyHostToDevice, st));
-    SCU(cudaMemcpyAsync(s.dscale + c->Jp, unscale.data(), sizeof(double) * c->Jp, cudaMemcpyHostToDevice,
-                        st));
-    launch_scale_to<T>(s.Res, s.dscale, (T*)s.Rk, vs, c->Jp, st);
+    const double tol_in =
+        fp64 ? std::max(0.3 * min_target, 1e-15) : std::max(c->opt.inner_rtol, 0.3 * min_target);
+    // unit-scaled Gram, deflated below the inner tolerance, SVQB
+    for (int j = 0; j < J; ++j) sc[j] = rn[j] > 0.0 ? 1.0 / rn[j] : 0.0;
+    Gs.assign((size_t)J * J, 0.0);
+    for (int i = 0; i < J; ++i)
+      for (int j = 0; j < J; ++j) Gs[(size_t)i * J + j] = G[(size_t)i * J + j] * sc[i] * sc[j];
+    const double tau = 0.1 * tol_in / std::sqrt((double)J);
+    const int r = svqb(J, Gs, std::max(tau * tau, 1e-30), Tm, Sm);
+    if (r == 0) return MHDE_OK;
+    C0.assign((size_t)J * r, 0.0);
+    for (int p = 0; p < J; ++p)
+      for (int t = 0; t < r; ++t) C0[(size_t)p * r + t] = sc[p] * Tm[(size_t)p * r + t];
     int used = 0;
-    if ((rc = block_gmres<T>(c, s, tol_in, c->opt.max_iter - s.iters, used))) return rc;
+    if ((rc = gmres_cycle<T>(c, s, C0, Sm, r, tol_in, c->opt.max_iter - s.iters, used))) return rc;
     s.iters += used;
-    launch_axpy_from<T>((const T*)s.Dk, s.dscale + c->Jp, s.X, vs, c->Jp, st);
+    for (int j = 0; j < J; ++j) unscale[j] = rn[j];
+    SCU(cudaMemcpyAsync(s.dscale, unscale.data(), sizeof(double) * c->Jp, cudaMemcpyHostToDevice, st));
+    launch_axpy_from<T>((const T*)s.Dk, s.dscale, s.X, vs, c->Jp, st);
     SCU(cudaStreamSynchronize(st));
     s.refine++;
   }
