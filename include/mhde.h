@@ -77,6 +77,10 @@ typedef struct {
   int jacobi_sweeps;    /* damped Jacobi sweeps approximating F^{-1}; default 3 */
   double jacobi_omega;  /* damping of those sweeps; default 0.3 */
   int amg_sweeps;       /* Jacobi sweeps per level in the pressure-Laplacian V-cycle; default 2 */
+  int inner_iters;      /* k of the inner per-column GMRES(k) on F (flexible outer GMRES);
+                           0 = damped Jacobi sweeps instead; default 8 */
+  int schur;            /* pressure Schur approximation: 0 Cahouet-Chabard, 1 pressure
+                           convection-diffusion (adds the mean-field P1 convection); default 1 */
   int strict;           /* 1: reject alpha_j <= 0 or mu <= 1/2 with MHDE_ESTAB; default 0 */
 } mhde_options;
 
@@ -169,9 +173,11 @@ int mhde_energy(mhde_ctx* ctx, double* E);
 
 int mhde_get_stats(const mhde_ctx* ctx, mhde_stats* stats);
 
-/* Copy of the full time-stepping state (step counter and the Elsaesser
- * fields with pressures) to / from a caller buffer of mhde_state_bytes()
- * bytes (host).  Loading reproduces an uninterrupted run bit for bit. */
+/* Copy of the full time-stepping state (step counter, the Elsaesser fields
+ * with pressures of the current and of the previous step; the previous one
+ * seeds the solver's initial guess) to / from a caller buffer of
+ * mhde_state_bytes() bytes (host).  Loading reproduces an uninterrupted run
+ * bit for bit. */
 int mhde_state_bytes(const mhde_ctx* ctx, size_t* bytes);
 int mhde_save_state(mhde_ctx* ctx, void* host_buffer);
 int mhde_load_state(mhde_ctx* ctx, const void* host_buffer);
@@ -213,6 +219,28 @@ int mhde_probe_spmm(mhde_ctx* ctx, int which, int precision, const double* X, do
  * 5 block preconditioner (Krylov precision), 6 block Gram of restart/2
  * basis blocks against one block (Krylov precision). */
 int mhde_time_kernel(mhde_ctx* ctx, int which, int kernel, int reps, double* ms);
+
+/* ------------------------------------------------------------------------
+ * Batched block Gram reduction of the block Krylov solve (Section 1: one
+ * shared matrix, all J right-hand sides solved together with block linear
+ * solvers).  Context-free, FP64, device pointers, asynchronous on `stream`
+ * (cudaStream_t as void*, NULL = legacy default stream).
+ * ---------------------------------------------------------------------- */
+
+/* Scratch bytes mhde_block_gram needs for n_rows rows, r columns and
+ * kblocks basis blocks. */
+int mhde_block_gram_scratch_bytes(int n_rows, int r, int kblocks, size_t* bytes);
+
+/* G[i][p][q] = sum_rows V_i[row][p] W[row][q] for i < kblocks, p, q < r.
+ * V_i = V + i * v_stride (elements); V_i and W are row-major [n_rows][ld]
+ * with ld a multiple of 4, r <= ld <= 64 (columns r..ld-1 are read but do
+ * not enter G).  G: device [kblocks][r][r].  scratch: device, at least
+ * mhde_block_gram_scratch_bytes() bytes, owned by the caller; fully
+ * rewritten by every call.  The summation order is fixed (deterministic).
+ * Errors: MHDE_EINVAL (bad sizes / NULL), MHDE_EWORKSPACE (scratch too
+ * small), MHDE_ECUDA (launch failed). */
+int mhde_block_gram(const double* V, size_t v_stride, int kblocks, const double* W, int n_rows, int ld,
+                    int r, double* G, void* scratch, size_t scratch_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -34,7 +34,8 @@ class Options(C.Structure):
     _fields_ = [("mu", C.c_double), ("conv_form", C.c_int), ("precision", C.c_int),
                 ("rtol", C.c_double), ("inner_rtol", C.c_double), ("restart", C.c_int),
                 ("max_iter", C.c_int), ("max_refine", C.c_int), ("jacobi_sweeps", C.c_int),
-                ("jacobi_omega", C.c_double), ("amg_sweeps", C.c_int), ("strict", C.c_int)]
+                ("jacobi_omega", C.c_double), ("amg_sweeps", C.c_int), ("inner_iters", C.c_int),
+                ("schur", C.c_int), ("strict", C.c_int)]
 
 
 class Sizes(C.Structure):
@@ -86,6 +87,9 @@ SIGNATURES = {
     "mhde_probe_rhs": (C.c_int, [_P, C.c_int, _D]),
     "mhde_probe_spmm": (C.c_int, [_P, C.c_int, C.c_int, _D, _D]),
     "mhde_time_kernel": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D]),
+    "mhde_block_gram_scratch_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "mhde_block_gram": (C.c_int, [_P, C.c_size_t, C.c_int, _P, C.c_int, C.c_int, C.c_int, _P, _P,
+                                  C.c_size_t, _P]),
 }
 
 
@@ -146,6 +150,28 @@ def default_options(**kw):
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+def block_gram(V, W, kblocks, r, stream=None):
+    """G_i = V_i^T W through mhde_block_gram.  V: torch float64 CUDA tensor
+    [kblocks, n_rows, ld], W: [n_rows, ld]; returns a torch tensor
+    [kblocks, r, r].  Scratch comes from torch."""
+    import torch
+    lib = load_library()
+    k, n_rows, ld = V.shape
+    nbytes = C.c_size_t()
+    rc = lib.mhde_block_gram_scratch_bytes(n_rows, r, kblocks, C.byref(nbytes))
+    if rc != 0:
+        raise MhdeError(rc, "mhde_block_gram_scratch_bytes")
+    scratch = torch.empty(max(int(nbytes.value), 1), dtype=torch.uint8, device=V.device)
+    G = torch.empty((kblocks, r, r), dtype=torch.float64, device=V.device)
+    st = stream if stream is not None else torch.cuda.current_stream(V.device)
+    rc = lib.mhde_block_gram(C.c_void_p(V.data_ptr()), n_rows * ld, kblocks, C.c_void_p(W.data_ptr()), n_rows,
+                             ld, r, C.c_void_p(G.data_ptr()), C.c_void_p(scratch.data_ptr()), nbytes.value,
+                             C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise MhdeError(rc, "mhde_block_gram")
+    return G
 
 
 class EnsembleSolver:

@@ -80,6 +80,8 @@ size_t layout(mhde_ctx* c, char* base) {
   c->BT.val = w.take<double>(2 * nb);
   c->BT.valf = w.take<float>(2 * nb);
   c->d_btsrc = w.take<int>(nb);
+  c->d_p1slot_ptr = w.take<int>(fe.Kp.nnz() + 1);
+  c->d_p1slot = w.take<int>(nt * 9);
   c->d_node_ptr = w.take<int>(n2 + 1);
   c->d_node_slot = w.take<int>(nt * 6);
   c->d_mp = w.take<double>(np);
@@ -136,6 +138,7 @@ size_t layout(mhde_ctx* c, char* base) {
     s.Bv = w.take<double>(vs);
     s.X = w.take<double>(vs);
     s.S = w.take<double>(vs);
+    s.Sprev = w.take<double>(vs);
     s.Res = w.take<double>(vs);
     s.basis = w.take<char>((size_t)(m + 1) * vs * ks);
     s.Wk = w.take<char>(vs * ks);
@@ -150,6 +153,19 @@ size_t layout(mhde_ctx* c, char* base) {
     s.coef = w.take<char>(4 * (size_t)(m + 1) * c->J * c->J * 8);
     s.colsq = w.take<double>((size_t)c->nchunk * Jp);
     s.dscale = w.take<double>(2 * Jp);
+    s.Np = w.take<double>(fe.Kp.nnz());
+    s.Npf = w.take<float>(fe.Kp.nnz());
+    {
+      const int kin = std::max(1, c->opt.inner_iters);
+      const size_t C2 = 2 * Jp;
+      s.ibasis = w.take<char>((size_t)(kin + 1) * n2 * C2 * ks);
+      s.ipart = w.take<double>((size_t)c->nchunk * (KIN_MAX + 2) * C2);
+      s.idot = w.take<double>((size_t)(kin + 2) * C2);
+      s.ih = w.take<double>((size_t)(kin + 1) * kin * C2);
+      s.ibeta = w.take<double>(2 * C2);
+      s.iy = w.take<double>((size_t)kin * C2);
+      s.zbasis = w.take<char>((size_t)m * vs * ks);
+    }
     s.amg.assign(amg.levels.size(), DevAmgLevel());
     for (size_t l = 0; l < amg.levels.size(); ++l) {
       size_t n = (size_t)amg.levels[l].A.nrows * Jp;
@@ -211,6 +227,8 @@ void mhde_default_options(mhde_options* o) {
   o->jacobi_sweeps = 3;
   o->jacobi_omega = 0.3;
   o->amg_sweeps = 2;
+  o->inner_iters = 8;
+  o->schur = 1;
   o->strict = 0;
 }
 
@@ -226,7 +244,8 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
     mhde_default_options(&c->opt);
   if (c->opt.restart < 1 || c->opt.restart > 200 || c->opt.max_iter < 1 || !(c->opt.rtol > 0) ||
       (c->opt.precision != MHDE_PREC_FP64 && c->opt.precision != MHDE_PREC_MIXED) ||
-      (c->opt.conv_form != 0 && c->opt.conv_form != 1)) {
+      (c->opt.conv_form != 0 && c->opt.conv_form != 1) || c->opt.inner_iters < 0 ||
+      c->opt.inner_iters > mhde::KIN_MAX || (c->opt.schur != 0 && c->opt.schur != 1)) {
     delete c;
     return MHDE_EINVAL;
   }
@@ -347,6 +366,8 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   CU(up(c->BT.rowptr, fe.BT.rowptr, st));
   CU(up(c->BT.col, fe.BT.col, st));
   CU(up(c->d_btsrc, fe.bt_src, st));
+  CU(up(c->d_p1slot_ptr, fe.p1_gather_ptr, st));
+  CU(up(c->d_p1slot, fe.p1_gather_slot, st));
   CU(up(c->d_node_ptr, fe.node_ptr, st));
   CU(up(c->d_node_slot, fe.node_slot, st));
   CU(up(c->d_mp, fe.mp_lumped, st));
@@ -431,6 +452,7 @@ int mhde_set_initial(mhde_ctx* c, const double* u0, const double* B0) {
     CU(cudaMemcpy(c->sub[which].S, buf.data(), vs * sizeof(double), cudaMemcpyHostToDevice));
   }
   c->have_initial = true;
+  c->have_prev = false;
   c->steps = 0;
   c->stats = mhde_stats();
   return MHDE_OK;
@@ -514,7 +536,14 @@ int mhde_step(mhde_ctx* c) {
       return c->sub[which].status;
     }
   }
-  for (int which = 0; which < 2; ++which) std::swap(c->sub[which].S, c->sub[which].X);
+  for (int which = 0; which < 2; ++which) {
+    Sub& s = c->sub[which];
+    double* old_prev = s.Sprev;
+    s.Sprev = s.S;
+    s.S = s.X;
+    s.X = old_prev;
+  }
+  c->have_prev = true;
   c->steps++;
   c->stats.steps = c->steps;
   for (int which = 0; which < 2; ++which) {
@@ -649,7 +678,7 @@ int mhde_get_stats(const mhde_ctx* c, mhde_stats* st) {
 
 int mhde_state_bytes(const mhde_ctx* c, size_t* bytes) {
   if (!c || !bytes) return MHDE_EINVAL;
-  *bytes = sizeof(long long) + 2 * (size_t)c->n_rows * c->Jp * sizeof(double);
+  *bytes = 2 * sizeof(long long) + 4 * (size_t)c->n_rows * c->Jp * sizeof(double);
   return MHDE_OK;
 }
 
@@ -658,10 +687,13 @@ int mhde_save_state(mhde_ctx* c, void* buf) {
   if (rc) return rc;
   if (!buf) return fail(c, MHDE_EINVAL, "buffer is NULL");
   char* p = (char*)buf;
-  std::memcpy(p, &c->steps, sizeof(long long));
+  long long hdr[2] = {c->steps, c->have_prev ? 1 : 0};
+  std::memcpy(p, hdr, sizeof(hdr));
   const size_t vs = (size_t)c->n_rows * c->Jp * sizeof(double);
-  for (int which = 0; which < 2; ++which)
-    CU(cudaMemcpy(p + sizeof(long long) + which * vs, c->sub[which].S, vs, cudaMemcpyDeviceToHost));
+  for (int which = 0; which < 2; ++which) {
+    CU(cudaMemcpy(p + sizeof(hdr) + (2 * which) * vs, c->sub[which].S, vs, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(p + sizeof(hdr) + (2 * which + 1) * vs, c->sub[which].Sprev, vs, cudaMemcpyDeviceToHost));
+  }
   return MHDE_OK;
 }
 
@@ -670,10 +702,15 @@ int mhde_load_state(mhde_ctx* c, const void* buf) {
   if (rc) return rc;
   if (!buf) return fail(c, MHDE_EINVAL, "buffer is NULL");
   const char* p = (const char*)buf;
-  std::memcpy(&c->steps, p, sizeof(long long));
+  long long hdr[2];
+  std::memcpy(hdr, p, sizeof(hdr));
+  c->steps = hdr[0];
+  c->have_prev = hdr[1] != 0;
   const size_t vs = (size_t)c->n_rows * c->Jp * sizeof(double);
-  for (int which = 0; which < 2; ++which)
-    CU(cudaMemcpy(c->sub[which].S, p + sizeof(long long) + which * vs, vs, cudaMemcpyHostToDevice));
+  for (int which = 0; which < 2; ++which) {
+    CU(cudaMemcpy(c->sub[which].S, p + sizeof(hdr) + (2 * which) * vs, vs, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->sub[which].Sprev, p + sizeof(hdr) + (2 * which + 1) * vs, vs, cudaMemcpyHostToDevice));
+  }
   c->have_initial = true;
   c->stats.steps = c->steps;
   return MHDE_OK;

@@ -200,8 +200,9 @@ std::string build_fe(const mhde_mesh* mesh, FeHost& fe) {
     csr_from_keys(uniq, fe.np, fe.np, fe.Kp);
     fe.Kp.val.assign(uniq.size(), 0.0);
     // deterministic: slots in ascending order per nnz
-    std::vector<int> ptr, slots;
-    invert_map(where, (long long)uniq.size(), ptr, slots);
+    invert_map(where, (long long)uniq.size(), fe.p1_gather_ptr, fe.p1_gather_slot);
+    const std::vector<int>& ptr = fe.p1_gather_ptr;
+    const std::vector<int>& slots = fe.p1_gather_slot;
     for (size_t k = 0; k < uniq.size(); ++k)
       for (int t = ptr[k]; t < ptr[k + 1]; ++t) fe.Kp.val[k] += vals[slots[t]];
     // pin node 0: identity row and column

@@ -63,9 +63,10 @@ void launch_jacobi_F(const mhde_ctx* c, const T* Fval, const T* Fdinv, T omega, 
                      const T* zin, T* zout, cudaStream_t st);
 // pressure part of the block preconditioner:
 //   zp = -(1/dt) x - nu_hat rp / mp, zp[0] = rp[0]
+//   (PCD adds - (N_p x) / mp when Np is not null; N_p has the P1 pattern rp/col)
 template <typename T>
 void launch_precond_p(int np, int Jp, const T* x, const T* rp, const T* mp, T inv_dt, T nu_hat,
-                      T* zp, cudaStream_t st);
+                      const int* nrp, const int* ncol, const T* Np, T* zp, cudaStream_t st);
 // tu = ru - B^T zp (velocity rows; Dirichlet rows keep ru)
 template <typename T>
 void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu,
@@ -95,6 +96,15 @@ void launch_axpy_from(const T* d, const double* scale, double* x, size_t n, int 
 template <typename T>
 void launch_axpby(T* out, T a, const T* x, T b, const T* y, size_t n, cudaStream_t st);
 void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st);
+
+// pressure convection matrix N_p(a) of the PCD Schur approximation (P1,
+// standard form (a . grad psi_k, psi_i), a = mean convecting field)
+void launch_Np(const mhde_ctx* c, const double* mean_conv, double* slots, double* Np, float* Npf,
+               cudaStream_t st);
+// inner per-column GMRES(k) on F (velocity block), z ~ F^{-1} r
+template <typename T>
+void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z,
+                        cudaStream_t st);
 
 // solver entry points (solver.cu)
 int assemble_sub(mhde_ctx* c, int which);

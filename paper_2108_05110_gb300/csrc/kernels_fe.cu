@@ -343,6 +343,54 @@ void launch_F_gather(const mhde_ctx* c, const double* Floc, double inv_dt, doubl
                                            Fdinv, Fdinvf);
 }
 
+// ------------------------------------------------------------ PCD pressure convection
+// Element slots [e][3][3]: (a . grad psi_k, psi_i) with psi = lambda (P1).
+__global__ void k_Np_local(int nt, const int* __restrict__ dofs, const double* __restrict__ geom,
+                           const double* __restrict__ mconv, double* __restrict__ slots) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  double gl[3][2], det;
+  load_geom(geom, e, gl, det);
+  double an[NLOC][2];
+  for (int a = 0; a < NLOC; ++a) {
+    int d = dofs[6 * (size_t)e + a];
+    an[a][0] = mconv[2 * (size_t)d];
+    an[a][1] = mconv[2 * (size_t)d + 1];
+  }
+  double loc[9];
+  for (int t = 0; t < 9; ++t) loc[t] = 0.0;
+  for (int q = 0; q < NQ; ++q) {
+    double ax = 0.0, ay = 0.0;
+    for (int a = 0; a < NLOC; ++a) {
+      ax += c_phi[q][a] * an[a][0];
+      ay += c_phi[q][a] * an[a][1];
+    }
+    double wq = c_w[q] * det;
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) loc[3 * i + k] += wq * (ax * gl[k][0] + ay * gl[k][1]) * c_lam[q][i];
+  }
+  for (int t = 0; t < 9; ++t) slots[9 * (size_t)e + t] = loc[t];
+}
+
+__global__ void k_Np_gather(long long nnz, const int* __restrict__ ptr, const int* __restrict__ slot,
+                            const double* __restrict__ slots, double* __restrict__ Np, float* __restrict__ Npf) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  double s = 0.0;
+  for (int t = ptr[k]; t < ptr[k + 1]; ++t) s += slots[slot[t]];
+  Np[k] = s;
+  Npf[k] = (float)s;
+}
+
+void launch_Np(const mhde_ctx* c, const double* mean_conv, double* slots, double* Np, float* Npf,
+               cudaStream_t st) {
+  count_launch(2);
+  int nt = c->fe.nt;
+  long long nnz = c->fe.Kp.nnz();
+  k_Np_local<<<(nt + 127) / 128, 128, 0, st>>>(nt, c->d_dofs, c->d_geom, mean_conv, slots);
+  k_Np_gather<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, c->d_p1slot_ptr, c->d_p1slot, slots, Np, Npf);
+}
+
 // ------------------------------------------------------------ right-hand sides
 // Element vectors of b*(a_j, u_j, phi) for a_j = fluctuation of the other
 // field and u_j = member j of this field (skew form 1/2[(a.grad u, phi) -

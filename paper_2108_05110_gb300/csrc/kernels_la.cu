@@ -38,52 +38,97 @@ __device__ __forceinline__ float4 vaxpby(float a, const float4& x, float b, cons
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // ------------------------------------------------------------ saddle SpMM
-// Velocity row (a, c):  sum_k F_ak X(col_k, c) + sum_i B^T_ai(c) X_p(i)
-// Pressure row i:       sum_k Bx_ik X(a_k, 0) + By_ik X(a_k, 1)
-// Dirichlet velocity rows and pressure row 0 are identity rows.
+// Velocity node a, chunk ch (both components):
+//   Y(a, c) = sum_k F_ak X(col_k, c) + sum_i B^T_ai(c) X_p(i)
+// Pressure row i:  sum_k Bx_ik X(a_k, 0) + By_ik X(a_k, 1)
+// Dirichlet velocity rows and pressure row 0 are identity rows.  Each thread
+// owns one 16-byte chunk of both components of a node, so F's values and
+// column indices are loaded once for the two components; the nonzero loops
+// are unrolled by two to keep independent gathers in flight.
 template <typename T, int MODE>
-__global__ void k_saddle(int n2, int np, int nch, const int* __restrict__ frp, const int* __restrict__ fcol,
-                         const T* __restrict__ Fval, const int* __restrict__ btrp,
-                         const int* __restrict__ btcol, const T* __restrict__ BTval,
-                         const int* __restrict__ brp, const int* __restrict__ bcol,
-                         const T* __restrict__ Bval, const unsigned char* __restrict__ isbnd,
-                         const T* __restrict__ X, const double* __restrict__ Bvec, T* __restrict__ Y) {
+__global__ void __launch_bounds__(256) k_saddle(int n2, int np, int nch, const int* __restrict__ frp,
+                                                const int* __restrict__ fcol, const T* __restrict__ Fval,
+                                                const int* __restrict__ btrp, const int* __restrict__ btcol,
+                                                const T* __restrict__ BTval, const int* __restrict__ brp,
+                                                const int* __restrict__ bcol, const T* __restrict__ Bval,
+                                                const unsigned char* __restrict__ isbnd, const T* __restrict__ X,
+                                                const double* __restrict__ Bvec, T* __restrict__ Y) {
   using V = typename Vec<T>::type;
   const V* Xv = reinterpret_cast<const V*>(X);
   V* Yv = reinterpret_cast<V*>(Y);
-  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long nvel = (long long)n2 * 2 * nch;
-  V acc = vzero(V());
-  size_t out;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nvel = (long long)n2 * nch;
   if (tid < nvel) {
-    int a = (int)(tid / (2 * nch));
-    int rem = (int)(tid % (2 * nch));
-    int c = rem / nch, ch = rem % nch;
-    out = ((size_t)(2 * a + c)) * nch + ch;
+    const int a = (int)(tid / nch), ch = (int)(tid % nch);
+    const size_t o0 = ((size_t)(2 * a)) * nch + ch, o1 = o0 + nch;
+    V acc0, acc1;
     if (isbnd[a]) {
-      acc = Xv[out];
+      acc0 = Xv[o0];
+      acc1 = Xv[o1];
     } else {
-      for (int k = frp[a]; k < frp[a + 1]; ++k)
-        vfma(acc, Fval[k], Xv[((size_t)(2 * fcol[k] + c)) * nch + ch]);
+      acc0 = vzero(V());
+      acc1 = vzero(V());
+      int k = frp[a];
+      const int e = frp[a + 1];
+      for (; k + 1 < e; k += 2) {
+        const int c0 = fcol[k], c1 = fcol[k + 1];
+        const T f0 = Fval[k], f1 = Fval[k + 1];
+        const V x00 = Xv[(size_t)(2 * c0) * nch + ch], x01 = Xv[(size_t)(2 * c0 + 1) * nch + ch];
+        const V x10 = Xv[(size_t)(2 * c1) * nch + ch], x11 = Xv[(size_t)(2 * c1 + 1) * nch + ch];
+        vfma(acc0, f0, x00);
+        vfma(acc1, f0, x01);
+        vfma(acc0, f1, x10);
+        vfma(acc1, f1, x11);
+      }
+      if (k < e) {
+        const int c0 = fcol[k];
+        const T f0 = Fval[k];
+        vfma(acc0, f0, Xv[(size_t)(2 * c0) * nch + ch]);
+        vfma(acc1, f0, Xv[(size_t)(2 * c0 + 1) * nch + ch]);
+      }
       const size_t pbase = (size_t)2 * n2 * nch;
-      for (int k = btrp[a]; k < btrp[a + 1]; ++k)
-        vfma(acc, BTval[2 * (size_t)k + c], Xv[pbase + (size_t)btcol[k] * nch + ch]);
-    }
-  } else if (tid < nvel + (long long)np * nch) {
-    long long p = tid - nvel;
-    int i = (int)(p / nch), ch = (int)(p % nch);
-    out = (size_t)2 * n2 * nch + (size_t)i * nch + ch;
-    if (i == 0) {
-      acc = Xv[out];
-    } else {
-      for (int k = brp[i]; k < brp[i + 1]; ++k) {
-        size_t x0 = ((size_t)(2 * bcol[k])) * nch + ch;
-        vfma(acc, Bval[2 * (size_t)k], Xv[x0]);
-        vfma(acc, Bval[2 * (size_t)k + 1], Xv[x0 + nch]);
+      for (int t = btrp[a]; t < btrp[a + 1]; ++t) {
+        const V xp = Xv[pbase + (size_t)btcol[t] * nch + ch];
+        vfma(acc0, BTval[2 * (size_t)t], xp);
+        vfma(acc1, BTval[2 * (size_t)t + 1], xp);
       }
     }
-  } else {
+    if (MODE == 0) {
+      Yv[o0] = acc0;
+      Yv[o1] = acc1;
+    } else {
+      const V* Bb = reinterpret_cast<const V*>(Bvec);
+      Yv[o0] = vaxpby(T(1), Bb[o0], T(-1), acc0);
+      Yv[o1] = vaxpby(T(1), Bb[o1], T(-1), acc1);
+    }
     return;
+  }
+  const long long p = tid - nvel;
+  if (p >= (long long)np * nch) return;
+  const int i = (int)(p / nch), ch = (int)(p % nch);
+  const size_t out = (size_t)2 * n2 * nch + (size_t)i * nch + ch;
+  V acc;
+  if (i == 0) {
+    acc = Xv[out];
+  } else {
+    acc = vzero(V());
+    V acc2 = vzero(V());
+    int k = brp[i];
+    const int e = brp[i + 1];
+    for (; k + 1 < e; k += 2) {
+      const size_t x0 = ((size_t)(2 * bcol[k])) * nch + ch, x1 = ((size_t)(2 * bcol[k + 1])) * nch + ch;
+      const V a0 = Xv[x0], a1 = Xv[x0 + nch], b0 = Xv[x1], b1 = Xv[x1 + nch];
+      vfma(acc, Bval[2 * (size_t)k], a0);
+      vfma(acc, Bval[2 * (size_t)k + 1], a1);
+      vfma(acc2, Bval[2 * (size_t)k + 2], b0);
+      vfma(acc2, Bval[2 * (size_t)k + 3], b1);
+    }
+    if (k < e) {
+      const size_t x0 = ((size_t)(2 * bcol[k])) * nch + ch;
+      vfma(acc, Bval[2 * (size_t)k], Xv[x0]);
+      vfma(acc, Bval[2 * (size_t)k + 1], Xv[x0 + nch]);
+    }
+    acc = vaxpby(T(1), acc, T(1), acc2);
   }
   if (MODE == 0) {
     Yv[out] = acc;
@@ -98,7 +143,7 @@ void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T
                         const double* Bvec, T* Y, int mode, cudaStream_t st) {
   count_launch();
   int nch = c->Jp / Vec<T>::W;
-  long long n = ((long long)2 * c->fe.n2 + c->fe.np) * nch;
+  long long n = ((long long)c->fe.n2 + c->fe.np) * nch;
   if (mode == 0)
     k_saddle<T, 0><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
                                                 c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
@@ -212,11 +257,12 @@ void launch_jacobi_F(const mhde_ctx* c, const T* Fval, const T* Fdinv, T omega, 
 
 template <typename T>
 __global__ void k_precond_p(int np, int nch, const T* __restrict__ x, const T* __restrict__ rp,
-                            const T* __restrict__ mp, T inv_dt, T nu_hat, T* __restrict__ zp) {
+                            const T* __restrict__ mp, T inv_dt, T nu_hat, const int* __restrict__ nrp,
+                            const int* __restrict__ ncol, const T* __restrict__ Np, T* __restrict__ zp) {
   using V = typename Vec<T>::type;
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (tid >= (long long)np * nch) return;
-  int i = (int)(tid / nch);
+  int i = (int)(tid / nch), ch = (int)(tid % nch);
   const V* xv = reinterpret_cast<const V*>(x);
   const V* rv = reinterpret_cast<const V*>(rp);
   V* zv = reinterpret_cast<V*>(zp);
@@ -224,16 +270,22 @@ __global__ void k_precond_p(int np, int nch, const T* __restrict__ x, const T* _
     zv[tid] = rv[tid];
     return;
   }
-  zv[tid] = vaxpby(-inv_dt, xv[tid], -nu_hat / mp[i], rv[tid]);
+  V z = vaxpby(-inv_dt, xv[tid], -nu_hat / mp[i], rv[tid]);
+  if (Np) {
+    V acc = vzero(V());
+    for (int k = nrp[i]; k < nrp[i + 1]; ++k) vfma(acc, Np[k], xv[(size_t)ncol[k] * nch + ch]);
+    z = vaxpby(T(1), z, -T(1) / mp[i], acc);
+  }
+  zv[tid] = z;
 }
 
 template <typename T>
 void launch_precond_p(int np, int Jp, const T* x, const T* rp, const T* mp, T inv_dt, T nu_hat,
-                      T* zp, cudaStream_t st) {
+                      const int* nrp, const int* ncol, const T* Np, T* zp, cudaStream_t st) {
   count_launch();
   int nch = Jp / Vec<T>::W;
   long long n = (long long)np * nch;
-  k_precond_p<T><<<nblk(n, 256), 256, 0, st>>>(np, nch, x, rp, mp, inv_dt, nu_hat, zp);
+  k_precond_p<T><<<nblk(n, 256), 256, 0, st>>>(np, nch, x, rp, mp, inv_dt, nu_hat, nrp, ncol, Np, zp);
 }
 
 template <typename T>
@@ -294,66 +346,69 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, size_t vs
   const int p0 = 4 * (tile / nt4), q0 = 4 * (tile % nt4);
   const int r0 = blockIdx.x * rows_per_chunk;
   const int r1 = min(n_rows, r0 + rows_per_chunk);
-  for (int i = 0; i < kblocks; ++i) {
-    const T* Vi = V + (size_t)i * vstride;
-    T acc[4][4];
+  const int i = blockIdx.y;                       // basis block of this CTA
+  const T* Vi = V + (size_t)i * vstride;
+  T acc[4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-    for (int tr0 = r0; tr0 < r1; tr0 += GRAM_TR) {
-      const int nr = min(GRAM_TR, r1 - tr0);
-      const int nel = nr * Jp;            // contiguous elements of the tile
-      const T* vsrc = Vi + (size_t)tr0 * Jp;
-      const T* wsrc = W + (size_t)tr0 * Jp;
-      for (int e = t; e < nel; e += blockDim.x) {
-        Vs[e] = vsrc[e];
-        Ws[e] = wsrc[e];
-      }
-      __syncthreads();
-      if (grp < G) {
-        for (int row = grp; row < nr; row += G) {
-          const T* vr = Vs + row * Jp;
-          const T* wr = Ws + row * Jp;
-          T a[4], b[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            a[u] = vr[p0 + u];
-            b[u] = wr[q0 + u];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
-        }
-      }
-      __syncthreads();
-    }
-    if (grp < G) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) red[((size_t)grp * ntile + tile) * 16 + 4 * u + v] = (double)acc[u][v];
+    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+  for (int tr0 = r0; tr0 < r1; tr0 += GRAM_TR) {
+    const int nr = min(GRAM_TR, r1 - tr0);
+    const int nel = nr * Jp;                      // contiguous elements of the tile
+    const T* vsrc = Vi + (size_t)tr0 * Jp;
+    const T* wsrc = W + (size_t)tr0 * Jp;
+    for (int e = t; e < nel; e += blockDim.x) {
+      Vs[e] = vsrc[e];
+      Ws[e] = wsrc[e];
     }
     __syncthreads();
-    for (int o = t; o < ntile * 16; o += blockDim.x) {
-      double sum = 0.0;
-      for (int g = 0; g < G; ++g) sum += red[(size_t)g * ntile * 16 + o];
-      int tl = o / 16, uv = o % 16;
-      int p = 4 * (tl / nt4) + uv / 4, q = 4 * (tl % nt4) + uv % 4;
-      if (p < r && q < r) part[(((size_t)blockIdx.x * kblocks) + i) * r * r + (size_t)p * r + q] = sum;
+    if (grp < G) {
+      for (int row = grp; row < nr; row += G) {
+        const T* vr = Vs + row * Jp;
+        const T* wr = Ws + row * Jp;
+        T a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = vr[p0 + u];
+          b[u] = wr[q0 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+      }
     }
     __syncthreads();
   }
+  if (grp < G) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) red[((size_t)grp * ntile + tile) * 16 + 4 * u + v] = (double)acc[u][v];
+  }
+  __syncthreads();
+  for (int o = t; o < ntile * 16; o += blockDim.x) {
+    double sum = 0.0;
+    for (int g = 0; g < G; ++g) sum += red[(size_t)g * ntile * 16 + o];
+    int tl = o / 16, uv = o % 16;
+    int p = 4 * (tl / nt4) + uv / 4, q = 4 * (tl % nt4) + uv % 4;
+    if (p < r && q < r) part[(((size_t)blockIdx.x * kblocks) + i) * r * r + (size_t)p * r + q] = sum;
+  }
 }
 
+// One warp per output entry: lanes stride over the chunks, then a fixed
+// butterfly of shuffles (deterministic order).
 __global__ void k_gram_reduce(int nchunk, int total, const double* __restrict__ part,
                               double* __restrict__ gram) {
-  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
   if (o >= total) return;
   double s = 0.0;
-  for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * total + o];
-  gram[o] = s;
+  for (int c = lane; c < nchunk; c += 32) s += part[(size_t)c * total + o];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) gram[o] = s;
 }
 
 template <typename T>
@@ -375,9 +430,10 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
   }
   int rows_per_chunk = (n_rows + nchunk - 1) / nchunk;
   size_t shmem = gram_smem<T>(Jp, r);
-  k_gram<T><<<nchunk, 256, shmem, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, rows_per_chunk, part);
+  k_gram<T><<<dim3(nchunk, kblocks), 256, shmem, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, rows_per_chunk,
+                                                        part);
   int total = kblocks * r * r;
-  k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(nchunk, total, part, gram);
+  k_gram_reduce<<<(total + 7) / 8, 256, 0, st>>>(nchunk, total, part, gram);
 }
 
 // ------------------------------------------------------------ block combine
@@ -600,7 +656,8 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
   template void launch_dense_apply<T>(int, const T*, const T*, T*, int, cudaStream_t);               \
   template void launch_jacobi_F<T>(const mhde_ctx*, const T*, const T*, T, const T*, const T*, T*,   \
                                    cudaStream_t);                                                    \
-  template void launch_precond_p<T>(int, int, const T*, const T*, const T*, T, T, T*, cudaStream_t); \
+  template void launch_precond_p<T>(int, int, const T*, const T*, const T*, T, T, const int*, const int*,  \
+                                    const T*, T*, cudaStream_t);                                        \
   template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, cudaStream_t); \
   template void launch_gram<T>(const T*, size_t, int, const T*, int, int, int, int, double*, double*, \
                                cudaStream_t);                                                        \

@@ -17,6 +17,7 @@ namespace mhde {
 constexpr int NQ = 7;        // quadrature points per triangle (degree-5 rule)
 constexpr int NLOC = 6;      // P2 nodes per triangle
 constexpr int MAX_J = 64;    // members per ensemble handled by the small dense kernels
+constexpr int KIN_MAX = 16;  // longest inner GMRES on F
 
 // ----------------------------------------------------------------- host FE data
 struct HostCsr {
@@ -69,8 +70,12 @@ struct FeHost {
   std::vector<int> node_ptr;              // [n2 + 1]
   std::vector<int> node_slot;             // [nt*6]
 
-  // pressure Laplacian (P1 stiffness, node 0 pinned) and lumped pressure mass
+  // pressure Laplacian (P1 stiffness, node 0 pinned) and lumped pressure mass;
+  // the element -> nnz map of its P1 pattern (slots e*9 + 3i + k) also
+  // assembles the pressure convection matrix of the PCD Schur approximation
   HostCsr Kp;
+  std::vector<int> p1_gather_ptr;         // [nnzKp + 1]
+  std::vector<int> p1_gather_slot;        // [nt*9]
   std::vector<double> mp_lumped;          // [np]
   AmgHost amg;
 };
@@ -135,6 +140,7 @@ struct Sub {                       // one subproblem (v: which = 0, w: which = 1
   double* Bv = nullptr;            // right-hand sides [n_rows][Jp]
   double* X = nullptr;             // next state [n_rows][Jp]
   double* S = nullptr;             // current state [n_rows][Jp]
+  double* Sprev = nullptr;         // previous state (initial-guess extrapolation)
   double* Res = nullptr;           // FP64 residual [n_rows][Jp]
   void* basis = nullptr;           // (m+1) blocks [n_rows][Jp] in the Krylov precision
   void* Wk = nullptr;              // work blocks of the Krylov precision
@@ -153,6 +159,15 @@ struct Sub {                       // one subproblem (v: which = 0, w: which = 1
   double* hbuf = nullptr;          // pinned host mirror of gram [m+1][J][J]
   double* hcol = nullptr;          // pinned host column norms [nchunk][Jp]
   std::vector<DevAmgLevel> amg;    // per-subproblem AMG work vectors (shared operators)
+  double* Np = nullptr;            // pressure convection matrix values (P1 pattern) [nnzKp]
+  float* Npf = nullptr;
+  void* ibasis = nullptr;          // inner GMRES basis (kin+1) x [n2][2 Jp] (Krylov precision)
+  double* ipart = nullptr;         // inner dot partial sums [nchunk][kin+2][2 Jp]
+  double* idot = nullptr;          // reduced inner dots [kin+2][2 Jp]
+  double* ih = nullptr;            // inner Hessenberg [kin+1][kin][2 Jp]
+  double* ibeta = nullptr;         // [2 Jp] initial norms, then [2 Jp] inverse norms
+  double* iy = nullptr;            // inner least-squares solutions [kin][2 Jp]
+  void* zbasis = nullptr;          // flexible GMRES: preconditioned basis m x [n_rows][Jp]
   // captured preconditioner graphs keyed by (input, output) device pointers
   std::map<std::pair<const void*, const void*>, std::pair<cudaGraphExec_t, long long>> prec_graphs;
   // stats
@@ -175,6 +190,7 @@ struct mhde_ctx {
   std::vector<double> c_cross, c_same;   // (nu_j - nu_m,j), (nu'_j + nu'_m,j)
   std::string err;
   bool bound = false, have_initial = false;
+  bool have_prev = false;              // Sprev holds the state of the previous step
   long long steps = 0;
   mhde_stats stats{};
   int nchunk = 0;
@@ -202,6 +218,8 @@ struct mhde_ctx {
   int* d_bslot = nullptr;
   mhde::DevCsr BT;                     // n2 x np, values as pairs
   int* d_btsrc = nullptr;
+  int* d_p1slot_ptr = nullptr;
+  int* d_p1slot = nullptr;
   int* d_node_ptr = nullptr;
   int* d_node_slot = nullptr;
   double* d_mp = nullptr;              // lumped pressure mass [np]

@@ -40,6 +40,7 @@ template <> struct Prec<double> {
   static double* b(DevAmgLevel& L) { return L.b; }
   static double* r(DevAmgLevel& L) { return L.r; }
   static const double* cinv(const mhde_ctx* c) { return c->d_coarse_inv; }
+  static const double* Np(const Sub& s) { return s.Np; }
   static constexpr double thresh = 1e-22;
 };
 template <> struct Prec<float> {
@@ -54,6 +55,7 @@ template <> struct Prec<float> {
   static float* b(DevAmgLevel& L) { return L.bf; }
   static float* r(DevAmgLevel& L) { return L.rf; }
   static const float* cinv(const mhde_ctx* c) { return c->d_coarse_invf; }
+  static const float* Np(const Sub& s) { return s.Npf; }
   static constexpr double thresh = 1e-9;
 };
 
@@ -112,8 +114,14 @@ static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out) {
   T* x0 = Prec<T>::x(s.amg[0]);
   vcycle<T>(c, s, 0, rp, x0);
   const double nu_hat = 0.5 * (c->nubar + c->nubar_m);
-  launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), (T)(1.0 / c->dt), (T)nu_hat, out + poff, st);
+  const DevCsr& Kp = c->amg_ops[0].A;
+  launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), (T)(1.0 / c->dt), (T)nu_hat, Kp.rowptr, Kp.col,
+                      c->opt.schur == 1 ? Prec<T>::Np(s) : (const T*)nullptr, out + poff, st);
   launch_bt_apply<T>(c, Prec<T>::BT(c), in, out + poff, tk, st);
+  if (c->opt.inner_iters > 0) {
+    launch_inner_gmres<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), tk, out, st);
+    return;
+  }
   const int nsw = std::max(1, c->opt.jacobi_sweeps);
   const T om = (T)c->opt.jacobi_omega;
   T* cur = out;
@@ -250,10 +258,12 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   ls.init(r, J, m, S0.data());
   std::vector<double> G, H, Y, Hsum;
   int k = 0;
+  T* Zb = (T*)s.zbasis;
   for (; k < m && used < maxit; ++k) {
     T* Vk = Vb + (size_t)k * vs;
-    apply_prec<T>(c, s, Vk, Zk);
-    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk, nullptr, Wk, 0, st);
+    T* Zk_ = Zb + (size_t)k * vs;                 // flexible GMRES keeps every preconditioned block
+    apply_prec<T>(c, s, Vk, Zk_);
+    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk_, nullptr, Wk, 0, st);
     // block classical Gram-Schmidt, twice
     Hsum.assign((size_t)(k + 1) * r * r, 0.0);
     for (int pass = 0; pass < 2; ++pass) {
@@ -295,8 +305,7 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   }
   ls.solve(Y);
   T* dc = upload_coef<T>(c, s, Y, 3);
-  launch_block_combine<T>(Wk, nullptr, T(0), Vb, vs, k, r, dc, J, c->n_rows, Jp, st);
-  apply_prec<T>(c, s, Wk, D);
+  launch_block_combine<T>(D, nullptr, T(0), Zb, vs, k, r, dc, J, c->n_rows, Jp, st);
   return MHDE_OK;
 }
 
@@ -311,6 +320,7 @@ int assemble_sub(mhde_ctx* c, int which) {
   launch_F_local(c->fe.nt, c->d_dofs, c->d_geom, mean_conv, l2, 2.0 * c->opt.mu * c->dt,
                  c->opt.conv_form, s.Floc, st);
   launch_F_gather(c, s.Floc, 1.0 / c->dt, nu_hat, s.Fval, s.Fvalf, s.Fdinv, s.Fdinvf, st);
+  if (c->opt.schur == 1) launch_Np(c, mean_conv, s.Floc, s.Np, s.Npf, st);   // slots reuse Floc
   launch_rhs_conv_local(c->fe.nt, c->J, c->Jp, c->d_dofs, c->d_geom, s.S, o.S, mean_conv,
                         c->opt.conv_form, s.Cloc, st);
   launch_rhs_assemble(c, s.S, o.S, c->have_forcing ? (which == 0 ? c->d_F1 : c->d_F2) : nullptr,
@@ -326,7 +336,11 @@ static int solve_sub_t(mhde_ctx* c, int which) {
   const int J = c->J;
   const size_t vs = (size_t)c->n_rows * c->Jp;
   int rc;
-  SCU(cudaMemcpyAsync(s.X, s.S, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // initial guess: linear extrapolation in time of the last two states
+  if (c->have_prev)
+    launch_axpby<double>(s.X, 2.0, s.S, -1.0, s.Sprev, vs, st);
+  else
+    SCU(cudaMemcpyAsync(s.X, s.S, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   std::vector<double> bn, G, Gs, Tm, Sm, C0;
   if ((rc = col_norms<double>(c, s, s.Bv, bn))) return rc;
   s.iters = 0;

@@ -160,7 +160,9 @@ def test_single_member_and_standard_form():
 
 @pytest.mark.parametrize("precision", [PREC_FP64, PREC_MIXED])
 def test_patch_solution_exact_on_gpu(precision):
-    ens, vf, wf = patch_ensemble(channel_step(cells_per_unit=1))
+    # dt = 0.02 keeps the cell CFL number of the w-problem (convected by
+    # <v> = (1+t)(y, x), |<v>| up to 44 on this channel) below about 1
+    ens, vf, wf = patch_ensemble(channel_step(cells_per_unit=1), dt=0.02)
     sol = gpu_run(ens, ens.nsteps, precision=precision)
     xy, _ = sol.p2_nodes()
     v, w, _, _ = sol.read_state()
@@ -212,3 +214,18 @@ def test_iteration_cap_reports_noconv_and_keeps_state():
     assert e.value.code == -3
     assert np.array_equal(sol.read_state()[0], before)
     sol.close()
+
+
+@pytest.mark.parametrize("n_rows,ld,r,k", [(1000, 4, 3, 1), (148739, 20, 20, 5), (5003, 64, 61, 3)])
+def test_block_gram_entry_point(n_rows, ld, r, k):
+    """mhde_block_gram against the FP64 definition V_i^T W (numpy)."""
+    import paper_2108_05110_gb300 as P
+    rng = np.random.default_rng(n_rows)
+    V = rng.standard_normal((k, n_rows, ld))
+    W = rng.standard_normal((n_rows, ld))
+    G = P.block_gram(torch.from_numpy(V).cuda(), torch.from_numpy(W).cuda(), k, r).cpu().numpy()
+    torch.cuda.synchronize()
+    for i in range(k):
+        ref = V[i][:, :r].T @ W[:, :r]
+        scale = np.abs(V[i][:, :r]).T @ np.abs(W[:, :r])
+        assert np.all(np.abs(G[i] - ref) <= 1e-13 * scale)
