@@ -242,6 +242,24 @@ int mhde_block_gram_scratch_bytes(int n_rows, int r, int kblocks, size_t* bytes)
 int mhde_block_gram(const double* V, size_t v_stride, int kblocks, const double* W, int n_rows, int ld,
                     int r, double* G, void* scratch, size_t scratch_bytes, void* stream);
 
+/* Allocation-free variant of mhde_block_gram, for callers that must not
+ * allocate device memory (hosts that own the whole device through their own
+ * pool, latency-critical loops that cannot afford cudaMalloc).  The paper has
+ * no counterpart: this is a property of the library, not of the method.
+ * Same arguments and result as mhde_block_gram without the scratch buffer:
+ * the partial sums live in one fixed 2 MiB __device__ array that every GPU
+ * loading the library holds until the process exits.  Sizes whose partials
+ * for one row chunk exceed it (kblocks * r * r > 262144) are rejected with
+ * MHDE_EWORKSPACE; larger n_rows are handled with fewer, longer chunks.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array, so calls that overlap on the GPU (different streams
+ * without ordering) race; order them on one stream.  Every call rewrites the
+ * partials it uses, so no clearing is needed.  Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine. */
+int mhde_block_gram_noalloc(const double* V, size_t v_stride, int kblocks, const double* W, int n_rows,
+                            int ld, int r, double* G, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,7 @@ SIGNATURES = {
     "mhde_block_gram_scratch_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "mhde_block_gram": (C.c_int, [_P, C.c_size_t, C.c_int, _P, C.c_int, C.c_int, C.c_int, _P, _P,
                                   C.c_size_t, _P]),
+    "mhde_block_gram_noalloc": (C.c_int, [_P, C.c_size_t, C.c_int, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
 }
 
 
@@ -171,6 +172,24 @@ def block_gram(V, W, kblocks, r, stream=None):
                              C.c_void_p(st.cuda_stream))
     if rc != 0:
         raise MhdeError(rc, "mhde_block_gram")
+    return G
+
+
+def block_gram_noalloc(V, W, kblocks, r, G=None, stream=None):
+    """G_i = V_i^T W through mhde_block_gram_noalloc, which uses the library's
+    fixed device scratch instead of allocating.  V: torch float64 CUDA
+    tensor [kblocks, n_rows, ld], W: [n_rows, ld]; G: optional output
+    [kblocks, r, r] (the caller's memory)."""
+    import torch
+    lib = load_library()
+    k, n_rows, ld = V.shape
+    if G is None:
+        G = torch.empty((kblocks, r, r), dtype=torch.float64, device=V.device)
+    st = stream if stream is not None else torch.cuda.current_stream(V.device)
+    rc = lib.mhde_block_gram_noalloc(C.c_void_p(V.data_ptr()), n_rows * ld, kblocks, C.c_void_p(W.data_ptr()),
+                                     n_rows, ld, r, C.c_void_p(G.data_ptr()), C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise MhdeError(rc, "mhde_block_gram_noalloc")
     return G
 
 
