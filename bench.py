@@ -37,6 +37,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-only", action="store_true",
+                   help="run W warm-up and K timed steps and exit (for ncu captures)")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--N", type=int, default=WORKLOAD["N"])
     p.add_argument("--J", type=int, default=WORKLOAD["J"])
@@ -146,6 +148,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# --------------------------------------------------------------------------- multi-rank aggregation
+def max_over_ranks(value, world, device=None):
+    """Maximum of a per-rank scalar over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 # --------------------------------------------------------------------------- reference arm
 def reference_arm(args, rank, world):
     if rank != 0:
@@ -193,7 +212,7 @@ def our_arm(args, rank, world, local_rank):
     from workloads.ensembles import lid_cavity
 
     cpu_secs = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_only:
         cpu_secs = run_cpu_sample_subprocess(args)      # before any GPU work in this process
 
     torch.cuda.set_device(local_rank)
@@ -204,6 +223,16 @@ def our_arm(args, rank, world, local_rank):
     ensemble_io.feed_initial(sol, ens)
     ensemble_io.feed_step_data(sol, ens, ens.dt)     # constant lid / field data
     sol.advance(args.warmup)
+    if args.profile_only:
+        torch.cuda.synchronize()
+        sol.advance(args.steps)
+        torch.cuda.synchronize()
+        st = sol.stats()
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "steps": args.steps, "launches": int(st.launches),
+                              "iters": int(st.total_iters)}), flush=True)
+        sol.close()
+        return
 
     def barrier():
         if world > 1:
@@ -226,11 +255,8 @@ def our_arm(args, rank, world, local_rank):
     clock_info = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     st1 = sol.stats()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local_rank}")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = ens.J * args.steps * world / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms, world, device=f"cuda:{local_rank}")
+    value = whole_job_rate(ens.J * args.steps, world, ms_max / 1000.0)
     launches = int(st1.launches - st0.launches)
     iters = int(st1.total_iters - st0.total_iters)
 
@@ -267,10 +293,8 @@ def our_arm(args, rank, world, local_rank):
         um, Bm = sol.read_mean()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local_rank}")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = ens.J * args.steps * world / float(e2e_t.item())
+    e2e_value = whole_job_rate(ens.J * args.steps, world,
+                               max_over_ranks(e2e_s, world, device=f"cuda:{local_rank}"))
     h2d = (u0.nbytes + B0.nbytes + ub.nbytes + Bb.nbytes) / args.steps
     d2h = um.nbytes + Bm.nbytes
     sol.close()

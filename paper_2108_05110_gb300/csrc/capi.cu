@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <thread>
 
@@ -159,7 +160,7 @@ size_t layout(mhde_ctx* c, char* base) {
       const int kin = std::max(1, c->opt.inner_iters);
       const size_t C2 = 2 * Jp;
       s.ibasis = w.take<char>((size_t)(kin + 1) * n2 * C2 * ks);
-      s.ipart = w.take<double>((size_t)c->nchunk * (KIN_MAX + 2) * C2);
+      s.ipart = w.take<double>((size_t)c->nchunk_in * (KIN_MAX + 2) * C2);
       s.idot = w.take<double>((size_t)(kin + 2) * C2);
       s.ih = w.take<double>((size_t)(kin + 1) * kin * C2);
       s.ibeta = w.take<double>(2 * C2);
@@ -288,6 +289,7 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
     return MHDE_ESTAB;
   }
   c->nchunk = std::max(1, std::min(304, (c->n_rows + 255) / 256));
+  c->nchunk_in = std::max(1, std::min(1024, (c->fe.n2 + 127) / 128));
   const char* tr = std::getenv("MHDE_TRACE");
   c->trace = tr && tr[0] == '1';
   const char* gr = std::getenv("MHDE_GRAPHS");
@@ -555,6 +557,17 @@ int mhde_step(mhde_ctx* c) {
   c->stats.launches += launch_count() - launches0;
   c->stats.last_step_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (c->trace) {
+    for (int which = 0; which < 2; ++which) {
+      Sub& s = c->sub[which];
+      std::fprintf(stderr,
+                   "[mhde] step %lld sub %d ms: assemble %.2f residual %.2f precond %.2f spmm %.2f cgs %.2f "
+                   "normalise %.2f | graphs built %d\n",
+                   c->steps, which, s.phase_ms[0], s.phase_ms[1], s.phase_ms[2], s.phase_ms[3], s.phase_ms[4],
+                   s.phase_ms[5], s.graphs_built);
+      for (double& v : s.phase_ms) v = 0.0;
+    }
+  }
   return MHDE_OK;
 }
 
@@ -813,7 +826,7 @@ int mhde_probe_spmm(mhde_ctx* c, int which, int precision, const double* X, doub
   CU(cudaStreamSynchronize(c->sv));
   CU(cudaMemcpy(dx, buf.data(), vs * sizeof(double), cudaMemcpyHostToDevice));
   if (precision == 0) {
-    launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, dx, nullptr, dy, 0, c->sv);
+    launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, dx, nullptr, dy, 0, c->Jp, c->sv);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(c->sv));
     CU(cudaMemcpy(buf.data(), dy, vs * sizeof(double), cudaMemcpyDeviceToHost));
@@ -824,7 +837,7 @@ int mhde_probe_spmm(mhde_ctx* c, int which, int precision, const double* X, doub
       // FP64 Krylov buffers are twice as large: reuse them as float storage
     }
     launch_d2f(dx, fx, vs, c->sv);
-    launch_saddle_spmm<float>(c, s.Fvalf, c->B.valf, c->BT.valf, fx, nullptr, fy, 0, c->sv);
+    launch_saddle_spmm<float>(c, s.Fvalf, c->B.valf, c->BT.valf, fx, nullptr, fy, 0, c->Jp, c->sv);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(c->sv));
     std::vector<float> fb(vs);
@@ -869,11 +882,11 @@ int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
   auto once = [&]() {
     switch (kernel) {
       case 0:
-        launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, xd, nullptr, yd, 0, st);
+        launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, xd, nullptr, yd, 0, c->Jp, st);
         break;
       case 1:
         launch_saddle_spmm<float>(c, s.Fvalf, c->B.valf, c->BT.valf, (const float*)s.Wk, nullptr,
-                                  (float*)s.Zk, 0, st);
+                                  (float*)s.Zk, 0, c->Jp, st);
         break;
       case 2: {
         const double* mean_conv = which == 0 ? c->d_mean_w : c->d_mean_v;

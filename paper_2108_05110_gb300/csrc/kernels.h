@@ -47,9 +47,10 @@ void launch_rhs_assemble(const mhde_ctx* c, const double* S_self, const double* 
 
 // ---- linear algebra kernels (T = double or float) -------------------------
 // Y = A X (mode 0) or Y = Bvec - A X (mode 1) for the saddle matrix.
+// (ld = row stride of X, Y and Bvec, a multiple of 4)
 template <typename T>
 void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T* BTval, const T* X,
-                        const double* Bvec, T* Y, int mode, cudaStream_t st);
+                        const double* Bvec, T* Y, int mode, int ld, cudaStream_t st);
 // generic CSR: mode 0 y = A x; 1 y = b - A x; 2 y = x + omega dinv (b - A x);
 // 3 y = omega dinv b; 4 y += A x
 template <typename T>
@@ -60,7 +61,7 @@ void launch_dense_apply(int n, const T* Ainv, const T* x, T* y, int Jp, cudaStre
 // velocity rows: z = dinv r (first) or z_out = z_in + omega dinv (r - F z_in); identity rows copy r
 template <typename T>
 void launch_jacobi_F(const mhde_ctx* c, const T* Fval, const T* Fdinv, T omega, const T* r,
-                     const T* zin, T* zout, cudaStream_t st);
+                     const T* zin, T* zout, int ld, cudaStream_t st);
 // pressure part of the block preconditioner:
 //   zp = -(1/dt) x - nu_hat rp / mp, zp[0] = rp[0]
 //   (PCD adds - (N_p x) / mp when Np is not null; N_p has the P1 pattern rp/col)
@@ -69,20 +70,22 @@ void launch_precond_p(int np, int Jp, const T* x, const T* rp, const T* mp, T in
                       const int* nrp, const int* ncol, const T* Np, T* zp, cudaStream_t st);
 // tu = ru - B^T zp (velocity rows; Dirichlet rows keep ru)
 template <typename T>
-void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu,
+void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu, int ld,
                      cudaStream_t st);
 // Gram partial sums: part[chunk][i][p][q] = sum_rows V_i[row][p] W[row][q]
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
                  int nchunk, double* part, double* gram, cudaStream_t st);
 // out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q], q < r_out; 0 beyond
+// (V rows have stride ldv, in/out rows stride Jp)
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
-                          int r_in, const T* C, int r_out, int n_rows, int Jp, cudaStream_t st);
-// out[row][q] = (T) sum_p X[row][p] C[p][q], q < r (0 beyond); X, C (J x r) in FP64
+                          int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st);
+// out[row][q] = (T) sum_p X[row][p] C[p][q], q < r (0 beyond); X, C (J x r) in FP64;
+// X rows have stride Jp, out rows stride ldo
 template <typename T>
 void launch_combine_from_f64(T* out, const double* X, const double* C, int J, int r, int n_rows, int Jp,
-                             cudaStream_t st);
+                             int ldo, cudaStream_t st);
 // per-chunk column sums of squares (FP64)
 template <typename T>
 void launch_colsq(const T* X, int n_rows, int Jp, int nchunk, double* out, cudaStream_t st);
@@ -103,7 +106,7 @@ void launch_Np(const mhde_ctx* c, const double* mean_conv, double* slots, double
                cudaStream_t st);
 // inner per-column GMRES(k) on F (velocity block), z ~ F^{-1} r
 template <typename T>
-void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z,
+void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
                         cudaStream_t st);
 
 // solver entry points (solver.cu)

@@ -4,8 +4,9 @@
 // inside the captured preconditioner graph.  The velocity part of a saddle
 // multi-vector is [n2][C] with C = 2 J_pad columns (component, member).
 //
-// One inner iteration i:  w = F D^{-1} v_i;  two classical Gram-Schmidt
-// passes against v_0..v_i per column; v_{i+1} = w / ||w||.  After k steps
+// One inner iteration i:  w = F D^{-1} v_i;  one classical Gram-Schmidt
+// pass against v_0..v_i per column (norm from the Pythagorean identity);
+// v_{i+1} = w / ||w||.  After k steps
 // the per-column least-squares problems min || beta e_1 - H y || are solved
 // by Givens rotations and z = D^{-1} sum_l v_l y_l.
 #include <cmath>
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
 // shared-memory tree finishes the sums (deterministic).  mode 0: first
 // Gram-Schmidt pass, H[l][i] = h; mode 1: second pass, H[l][i] += h, norm
 // from the Pythagorean identity, H[i+1][i] = norm, inv[col] = 1/norm;
-// mode 2: initial norms beta[col], inv[col] = 1/beta.
+// mode 2: initial norms beta[col], inv[col] = 1/beta; mode 3: single pass,
+// H[l][i] = h and the norm as in mode 1.
 constexpr int RED_T = 128;
 
 __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl, int kin,
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
                                                       double* __restrict__ beta, double* __restrict__ inv) {
   __shared__ double sh[KIN_MAX + 2][RED_T];
   const int c = blockIdx.x;
-  const int nout = nl + (mode == 1 ? 1 : 0);
+  const int nout = nl + ((mode == 1 || mode == 3) ? 1 : 0);
   for (int l = 0; l < nout; ++l) {
     double s = 0.0;
     for (int ch = threadIdx.x; ch < nchunk; ch += RED_T) s += part[((size_t)ch * (KIN_MAX + 2) + l) * C + c];
@@ -122,10 +124,10 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
     const double s = sh[l][0];
     dots[(size_t)l * C + c] = s;
     ss += s * s;
-    if (mode == 0) H[((size_t)l * kin + i) * C + c] = s;
+    if (mode == 0 || mode == 3) H[((size_t)l * kin + i) * C + c] = s;
     if (mode == 1) H[((size_t)l * kin + i) * C + c] += s;
   }
-  if (mode == 1) {
+  if (mode == 1 || mode == 3) {
     const double n2v = sh[nl][0] - ss;
     const double nrm = n2v > 0.0 ? sqrt(n2v) : 0.0;
     H[((size_t)(i + 1) * kin + i) * C + c] = nrm;
@@ -197,18 +199,18 @@ __global__ void k_col_final(int n_rows, int C, int kin, const T* __restrict__ V,
 }
 
 template <typename T>
-void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z,
+void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
                         cudaStream_t st) {
-  const int n2 = c->fe.n2, C = 2 * c->Jp, kin = c->opt.inner_iters;
+  const int n2 = c->fe.n2, C = 2 * ld, kin = c->opt.inner_iters;
   const int nch = C / IVec<T>::W;
   const size_t vstride = (size_t)n2 * C;
-  const int nchunk = c->nchunk;
+  const int nchunk = c->nchunk_in;
   const int rows_per_chunk = (n2 + nchunk - 1) / nchunk;
   const int threads = (256 / C) * C;
   const size_t shm = (size_t)threads * sizeof(double);
   T* Vb = (T*)s.ibasis;
   const long long nel = (long long)n2 * C;
-  count_launch(3 + 7 * kin + 2);
+  count_launch(3 + 4 * kin + 2);
   // beta = ||r||, v_0 = r / beta
   k_col_dots<T><<<nchunk, threads, shm, st>>>(n2, C, 1, r, 0, r, rows_per_chunk, 0, s.ipart);
   k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, 1, kin, s.ipart, s.idot, 2, 0, s.ih, s.ibeta,
@@ -218,13 +220,11 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* d
     T* vi = Vb + (size_t)i * vstride;
     T* w = Vb + (size_t)(i + 1) * vstride;
     k_fd_spmm<T><<<nb((long long)n2 * nch, 256), 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, vi, w);
-    k_col_dots<T><<<nchunk, threads, shm, st>>>(n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 0, s.ipart);
-    k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, i + 1, kin, s.ipart, s.idot, 0, i, s.ih, s.ibeta,
-                                           s.ibeta + C);
-    k_col_update<T><<<nb(nel, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, s.idot, w, w, nullptr);
+    // one classical Gram-Schmidt pass: dots against v_0..v_i and ||w||^2 in a
+    // single sweep; the projected norm follows from the Pythagorean identity
     k_col_dots<T><<<nchunk, threads, shm, st>>>(n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 1, s.ipart);
-    k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, i + 1, kin, s.ipart, s.idot, 1, i, s.ih, s.ibeta,
-                                           s.ibeta + C);
+    k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, i + 1, kin, s.ipart, s.idot, 3, i, s.ih, s.ibeta,
+                                      s.ibeta + C);
     k_col_update<T><<<nb(nel, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, s.idot, w, w, s.ibeta + C);
   }
   k_col_lsq<<<nb(C, 64), 64, 0, st>>>(C, kin, s.ih, s.ibeta, s.iy);
@@ -232,8 +232,8 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* d
 }
 
 template void launch_inner_gmres<double>(const mhde_ctx*, const Sub&, const double*, const double*,
-                                         const double*, double*, cudaStream_t);
+                                         const double*, double*, int, cudaStream_t);
 template void launch_inner_gmres<float>(const mhde_ctx*, const Sub&, const float*, const float*, const float*,
-                                        float*, cudaStream_t);
+                                        float*, int, cudaStream_t);
 
 }  // namespace mhde

@@ -140,9 +140,9 @@ __global__ void __launch_bounds__(256) k_saddle(int n2, int np, int nch, const i
 
 template <typename T>
 void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T* BTval, const T* X,
-                        const double* Bvec, T* Y, int mode, cudaStream_t st) {
+                        const double* Bvec, T* Y, int mode, int ld, cudaStream_t st) {
   count_launch();
-  int nch = c->Jp / Vec<T>::W;
+  int nch = ld / Vec<T>::W;
   long long n = ((long long)c->fe.n2 + c->fe.np) * nch;
   if (mode == 0)
     k_saddle<T, 0><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
@@ -247,9 +247,9 @@ __global__ void k_jacobi_F(int n2, int nch, const int* __restrict__ rp, const in
 
 template <typename T>
 void launch_jacobi_F(const mhde_ctx* c, const T* Fval, const T* Fdinv, T omega, const T* r,
-                     const T* zin, T* zout, cudaStream_t st) {
+                     const T* zin, T* zout, int ld, cudaStream_t st) {
   count_launch();
-  int nch = c->Jp / Vec<T>::W;
+  int nch = ld / Vec<T>::W;
   long long n = (long long)c->fe.n2 * 2 * nch;
   k_jacobi_F<T><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, nch, c->F.rowptr, c->F.col, Fval, Fdinv,
                                              c->d_isbnd, omega, r, zin, zout);
@@ -312,10 +312,10 @@ __global__ void k_bt_apply(int n2, int nch, const int* __restrict__ rp, const in
 }
 
 template <typename T>
-void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu,
+void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu, int ld,
                      cudaStream_t st) {
   count_launch();
-  int nch = c->Jp / Vec<T>::W;
+  int nch = ld / Vec<T>::W;
   long long n = (long long)c->fe.n2 * 2 * nch;
   k_bt_apply<T><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, nch, c->BT.rowptr, c->BT.col, BTval, c->d_isbnd,
                                              ru, zp, tu);
@@ -445,7 +445,7 @@ template <typename T, int QMAX>
 __global__ void __launch_bounds__(128) k_block_combine(T* __restrict__ out, const T* __restrict__ in, T alpha,
                                                        const T* __restrict__ V, size_t vstride, int kblocks,
                                                        int r_in, const T* __restrict__ C, int r_out,
-                                                       int n_rows, int Jp, int kgroup) {
+                                                       int n_rows, int ldv, int Jp, int kgroup) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Cs = reinterpret_cast<T*>(smem_raw);           // [kgroup * r_in][QMAX]
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(128) k_block_combine(T* __restrict__ out, cons
     __syncthreads();
     if (row < n_rows) {
       for (int ib = 0; ib < nb; ++ib) {
-        const T* vr = V + (size_t)(i0 + ib) * vstride + (size_t)row * Jp;
+        const T* vr = V + (size_t)(i0 + ib) * vstride + (size_t)row * ldv;
         const T* cb = Cs + (size_t)ib * r_in * QMAX;
         for (int p = 0; p < r_in; ++p) {
           const T v = vr[p];
@@ -485,33 +485,33 @@ __global__ void __launch_bounds__(128) k_block_combine(T* __restrict__ out, cons
 
 template <typename T, int QMAX>
 static void combine_q(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
-                      const T* C, int r_out, int n_rows, int Jp, cudaStream_t st) {
+                      const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st) {
   const size_t per_block = (size_t)r_in * QMAX * sizeof(T);
   int kgroup = (int)std::max<size_t>(1, (48 * 1024) / std::max<size_t>(per_block, 1));
   kgroup = std::min(kgroup, std::max(kblocks, 1));
   size_t shmem = (size_t)kgroup * per_block;
   k_block_combine<T, QMAX><<<nblk(n_rows, 128), 128, shmem, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C,
-                                                                  r_out, n_rows, Jp, kgroup);
+                                                                  r_out, n_rows, ldv, Jp, kgroup);
 }
 
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
-                          int r_in, const T* C, int r_out, int n_rows, int Jp, cudaStream_t st) {
+                          int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st) {
   count_launch();
   if (r_out <= 4)
-    combine_q<T, 4>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+    combine_q<T, 4>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
   else if (r_out <= 8)
-    combine_q<T, 8>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+    combine_q<T, 8>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
   else if (r_out <= 16)
-    combine_q<T, 16>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+    combine_q<T, 16>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
   else if (r_out <= 24)
-    combine_q<T, 24>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+    combine_q<T, 24>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
   else if (r_out <= 32)
-    combine_q<T, 32>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+    combine_q<T, 32>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
   else if (r_out <= 48)
-    combine_q<T, 48>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+    combine_q<T, 48>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
   else
-    combine_q<T, 64>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, Jp, st);
+    combine_q<T, 64>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
 }
 
 // out[row][q] = (T) sum_p X[row][p] C[p][q] for q < r (0 beyond), X and C in FP64:
@@ -519,7 +519,7 @@ void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstri
 template <typename T, int QMAX>
 __global__ void __launch_bounds__(128) k_combine_from_f64(T* __restrict__ out, const double* __restrict__ X,
                                                           const double* __restrict__ C, int J, int r,
-                                                          int n_rows, int Jp) {
+                                                          int n_rows, int Jp, int ldo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* Cs = reinterpret_cast<double*>(smem_raw);   // [J][QMAX]
   for (int e = threadIdx.x; e < J * QMAX; e += blockDim.x) {
@@ -538,20 +538,20 @@ __global__ void __launch_bounds__(128) k_combine_from_f64(T* __restrict__ out, c
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) acc[q] += v * Cs[p * QMAX + q];
   }
-  T* orow = out + (size_t)row * Jp;
+  T* orow = out + (size_t)row * ldo;
 #pragma unroll
   for (int q = 0; q < QMAX; ++q)
-    if (q < Jp) orow[q] = q < r ? (T)acc[q] : T(0);
-  for (int q = QMAX; q < Jp; ++q) orow[q] = T(0);
+    if (q < ldo) orow[q] = q < r ? (T)acc[q] : T(0);
+  for (int q = QMAX; q < ldo; ++q) orow[q] = T(0);
 }
 
 template <typename T>
 void launch_combine_from_f64(T* out, const double* X, const double* C, int J, int r, int n_rows, int Jp,
-                             cudaStream_t st) {
+                             int ldo, cudaStream_t st) {
   count_launch();
 #define MHDE_CF(Q)                                                                                     \
   k_combine_from_f64<T, Q><<<nblk(n_rows, 128), 128, (size_t)J * Q * sizeof(double), st>>>(out, X, C, J, r, \
-                                                                                           n_rows, Jp)
+                                                                                           n_rows, Jp, ldo)
   if (r <= 8)
     MHDE_CF(8);
   else if (r <= 16)
@@ -650,25 +650,25 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
 // explicit instantiations
 #define MHDE_INST(T)                                                                                 \
   template void launch_saddle_spmm<T>(const mhde_ctx*, const T*, const T*, const T*, const T*,       \
-                                      const double*, T*, int, cudaStream_t);                         \
+                                      const double*, T*, int, int, cudaStream_t);                    \
   template void launch_csr<T>(int, const int*, const int*, const T*, const T*, T, const T*, const T*, \
                               T*, int, int, cudaStream_t);                                           \
   template void launch_dense_apply<T>(int, const T*, const T*, T*, int, cudaStream_t);               \
   template void launch_jacobi_F<T>(const mhde_ctx*, const T*, const T*, T, const T*, const T*, T*,   \
-                                   cudaStream_t);                                                    \
+                                   int, cudaStream_t);                                               \
   template void launch_precond_p<T>(int, int, const T*, const T*, const T*, T, T, const int*, const int*,  \
                                     const T*, T*, cudaStream_t);                                        \
-  template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, cudaStream_t); \
+  template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, int, cudaStream_t); \
   template void launch_gram<T>(const T*, size_t, int, const T*, int, int, int, int, double*, double*, \
                                cudaStream_t);                                                        \
   template void launch_block_combine<T>(T*, const T*, T, const T*, size_t, int, int, const T*, int,  \
-                                        int, int, cudaStream_t);                                     \
+                                        int, int, int, cudaStream_t);                                \
   template void launch_colsq<T>(const T*, int, int, int, double*, cudaStream_t);                     \
   template void launch_scale_to<T>(const double*, const double*, T*, size_t, int, cudaStream_t);     \
   template void launch_axpy_from<T>(const T*, const double*, double*, size_t, int, cudaStream_t);     \
   template void launch_axpby<T>(T*, T, const T*, T, const T*, size_t, cudaStream_t);               \
   template void launch_combine_from_f64<T>(T*, const double*, const double*, int, int, int, int,     \
-                                           cudaStream_t);
+                                           int, cudaStream_t);
 MHDE_INST(double)
 MHDE_INST(float)
 

@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <map>
+#include <tuple>
 #include <utility>
 #include <string>
 #include <vector>
@@ -169,9 +170,11 @@ struct Sub {                       // one subproblem (v: which = 0, w: which = 1
   double* iy = nullptr;            // inner least-squares solutions [kin][2 Jp]
   void* zbasis = nullptr;          // flexible GMRES: preconditioned basis m x [n_rows][Jp]
   // captured preconditioner graphs keyed by (input, output) device pointers
-  std::map<std::pair<const void*, const void*>, std::pair<cudaGraphExec_t, long long>> prec_graphs;
+  std::map<std::tuple<const void*, const void*, int>, std::pair<cudaGraphExec_t, long long>> prec_graphs;
   // stats
   int iters = 0, refine = 0;
+  int graphs_built = 0;
+  double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // MHDE_TRACE: assemble, residual, precond, spmm, cgs, normalise
   double relres = 0.0;
   int status = 0;
   std::string err;
@@ -194,6 +197,7 @@ struct mhde_ctx {
   long long steps = 0;
   mhde_stats stats{};
   int nchunk = 0;
+  int nchunk_in = 0;                   // row chunks of the inner (velocity-block) dot products
   int amg_levels = 0;
 
   // device workspace

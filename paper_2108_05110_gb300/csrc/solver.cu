@@ -11,6 +11,7 @@
 // M_p the lumped pressure mass.
 #include <algorithm>
 #include <cmath>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 
@@ -26,6 +27,25 @@ namespace mhde {
       return MHDE_ECUDA;                                                 \
     }                                                                    \
   } while (0)
+
+// Phase timing for MHDE_TRACE=1 runs: synchronizes the stream at phase
+// boundaries (diagnostics only; off by default).
+struct PhaseClock {
+  const mhde_ctx* c;
+  Sub& s;
+  std::chrono::steady_clock::time_point t0;
+  PhaseClock(const mhde_ctx* c_, Sub& s_) : c(c_), s(s_) {
+    if (c->trace) {
+      cudaStreamSynchronize(s.stream);
+      t0 = std::chrono::steady_clock::now();
+    }
+  }
+  void stop(int phase) {
+    if (!c->trace) return;
+    cudaStreamSynchronize(s.stream);
+    s.phase_ms[phase] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
 
 template <typename T> struct Prec;
 template <> struct Prec<double> {
@@ -61,9 +81,8 @@ template <> struct Prec<float> {
 
 // ------------------------------------------------------------------ preconditioner
 template <typename T>
-static void vcycle(const mhde_ctx* c, Sub& s, int l, const T* b, T* x) {
+static void vcycle(const mhde_ctx* c, Sub& s, int l, const T* b, T* x, int Jp) {
   const int L = (int)c->amg_ops.size();
-  const int Jp = c->Jp;
   cudaStream_t st = s.stream;
   if (l == L - 1) {
     launch_dense_apply<T>(c->fe.amg.nc, Prec<T>::cinv(c), b, x, Jp, st);
@@ -90,7 +109,7 @@ static void vcycle(const mhde_ctx* c, Sub& s, int l, const T* b, T* x) {
   const DevCsr& R = op.R;
   launch_csr<T>(R.nrows, R.rowptr, R.col, Prec<T>::Aval(R), nullptr, T(0), other, nullptr,
                 Prec<T>::b(wn), 0, Jp, st);
-  vcycle<T>(c, s, l + 1, Prec<T>::b(wn), Prec<T>::x(wn));
+  vcycle<T>(c, s, l + 1, Prec<T>::b(wn), Prec<T>::x(wn), Jp);
   const DevCsr& P = op.P;
   launch_csr<T>(P.nrows, P.rowptr, P.col, Prec<T>::Aval(P), nullptr, T(0), Prec<T>::x(wn), nullptr, cur, 4,
                 Jp, st);
@@ -104,31 +123,30 @@ static void vcycle(const mhde_ctx* c, Sub& s, int l, const T* b, T* x) {
 }
 
 template <typename T>
-static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out) {
-  const int Jp = c->Jp;
+static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out, int Jp) {
   const size_t poff = (size_t)2 * c->fe.n2 * Jp;
   cudaStream_t st = s.stream;
   T* tk = (T*)s.Tk;
   T* pk = (T*)s.Pk;
   const T* rp = in + poff;
   T* x0 = Prec<T>::x(s.amg[0]);
-  vcycle<T>(c, s, 0, rp, x0);
+  vcycle<T>(c, s, 0, rp, x0, Jp);
   const double nu_hat = 0.5 * (c->nubar + c->nubar_m);
   const DevCsr& Kp = c->amg_ops[0].A;
   launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), (T)(1.0 / c->dt), (T)nu_hat, Kp.rowptr, Kp.col,
                       c->opt.schur == 1 ? Prec<T>::Np(s) : (const T*)nullptr, out + poff, st);
-  launch_bt_apply<T>(c, Prec<T>::BT(c), in, out + poff, tk, st);
+  launch_bt_apply<T>(c, Prec<T>::BT(c), in, out + poff, tk, Jp, st);
   if (c->opt.inner_iters > 0) {
-    launch_inner_gmres<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), tk, out, st);
+    launch_inner_gmres<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), tk, out, Jp, st);
     return;
   }
   const int nsw = std::max(1, c->opt.jacobi_sweeps);
   const T om = (T)c->opt.jacobi_omega;
   T* cur = out;
   T* other = pk;
-  launch_jacobi_F<T>(c, Prec<T>::F(s), Prec<T>::Fd(s), om, tk, nullptr, cur, st);
+  launch_jacobi_F<T>(c, Prec<T>::F(s), Prec<T>::Fd(s), om, tk, nullptr, cur, Jp, st);
   for (int k = 1; k < nsw; ++k) {
-    launch_jacobi_F<T>(c, Prec<T>::F(s), Prec<T>::Fd(s), om, tk, cur, other, st);
+    launch_jacobi_F<T>(c, Prec<T>::F(s), Prec<T>::Fd(s), om, tk, cur, other, Jp, st);
     std::swap(cur, other);
   }
   if (cur != out) cudaMemcpyAsync(out, cur, poff * sizeof(T), cudaMemcpyDeviceToDevice, st);
@@ -139,32 +157,33 @@ static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out) {
 // read at execution time), so each (in, out) pair is captured once into a
 // CUDA graph and replayed.
 template <typename T>
-static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out) {
+static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out, int ld) {
   if (!c->use_graphs) {
-    apply_prec_raw<T>(c, s, in, out);
+    apply_prec_raw<T>(c, s, in, out, ld);
     return;
   }
-  auto key = std::make_pair((const void*)in, (const void*)out);
+  auto key = std::make_tuple((const void*)in, (const void*)out, ld);
   auto it = s.prec_graphs.find(key);
   if (it == s.prec_graphs.end()) {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      apply_prec_raw<T>(c, s, in, out);
+      apply_prec_raw<T>(c, s, in, out, ld);
       return;
     }
     set_capturing(true);
-    apply_prec_raw<T>(c, s, in, out);
+    apply_prec_raw<T>(c, s, in, out, ld);
     set_capturing(false);
     size_t nodes = 0;
     if (cudaStreamEndCapture(s.stream, &g) != cudaSuccess || cudaGraphGetNodes(g, nullptr, &nodes) != cudaSuccess ||
         cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
-      apply_prec_raw<T>(c, s, in, out);
+      apply_prec_raw<T>(c, s, in, out, ld);
       return;
     }
     cudaGraphDestroy(g);
+    s.graphs_built++;
     it = s.prec_graphs.emplace(key, std::make_pair(ge, (long long)nodes)).first;
   }
   cudaGraphLaunch(it->second.first, s.stream);
@@ -189,8 +208,14 @@ static int col_norms(const mhde_ctx* c, Sub& s, const T* X, std::vector<double>&
 // Gram of V_0..V_{k-1} against W (r columns) -> host array [k][r][r].
 template <typename T>
 static int gram_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int k, const T* W, int r,
-                     std::vector<double>& out) {
-  launch_gram<T>(V, vstride, k, W, c->n_rows, c->Jp, r, c->nchunk, s.part, s.gram, s.stream);
+                     std::vector<double>& out, int ld) {
+  // as many row chunks as the partial-sum buffer holds (up to 8 per SM), so
+  // that small blocks still fill the GPU
+  const size_t cap = (size_t)c->nchunk * (c->opt.restart + 1) * c->J * c->J;
+  const size_t per = (size_t)k * r * r;
+  const int nchunk = (int)std::max<size_t>(
+      1, std::min<size_t>({cap / per, (size_t)1216, (size_t)((c->n_rows + 63) / 64)}));
+  launch_gram<T>(V, vstride, k, W, c->n_rows, ld, r, nchunk, s.part, s.gram, s.stream);
   SCU(cudaMemcpyAsync(s.hbuf, s.gram, sizeof(double) * k * r * r, cudaMemcpyDeviceToHost, s.stream));
   SCU(cudaStreamSynchronize(s.stream));
   out.assign(s.hbuf, s.hbuf + (size_t)k * r * r);
@@ -252,8 +277,10 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   const double thresh = Prec<T>::thresh;
   used = 0;
   int rc;
+  // the Krylov blocks carry only the r kept directions: rows of stride Rp
+  const int Rp = (r + 3) / 4 * 4;
   double* dC0 = upload_coef<double>(c, s, C0, 3);
-  launch_combine_from_f64<T>(Vb, s.Res, dC0, J, r, c->n_rows, Jp, st);
+  launch_combine_from_f64<T>(Vb, s.Res, dC0, J, r, c->n_rows, Jp, Rp, st);
   BlockLS ls;
   ls.init(r, J, m, S0.data());
   std::vector<double> G, H, Y, Hsum;
@@ -262,19 +289,26 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   for (; k < m && used < maxit; ++k) {
     T* Vk = Vb + (size_t)k * vs;
     T* Zk_ = Zb + (size_t)k * vs;                 // flexible GMRES keeps every preconditioned block
-    apply_prec<T>(c, s, Vk, Zk_);
-    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk_, nullptr, Wk, 0, st);
+    PhaseClock pc1(c, s);
+    apply_prec<T>(c, s, Vk, Zk_, Rp);
+    pc1.stop(2);
+    PhaseClock pc2(c, s);
+    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk_, nullptr, Wk, 0, Rp, st);
+    pc2.stop(3);
+    PhaseClock pc3(c, s);
     // block classical Gram-Schmidt, twice
     Hsum.assign((size_t)(k + 1) * r * r, 0.0);
     for (int pass = 0; pass < 2; ++pass) {
-      if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wk, r, H))) return rc;
+      if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wk, r, H, Rp))) return rc;
       for (size_t t = 0; t < H.size(); ++t) Hsum[t] += H[t];
       for (auto& v : H) v = -v;
       T* dc = upload_coef<T>(c, s, H, pass);
-      launch_block_combine<T>(Wk, Wk, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Jp, st);
+      launch_block_combine<T>(Wk, Wk, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st);
     }
+    pc3.stop(4);
+    PhaseClock pc4(c, s);
     // normalise the new block (SVQB)
-    if ((rc = gram_host<T>(c, s, Wk, 0, 1, Wk, r, G))) return rc;
+    if ((rc = gram_host<T>(c, s, Wk, 0, 1, Wk, r, G, Rp))) return rc;
     std::vector<double> Tn, Sn;
     int rk = svqb(r, G, thresh, Tn, Sn);
     bool breakdown = rk < r;
@@ -288,9 +322,11 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
       for (int p = 0; p < r; ++p)
         for (int q = 0; q < r; ++q) hcol[(size_t)q * rows + (k + 1) * r + p] = Sn[(size_t)p * r + q];
       T* dc = upload_coef<T>(c, s, Tn, 2);
-      launch_block_combine<T>(Vb + (size_t)(k + 1) * vs, nullptr, T(0), Wk, 0, 1, r, dc, r, c->n_rows, Jp, st);
+      launch_block_combine<T>(Vb + (size_t)(k + 1) * vs, nullptr, T(0), Wk, 0, 1, r, dc, r, c->n_rows, Rp, Rp,
+                              st);
     }
     bool ok = ls.add(hcol.data());
+    pc4.stop(5);
     used++;
     double worst = 0.0;
     for (int j = 0; j < J; ++j) worst = std::max(worst, ls.resid(j));
@@ -305,7 +341,7 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   }
   ls.solve(Y);
   T* dc = upload_coef<T>(c, s, Y, 3);
-  launch_block_combine<T>(D, nullptr, T(0), Zb, vs, k, r, dc, J, c->n_rows, Jp, st);
+  launch_block_combine<T>(D, nullptr, T(0), Zb, vs, k, r, dc, J, c->n_rows, Rp, Jp, st);
   return MHDE_OK;
 }
 
@@ -313,6 +349,7 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
 int assemble_sub(mhde_ctx* c, int which) {
   Sub& s = c->sub[which];
   cudaStream_t st = s.stream;
+  PhaseClock pa(c, s);
   const Sub& o = c->sub[1 - which];
   const double* mean_conv = which == 0 ? c->d_mean_w : c->d_mean_v;
   const double* l2 = which == 0 ? c->d_l2_w : c->d_l2_v;
@@ -326,6 +363,7 @@ int assemble_sub(mhde_ctx* c, int which) {
   launch_rhs_assemble(c, s.S, o.S, c->have_forcing ? (which == 0 ? c->d_F1 : c->d_F2) : nullptr,
                       which == 0 ? c->d_Gv : c->d_Gw, s.Cloc, c->d_ccross, c->d_csame, s.Bv, st);
   SCU(cudaGetLastError());
+  pa.stop(0);
   return MHDE_OK;
 }
 
@@ -349,8 +387,9 @@ static int solve_sub_t(mhde_ctx* c, int which) {
   std::vector<double> rn(J), sc(J), unscale(c->Jp, 0.0);
   for (;;) {
     // FP64 residual and its Gram matrix (column norms on the diagonal)
-    launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, s.X, s.Bv, s.Res, 1, st);
-    if ((rc = gram_host<double>(c, s, s.Res, 0, 1, s.Res, J, G))) return rc;
+    PhaseClock pc0(c, s);
+    launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, s.X, s.Bv, s.Res, 1, c->Jp, st);
+    if ((rc = gram_host<double>(c, s, s.Res, 0, 1, s.Res, J, G, c->Jp))) return rc;
     double worst = 0.0, min_target = 1.0;
     for (int j = 0; j < J; ++j) {
       rn[j] = std::sqrt(std::max(G[(size_t)j * J + j], 0.0));
@@ -364,6 +403,7 @@ static int solve_sub_t(mhde_ctx* c, int which) {
       if (rn[j] > 0.0) min_target = std::min(min_target, c->opt.rtol * ref / rn[j]);
     }
     s.relres = worst;
+    pc0.stop(1);
     if (c->trace)
       std::fprintf(stderr, "[mhde] sub %d sweep %d iters %d relres %.3e\n", which, s.refine, s.iters, worst);
     if (worst <= c->opt.rtol) return MHDE_OK;
@@ -381,6 +421,7 @@ static int solve_sub_t(mhde_ctx* c, int which) {
     const double tau = 0.1 * tol_in / std::sqrt((double)J);
     const int r = svqb(J, Gs, std::max(tau * tau, 1e-30), Tm, Sm);
     if (r == 0) return MHDE_OK;
+    if (c->trace) std::fprintf(stderr, "[mhde] sub %d sweep %d block width %d\n", which, s.refine, r);
     C0.assign((size_t)J * r, 0.0);
     for (int p = 0; p < J; ++p)
       for (int t = 0; t < r; ++t) C0[(size_t)p * r + t] = sc[p] * Tm[(size_t)p * r + t];
@@ -398,9 +439,9 @@ static int solve_sub_t(mhde_ctx* c, int which) {
 void precond_apply_any(mhde_ctx* c, int which, const void* in, void* out) {
   Sub& s = c->sub[which];
   if (c->opt.precision == MHDE_PREC_FP64)
-    apply_prec<double>(c, s, (const double*)in, (double*)out);
+    apply_prec<double>(c, s, (const double*)in, (double*)out, c->Jp);
   else
-    apply_prec<float>(c, s, (const float*)in, (float*)out);
+    apply_prec<float>(c, s, (const float*)in, (float*)out, c->Jp);
 }
 
 void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W) {
