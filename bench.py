@@ -37,6 +37,12 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-separate", action="store_true", help="skip the separate-solve comparator")
+    p.add_argument("--workload", default="cavity", choices=["cavity", "batched"],
+                   help="cavity: the metric's workload; batched: uneven independent ensembles")
+    p.add_argument("--batch-count", type=int, default=64)
+    p.add_argument("--batch-mem-gb", type=float, default=240.0,
+                   help="cap on the summed workspaces of the batched ensembles")
     p.add_argument("--profile-only", action="store_true",
                    help="run W warm-up and K timed steps and exit (for ncu captures)")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -191,6 +197,92 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- separate-solve comparator
+def separate_solve_baseline(args, prec, device, steps=3, warmup=1):
+    """The usual per-member approach: each member is its own ensemble of one
+    (its own nu_j, nu_m,j, data and convecting field), so every step does J
+    assemblies and J single-right-hand-side solves, one member after the
+    other, through the same library.  Returns member-steps/s."""
+    import numpy as np
+    import torch
+    from paper_2108_05110_gb300 import ensemble_io
+    from workloads.ensembles import lid_cavity, Ensemble
+    ens = lid_cavity(N=args.N, J=args.J, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"], seed=2)
+    solvers = []
+    for j in range(ens.J):
+        pick = (lambda fn, jj: (lambda *a: fn(*a)[jj:jj + 1]))
+        one = Ensemble(f"member-{j}", ens.mesh, ens.nu[j:j + 1], ens.nu_m[j:j + 1], ens.s, ens.dt, ens.nsteps,
+                       u0=pick(ens.u0, j), B0=pick(ens.B0, j), u_bc=pick(ens.u_bc, j), B_bc=pick(ens.B_bc, j))
+        sol = ensemble_io.solver_for(one, precision=prec, device=device)
+        ensemble_io.feed_initial(sol, one)
+        ensemble_io.feed_step_data(sol, one, one.dt)
+        solvers.append(sol)
+    for _ in range(warmup):
+        for sol in solvers:
+            sol.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for sol in solvers:
+            sol.step()
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    for sol in solvers:
+        sol.close()
+    return {"value": ens.J * steps / secs, "unit": UNIT, "steps": steps, "warmup": warmup,
+            "what": "J=20 single-member contexts stepped one after the other (J assemblies and J "
+                    "single-RHS solves per step), same library and tolerance"}
+
+
+# --------------------------------------------------------------------------- batched ensembles
+def batched_arm(args, local_rank):
+    """Independent lid-cavity ensembles of uneven size (seed 5000+k: J_k in
+    1..64, N_k in {32, 64, 128, 256}, Re_k in [1000, 15000]) stepped
+    concurrently by mhde_advance_many; member-steps/s over all ensembles and
+    the per-step latency distribution."""
+    import numpy as np
+    import torch
+    import paper_2108_05110_gb300 as P
+    from paper_2108_05110_gb300 import ensemble_io
+    from workloads.ensembles import batched_family
+    torch.cuda.set_device(local_rank)
+    fam = batched_family(count=args.batch_count, nsteps=args.steps)
+    sols, members, total_bytes = [], 0, 0
+    for ens in fam:
+        probe = ensemble_io.solver_for(ens, bind=False, restart=15)
+        need = probe.workspace_size()
+        probe.close()
+        if total_bytes + need > args.batch_mem_gb * 1e9:
+            continue
+        sol = ensemble_io.solver_for(ens, restart=15, device=f"cuda:{local_rank}")
+        ensemble_io.feed_initial(sol, ens)
+        ensemble_io.feed_step_data(sol, ens, ens.dt)
+        sols.append(sol)
+        members += ens.J
+        total_bytes += need
+    P.advance_many(sols, args.warmup, nthreads=16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ms = P.advance_many(sols, args.steps, nthreads=16)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    value = members * args.steps / secs
+    sizes = sorted({(int(s.sizes.nv), int(s.J)) for s in sols})
+    line = {"metric": "batched ensemble member-steps/s (uneven J, N)", "value": value, "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{len(sols)} of {len(fam)} lid-cavity ensembles (seed 5000+k) that fit "
+                                   f"{args.batch_mem_gb:g} GB, J_k in 1..64, N_k in 32..256",
+                       "ensembles": len(sols), "members": members, "workspace_gb": total_bytes / 1e9,
+                       "concurrency": "mhde_advance_many, 16 host threads, 2 streams per ensemble"},
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                           "max": float(ms.max())}}
+    for sol in sols:
+        sol.close()
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- our arm
 def spmm_bytes(sz, prec_bytes):
     """Algorithmic bytes of one saddle SpMM: matrix structure and values read
@@ -298,6 +390,9 @@ def our_arm(args, rank, world, local_rank):
     h2d = (u0.nbytes + B0.nbytes + ub.nbytes + Bb.nbytes) / args.steps
     d2h = um.nbytes + Bm.nbytes
     sol.close()
+    separate = None
+    if rank == 0 and world == 1 and not args.no_separate:
+        separate = separate_solve_baseline(args, prec, f"cuda:{local_rank}")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -312,6 +407,8 @@ def our_arm(args, rank, world, local_rank):
                 "wall_ms_per_step": 1000.0 * wall / args.steps}
         if cpu_secs is not None:
             line["cpu_baseline"] = cpu_baseline_block(cpu_secs)
+        if separate is not None:
+            line["separate_solve_baseline"] = separate
         print(json.dumps(line), flush=True)
 
 
@@ -325,6 +422,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.workload == "batched":
+        if rank == 0:
+            batched_arm(args, local_rank)
         return
     if world > 1:
         import torch

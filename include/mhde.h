@@ -77,8 +77,13 @@ typedef struct {
   int jacobi_sweeps;    /* damped Jacobi sweeps approximating F^{-1}; default 3 */
   double jacobi_omega;  /* damping of those sweeps; default 0.3 */
   int amg_sweeps;       /* Jacobi sweeps per level in the pressure-Laplacian V-cycle; default 2 */
-  int inner_iters;      /* k of the inner per-column GMRES(k) on F (flexible outer GMRES);
-                           0 = damped Jacobi sweeps instead; default 8 */
+  int poly_degree;      /* degree d (even, <= 16) of the GMRES polynomial in D^{-1} F that
+                           approximates F^{-1}, rebuilt every step from d Arnoldi steps;
+                           0 = use inner_iters instead; default 0 (the fixed polynomial is
+                           cheaper per application but lost robustness as the cavity flow
+                           developed, so the inner GMRES is the default) */
+  int inner_iters;      /* k of the inner per-column GMRES(k) on F (flexible outer GMRES), used
+                           when poly_degree = 0; 0 = damped Jacobi sweeps instead; default 8 */
   int schur;            /* pressure Schur approximation: 0 Cahouet-Chabard, 1 pressure
                            convection-diffusion (adds the mean-field P1 convection); default 1 */
   int strict;           /* 1: reject alpha_j <= 0 or mu <= 1/2 with MHDE_ESTAB; default 0 */
@@ -153,6 +158,14 @@ int mhde_step(mhde_ctx* ctx);
 
 /* nsteps calls of mhde_step with the forcing and Dirichlet data held fixed. */
 int mhde_advance(mhde_ctx* ctx, int nsteps);
+
+/* Batched uneven ensembles: advance `count` independent, bound contexts
+ * (any meshes and member counts) by nsteps steps each, from a pool of
+ * nthreads host threads; every ensemble keeps its own two streams, so the
+ * ensembles' kernels run concurrently on the device.  step_ms (optional,
+ * [count][nsteps]) receives each step's wall time for latency statistics.
+ * Returns the first failing context's error code. */
+int mhde_advance_many(mhde_ctx** ctxs, int count, int nsteps, int nthreads, double* step_ms);
 
 /* Ensemble means <u> = (<v>+<w>)/2 and <B> = (<v>-<w>)/(2 sqrt s) at the
  * current step as [n2][2] (host).  B_mean may be NULL; with s = 0 a non-NULL

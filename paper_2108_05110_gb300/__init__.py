@@ -5,5 +5,5 @@ ABI of ``include/mhde.h``); :mod:`.binding` marshals arguments only.
 """
 from .binding import (  # noqa: F401
     Library, load_library, Options, Sizes, Stats, MhdeError, EnsembleSolver, library_path,
-    declared_functions, block_gram, block_gram_noalloc, PREC_FP64, PREC_MIXED,
+    declared_functions, block_gram, block_gram_noalloc, advance_many, PREC_FP64, PREC_MIXED,
 )

@@ -34,7 +34,8 @@ class Options(C.Structure):
     _fields_ = [("mu", C.c_double), ("conv_form", C.c_int), ("precision", C.c_int),
                 ("rtol", C.c_double), ("inner_rtol", C.c_double), ("restart", C.c_int),
                 ("max_iter", C.c_int), ("max_refine", C.c_int), ("jacobi_sweeps", C.c_int),
-                ("jacobi_omega", C.c_double), ("amg_sweeps", C.c_int), ("inner_iters", C.c_int),
+                ("jacobi_omega", C.c_double), ("amg_sweeps", C.c_int), ("poly_degree", C.c_int),
+                ("inner_iters", C.c_int),
                 ("schur", C.c_int), ("strict", C.c_int)]
 
 
@@ -72,6 +73,7 @@ SIGNATURES = {
     "mhde_set_dirichlet": (C.c_int, [_P, _D, _D]),
     "mhde_step": (C.c_int, [_P]),
     "mhde_advance": (C.c_int, [_P, C.c_int]),
+    "mhde_advance_many": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, C.c_int, _D]),
     "mhde_read_mean": (C.c_int, [_P, _D, _D]),
     "mhde_read_state": (C.c_int, [_P, _D, _D, _D, _D]),
     "mhde_read_member": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
@@ -151,6 +153,18 @@ def default_options(**kw):
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+def advance_many(solvers, nsteps, nthreads=8):
+    """Step independent ensembles concurrently through mhde_advance_many;
+    returns per-step wall times [len(solvers), nsteps] in ms."""
+    lib = load_library()
+    arr = (_P * len(solvers))(*[s.ctx for s in solvers])
+    ms = np.zeros((len(solvers), nsteps))
+    rc = lib.mhde_advance_many(arr, len(solvers), int(nsteps), int(nthreads), _dptr(ms))
+    if rc != 0:
+        raise MhdeError(rc, "mhde_advance_many")
+    return ms
 
 
 def block_gram(V, W, kblocks, r, stream=None):

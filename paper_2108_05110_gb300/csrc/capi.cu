@@ -2,6 +2,7 @@
 // workspace layout, input conversion to Elsaesser variables (Section 1),
 // the time step of Algorithm 1 on two streams, read-outs and parity probes.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -115,6 +116,7 @@ size_t layout(mhde_ctx* c, char* base) {
   }
   c->d_coarse_inv = w.take<double>((size_t)amg.nc * amg.nc);
   c->d_coarse_invf = w.take<float>((size_t)amg.nc * amg.nc);
+  c->d_prand = w.take<char>(n2 * 4 * ksize(c));
   c->d_ccross = w.take<double>(Jp);
   c->d_csame = w.take<double>(Jp);
   // inputs and ensemble quantities
@@ -157,7 +159,7 @@ size_t layout(mhde_ctx* c, char* base) {
     s.Np = w.take<double>(fe.Kp.nnz());
     s.Npf = w.take<float>(fe.Kp.nnz());
     {
-      const int kin = std::max(1, c->opt.inner_iters);
+      const int kin = std::max({1, c->opt.inner_iters, c->opt.poly_degree});
       const size_t C2 = 2 * Jp;
       s.ibasis = w.take<char>((size_t)(kin + 1) * n2 * C2 * ks);
       s.ipart = w.take<double>((size_t)c->nchunk_in * (KIN_MAX + 2) * C2);
@@ -166,6 +168,7 @@ size_t layout(mhde_ctx* c, char* base) {
       s.ibeta = w.take<double>(2 * C2);
       s.iy = w.take<double>((size_t)kin * C2);
       s.zbasis = w.take<char>((size_t)m * vs * ks);
+      s.poly = w.take<double>(KIN_MAX + 2);
     }
     s.amg.assign(amg.levels.size(), DevAmgLevel());
     for (size_t l = 0; l < amg.levels.size(); ++l) {
@@ -228,6 +231,7 @@ void mhde_default_options(mhde_options* o) {
   o->jacobi_sweeps = 3;
   o->jacobi_omega = 0.3;
   o->amg_sweeps = 2;
+  o->poly_degree = 0;
   o->inner_iters = 8;
   o->schur = 1;
   o->strict = 0;
@@ -245,7 +249,8 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
     mhde_default_options(&c->opt);
   if (c->opt.restart < 1 || c->opt.restart > 200 || c->opt.max_iter < 1 || !(c->opt.rtol > 0) ||
       (c->opt.precision != MHDE_PREC_FP64 && c->opt.precision != MHDE_PREC_MIXED) ||
-      (c->opt.conv_form != 0 && c->opt.conv_form != 1) || c->opt.inner_iters < 0 ||
+      (c->opt.conv_form != 0 && c->opt.conv_form != 1) || c->opt.inner_iters < 0 || c->opt.poly_degree < 0 ||
+      c->opt.poly_degree > mhde::KIN_MAX || c->opt.poly_degree % 2 != 0 ||
       c->opt.inner_iters > mhde::KIN_MAX || (c->opt.schur != 0 && c->opt.schur != 1)) {
     delete c;
     return MHDE_EINVAL;
@@ -381,6 +386,25 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
     cs[j] = c->c_same[j];
   }
   CU(up(c->d_ccross, cc, st));
+  {
+    // fixed pseudo-random start block of the per-step polynomial setup
+    std::vector<double> pr((size_t)fe.n2 * 4);
+    unsigned long long x = 0x9E3779B97F4A7C15ull;
+    for (auto& v : pr) {
+      x ^= x << 13;
+      x ^= x >> 7;
+      x ^= x << 17;
+      v = (double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    if (ksize(c) == 8) {
+      CU(cudaMemcpyAsync(c->d_prand, pr.data(), pr.size() * 8, cudaMemcpyHostToDevice, st));
+      CU(cudaStreamSynchronize(st));
+    } else {
+      std::vector<float> pf(pr.begin(), pr.end());
+      CU(cudaMemcpyAsync(c->d_prand, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice, st));
+      CU(cudaStreamSynchronize(st));
+    }
+  }
   CU(up(c->d_csame, cs, st));
   // AMG operators
   std::vector<std::vector<float>> keep_f;   // host float copies alive until the sync below
@@ -568,6 +592,40 @@ int mhde_step(mhde_ctx* c) {
       for (double& v : s.phase_ms) v = 0.0;
     }
   }
+  return MHDE_OK;
+}
+
+int mhde_advance_many(mhde_ctx** ctxs, int count, int nsteps, int nthreads, double* step_ms) {
+  if (!ctxs || count < 1 || nsteps < 0 || nthreads < 1) return MHDE_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    int rc = check_ready(ctxs[i], true);
+    if (rc) return rc;
+  }
+  std::atomic<int> next{0};
+  std::vector<int> status(count, MHDE_OK);
+  auto worker = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) return;
+      cudaSetDevice(ctxs[i]->device);
+      for (int n = 0; n < nsteps; ++n) {
+        auto t0 = std::chrono::steady_clock::now();
+        int rc = mhde_step(ctxs[i]);
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (step_ms) step_ms[(size_t)i * nsteps + n] = ms;
+        if (rc) {
+          status[i] = rc;
+          break;
+        }
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  const int nt = std::min(nthreads, count);
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (status[i] != MHDE_OK) return status[i];
   return MHDE_OK;
 }
 

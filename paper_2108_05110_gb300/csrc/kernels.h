@@ -107,7 +107,11 @@ void launch_Np(const mhde_ctx* c, const double* mean_conv, double* slots, double
 // inner per-column GMRES(k) on F (velocity block), z ~ F^{-1} r
 template <typename T>
 void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
-                        cudaStream_t st);
+                        int kin, cudaStream_t st);
+// GMRES-polynomial approximation z ~ F^{-1} r with the factors in s.poly
+template <typename T>
+void launch_poly_apply(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
+                       cudaStream_t st);
 
 // solver entry points (solver.cu)
 int assemble_sub(mhde_ctx* c, int which);

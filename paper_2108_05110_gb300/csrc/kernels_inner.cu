@@ -34,6 +34,23 @@ __device__ __forceinline__ float4 izero(float4) { return make_float4(0.f, 0.f, 0
 
 static inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// four consecutive entries (16-byte aligned for float, 32-byte for double)
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // w[a][:] = sum_k F_ak dinv_k v[col_k][:]
 template <typename T>
 __global__ void k_fd_spmm(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
@@ -53,26 +70,38 @@ __global__ void k_fd_spmm(int n2, int nch, const int* __restrict__ rp, const int
 }
 
 // Partial column dots: part[chunk][l][col] = sum_rows V_l[row][col] w[row][col]
-// (l < nl), and part[chunk][nl][col] = sum_rows w^2 when with_norm.
+// (l < nl), and part[chunk][nl][col] = sum_rows w^2 when with_norm.  A thread
+// owns 4 consecutive columns of a row (one 16-byte load per vector for FP32),
+// so many rows are in flight per CTA.
 template <typename T>
 __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, const T* V, size_t vstride,
                                                   const T* w, int rows_per_chunk, int with_norm,
                                                   double* __restrict__ part) {
   extern __shared__ double red[];
-  const int G = blockDim.x / C;
-  const int c = threadIdx.x % C, g = threadIdx.x / C;
+  const int C4 = C / 4;
+  const int G = blockDim.x / C4;
+  const int c4 = threadIdx.x % C4, g = threadIdx.x / C4;
   const int r0 = blockIdx.x * rows_per_chunk, r1 = min(n_rows, r0 + rows_per_chunk);
-  T acc[KIN_MAX + 2];
+  T acc[KIN_MAX + 2][4];
 #pragma unroll
-  for (int l = 0; l < KIN_MAX + 2; ++l) acc[l] = T(0);
+  for (int l = 0; l < KIN_MAX + 2; ++l)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[l][q] = T(0);
   if (g < G) {
     for (int row = r0 + g; row < r1; row += G) {
-      const size_t o = (size_t)row * C + c;
-      const T wv = w[o];
+      const size_t o = (size_t)row * C + 4 * c4;
+      T wv[4];
+      ld4(w + o, wv);
 #pragma unroll
       for (int l = 0; l < KIN_MAX + 1; ++l)
-        if (l < nl) acc[l] += V[(size_t)l * vstride + o] * wv;
-      acc[KIN_MAX + 1] += wv * wv;
+        if (l < nl) {
+          T vv[4];
+          ld4(V + (size_t)l * vstride + o, vv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[l][q] += vv[q] * wv[q];
+        }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[KIN_MAX + 1][q] += wv[q] * wv[q];
     }
   }
 #pragma unroll
@@ -80,7 +109,9 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
     const bool active = (l < nl) || (l == KIN_MAX + 1 && with_norm);   // uniform over the block
     if (!active) continue;
     const int slot = (l < nl) ? l : nl;
-    if (g < G) red[g * C + c] = (double)acc[l];
+    if (g < G)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[g * C + 4 * c4 + q] = (double)acc[l][q];
     __syncthreads();
     if (threadIdx.x < C) {
       double sum = 0.0;
@@ -140,30 +171,44 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
 }
 
 // out[row][col] = (in[row][col] - sum_l V_l[row][col] dots[l][col]) * scale[col]
-// (in and out may alias; nl may be 0)
+// (in and out may alias; nl may be 0); 4 consecutive entries per thread
 template <typename T>
 __global__ void k_col_update(int n_rows, int C, int nl, const T* V, size_t vstride, const double* __restrict__ dots,
                              const T* in, T* out, const double* __restrict__ scale) {
-  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= (long long)n_rows * C) return;
-  const int c = (int)(tid % C);
-  T acc = in[tid];
-  for (int l = 0; l < nl; ++l) acc -= V[(size_t)l * vstride + tid] * (T)dots[(size_t)l * C + c];
-  if (scale) acc *= (T)scale[c];
-  out[tid] = acc;
+  long long t4 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)n_rows * C;
+  if (4 * t4 >= n) return;
+  const size_t o = (size_t)(4 * t4);
+  const int c0 = (int)(o % C);
+  T acc[4];
+  ld4(in + o, acc);
+  for (int l = 0; l < nl; ++l) {
+    T vv[4];
+    ld4(V + (size_t)l * vstride + o, vv);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] -= vv[q] * (T)dots[(size_t)l * C + c0 + q];
+  }
+  if (scale)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] *= (T)scale[c0 + q];
+  st4(out + o, acc);
 }
 
 // Per-column least squares min || beta e_1 - H y || by Givens rotations.
+// One CTA per column: the Hessenberg matrix is staged in shared memory by
+// the CTA and reduced by its first thread.
 __global__ void k_col_lsq(int C, int kin, const double* __restrict__ H, const double* __restrict__ beta,
                           double* __restrict__ y) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  double h[KIN_MAX + 1][KIN_MAX];
-  double g[KIN_MAX + 1];
-  for (int l = 0; l <= kin; ++l) {
-    g[l] = 0.0;
-    for (int i = 0; i < kin; ++i) h[l][i] = (l <= i + 1) ? H[((size_t)l * kin + i) * C + c] : 0.0;
+  __shared__ double h[KIN_MAX + 1][KIN_MAX];
+  __shared__ double g[KIN_MAX + 1];
+  const int c = blockIdx.x;
+  for (int e = threadIdx.x; e < (kin + 1) * kin; e += blockDim.x) {
+    int l = e / kin, i = e % kin;
+    h[l][i] = (l <= i + 1) ? H[((size_t)l * kin + i) * C + c] : 0.0;
   }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int l = 0; l <= kin; ++l) g[l] = 0.0;
   g[0] = beta[c];
   for (int i = 0; i < kin; ++i) {
     double a = h[i][i], b = h[i + 1][i];
@@ -179,35 +224,45 @@ __global__ void k_col_lsq(int C, int kin, const double* __restrict__ H, const do
     g[i + 1] = -sn * t1 + cs * t2;
   }
   for (int i = kin - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int j = i + 1; j < kin; ++j) s -= h[i][j] * y[(size_t)j * C + c];
-    y[(size_t)i * C + c] = h[i][i] != 0.0 ? s / h[i][i] : 0.0;
+    double sum = g[i];
+    for (int j = i + 1; j < kin; ++j) sum -= h[i][j] * y[(size_t)j * C + c];
+    y[(size_t)i * C + c] = h[i][i] != 0.0 ? sum / h[i][i] : 0.0;
   }
 }
 
-// z[row][col] = dinv[row] * sum_l V_l[row][col] y[l][col]
+// z[row][col] = dinv[row] * sum_l V_l[row][col] y[l][col]; 4 entries per thread
 template <typename T>
 __global__ void k_col_final(int n_rows, int C, int kin, const T* __restrict__ V, size_t vstride,
                             const double* __restrict__ y, const T* __restrict__ dinv, T* __restrict__ z) {
-  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= (long long)n_rows * C) return;
-  const int c = (int)(tid % C);
-  const int row = (int)(tid / C);
-  T acc = T(0);
-  for (int l = 0; l < kin; ++l) acc += V[(size_t)l * vstride + tid] * (T)y[(size_t)l * C + c];
-  z[tid] = acc * dinv[row];
+  long long t4 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)n_rows * C;
+  if (4 * t4 >= n) return;
+  const size_t o = (size_t)(4 * t4);
+  const int c0 = (int)(o % C);
+  const int row = (int)(o / C);
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (int l = 0; l < kin; ++l) {
+    T vv[4];
+    ld4(V + (size_t)l * vstride + o, vv);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += vv[q] * (T)y[(size_t)l * C + c0 + q];
+  }
+  const T d = dinv[row];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] *= d;
+  st4(z + o, acc);
 }
 
 template <typename T>
 void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
-                        cudaStream_t st) {
-  const int n2 = c->fe.n2, C = 2 * ld, kin = c->opt.inner_iters;
+                        int kin, cudaStream_t st) {
+  const int n2 = c->fe.n2, C = 2 * ld;
   const int nch = C / IVec<T>::W;
   const size_t vstride = (size_t)n2 * C;
   const int nchunk = c->nchunk_in;
   const int rows_per_chunk = (n2 + nchunk - 1) / nchunk;
-  const int threads = (256 / C) * C;
-  const size_t shm = (size_t)threads * sizeof(double);
+  const int threads = (256 / (C / 4)) * (C / 4);          // whole row groups of C/4 threads
+  const size_t shm = (size_t)(threads / (C / 4)) * C * sizeof(double);
   T* Vb = (T*)s.ibasis;
   const long long nel = (long long)n2 * C;
   count_launch(3 + 4 * kin + 2);
@@ -215,7 +270,7 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* d
   k_col_dots<T><<<nchunk, threads, shm, st>>>(n2, C, 1, r, 0, r, rows_per_chunk, 0, s.ipart);
   k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, 1, kin, s.ipart, s.idot, 2, 0, s.ih, s.ibeta,
                                          s.ibeta + C);
-  k_col_update<T><<<nb(nel, 256), 256, 0, st>>>(n2, C, 0, Vb, vstride, s.idot, r, Vb, s.ibeta + C);
+  k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, 0, Vb, vstride, s.idot, r, Vb, s.ibeta + C);
   for (int i = 0; i < kin; ++i) {
     T* vi = Vb + (size_t)i * vstride;
     T* w = Vb + (size_t)(i + 1) * vstride;
@@ -225,15 +280,116 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* d
     k_col_dots<T><<<nchunk, threads, shm, st>>>(n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 1, s.ipart);
     k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, i + 1, kin, s.ipart, s.idot, 3, i, s.ih, s.ibeta,
                                       s.ibeta + C);
-    k_col_update<T><<<nb(nel, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, s.idot, w, w, s.ibeta + C);
+    k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, s.idot, w, w, s.ibeta + C);
   }
-  k_col_lsq<<<nb(C, 64), 64, 0, st>>>(C, kin, s.ih, s.ibeta, s.iy);
-  k_col_final<T><<<nb(nel, 256), 256, 0, st>>>(n2, C, kin, Vb, vstride, s.iy, dinv, z);
+  k_col_lsq<<<C, 32, 0, st>>>(C, kin, s.ih, s.ibeta, s.iy);
+  k_col_final<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, kin, Vb, vstride, s.iy, dinv, z);
 }
 
 template void launch_inner_gmres<double>(const mhde_ctx*, const Sub&, const double*, const double*,
-                                         const double*, double*, int, cudaStream_t);
+                                         const double*, double*, int, int, cudaStream_t);
 template void launch_inner_gmres<float>(const mhde_ctx*, const Sub&, const float*, const float*, const float*,
-                                        float*, int, cudaStream_t);
+                                        float*, int, int, cudaStream_t);
+
+// ------------------------------------------------------------ GMRES polynomial
+// z ~ F^{-1} r as q(A) D^{-1} r with A = D^{-1} F and q(z) = (1 - pi(z)) / z,
+// pi(z) = prod_i (1 - c1_i z + c2_i z^2).  Per quadratic factor:
+//   y   += c1 prod - c2 A prod
+//   prod = prod - c1 A prod + c2 A^2 prod
+// Rows are [n2][C] (C = 2 ld: component, member); Dirichlet rows of F are
+// identity rows and get z = r exactly.
+
+// w = D^{-1} F prod
+template <typename T>
+__global__ void k_poly_a(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
+                         const T* __restrict__ F, const T* __restrict__ dinv, const T* __restrict__ prod,
+                         T* __restrict__ w) {
+  using V = typename IVec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)n2 * nch) return;
+  int a = (int)(tid / nch), ch = (int)(tid % nch);
+  const V* pv = reinterpret_cast<const V*>(prod);
+  V acc = izero(V());
+  for (int k = rp[a]; k < rp[a + 1]; ++k) ifma(acc, F[k], pv[(size_t)col[k] * nch + ch]);
+  const T d = dinv[a];
+  V out;
+  out.x = d * acc.x;
+  out.y = d * acc.y;
+  if constexpr (IVec<T>::W == 4) {
+    out.z = d * acc.z;
+    out.w = d * acc.w;
+  }
+  reinterpret_cast<V*>(w)[(size_t)a * nch + ch] = out;
+}
+
+// t = A w (gathered), then the factor update of y and prod at the own row.
+// last: no prod update, Dirichlet rows set y = r.
+template <typename T, bool LAST>
+__global__ void k_poly_b(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
+                         const T* __restrict__ F, const T* __restrict__ dinv, const unsigned char* __restrict__ isbnd,
+                         const double* __restrict__ coef, int item, int first, T* prod, const T* __restrict__ w,
+                         T* y, const T* __restrict__ r) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)n2 * nch) return;
+  constexpr int W = IVec<T>::W;
+  const int a = (int)(tid / nch), ch = (int)(tid % nch);
+  const T c1 = (T)coef[2 * item], c2 = (T)coef[2 * item + 1];
+  const size_t o = ((size_t)a * nch + ch) * W;
+  T tv[W];
+  if (!LAST) {
+    for (int q = 0; q < W; ++q) tv[q] = T(0);
+    for (int k = rp[a]; k < rp[a + 1]; ++k) {
+      const T f = F[k];
+      const size_t oc = ((size_t)col[k] * nch + ch) * W;
+#pragma unroll
+      for (int q = 0; q < W; ++q) tv[q] += f * w[oc + q];
+    }
+  }
+  const T d = dinv[a];
+  const bool bnd = isbnd[a] != 0;
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    const T pq = prod[o + q], wq = w[o + q];
+    T yq = (first ? T(0) : y[o + q]) + c1 * pq - c2 * wq;
+    if (LAST && bnd) yq = r[o + q];
+    y[o + q] = yq;
+    if (!LAST) prod[o + q] = pq - c1 * wq + c2 * d * tv[q];
+  }
+}
+
+template <typename T>
+__global__ void k_poly_scale(long long n, int C, const T* __restrict__ dinv, const T* __restrict__ r,
+                             T* __restrict__ prod) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  prod[i] = dinv[i / C] * r[i];
+}
+
+template <typename T>
+void launch_poly_apply(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
+                       cudaStream_t st) {
+  const int n2 = c->fe.n2, C = 2 * ld, d = c->opt.poly_degree, items = d / 2;
+  const int nch = C / IVec<T>::W;
+  const long long nel = (long long)n2 * C;
+  T* prod = (T*)s.ibasis;
+  T* w = prod + (size_t)n2 * C;
+  count_launch(1 + 2 * items);
+  k_poly_scale<T><<<nb(nel, 256), 256, 0, st>>>(nel, C, dinv, r, prod);
+  const unsigned g = nb((long long)n2 * nch, 256);
+  for (int i = 0; i < items; ++i) {
+    k_poly_a<T><<<g, 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, prod, w);
+    if (i + 1 < items)
+      k_poly_b<T, false><<<g, 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, c->d_isbnd, s.poly, i, i == 0,
+                                            prod, w, z, r);
+    else
+      k_poly_b<T, true><<<g, 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, c->d_isbnd, s.poly, i, i == 0,
+                                           prod, w, z, r);
+  }
+}
+
+template void launch_poly_apply<double>(const mhde_ctx*, const Sub&, const double*, const double*, const double*,
+                                        double*, int, cudaStream_t);
+template void launch_poly_apply<float>(const mhde_ctx*, const Sub&, const float*, const float*, const float*,
+                                       float*, int, cudaStream_t);
 
 }  // namespace mhde

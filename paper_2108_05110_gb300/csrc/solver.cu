@@ -136,8 +136,12 @@ static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out, int J
   launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), (T)(1.0 / c->dt), (T)nu_hat, Kp.rowptr, Kp.col,
                       c->opt.schur == 1 ? Prec<T>::Np(s) : (const T*)nullptr, out + poff, st);
   launch_bt_apply<T>(c, Prec<T>::BT(c), in, out + poff, tk, Jp, st);
+  if (c->opt.poly_degree > 0) {
+    launch_poly_apply<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), tk, out, Jp, st);
+    return;
+  }
   if (c->opt.inner_iters > 0) {
-    launch_inner_gmres<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), tk, out, Jp, st);
+    launch_inner_gmres<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), tk, out, Jp, c->opt.inner_iters, st);
     return;
   }
   const int nsw = std::max(1, c->opt.jacobi_sweeps);
@@ -289,28 +293,69 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   for (; k < m && used < maxit; ++k) {
     T* Vk = Vb + (size_t)k * vs;
     T* Zk_ = Zb + (size_t)k * vs;                 // flexible GMRES keeps every preconditioned block
+    T* Wn = Vb + (size_t)(k + 1) * vs;            // W = A Z_k is built in the next basis slot
     PhaseClock pc1(c, s);
     apply_prec<T>(c, s, Vk, Zk_, Rp);
     pc1.stop(2);
     PhaseClock pc2(c, s);
-    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk_, nullptr, Wk, 0, Rp, st);
+    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk_, nullptr, Wn, 0, Rp, st);
     pc2.stop(3);
     PhaseClock pc3(c, s);
-    // block classical Gram-Schmidt, twice
-    Hsum.assign((size_t)(k + 1) * r * r, 0.0);
-    for (int pass = 0; pass < 2; ++pass) {
-      if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wk, r, H, Rp))) return rc;
+    // one reduction: [V_0 .. V_k, W]^T W gives the projections H_i = V_i^T W
+    // and W^T W; the projected block's Gram follows from W^T W - H^T H
+    if ((rc = gram_host<T>(c, s, Vb, vs, k + 2, Wn, r, G, Rp))) return rc;
+    Hsum.assign(G.begin(), G.begin() + (size_t)(k + 1) * r * r);
+    std::vector<double> Gp(G.begin() + (size_t)(k + 1) * r * r, G.end());
+    double trW = 0.0, trP = 0.0;
+    for (int p = 0; p < r; ++p) trW += Gp[(size_t)p * r + p];
+    for (int i = 0; i <= k; ++i)
+      for (int p = 0; p < r; ++p)
+        for (int q = 0; q < r; ++q) {
+          double acc = 0.0;
+          for (int t = 0; t < r; ++t) acc += Hsum[(size_t)i * r * r + t * r + p] * Hsum[(size_t)i * r * r + t * r + q];
+          Gp[(size_t)p * r + q] -= acc;
+        }
+    for (int p = 0; p < r; ++p) trP += Gp[(size_t)p * r + p];
+    std::vector<double> Tn, Sn;
+    int rk;
+    if (trP > 1e-3 * trW) {
+      rk = svqb(r, Gp, thresh, Tn, Sn);
+      if (rk == r) {
+        // V_{k+1} = (W - sum_i V_i H_i) T  in one pass, in place
+        std::vector<double> Cc((size_t)(k + 2) * r * r, 0.0);
+        for (int i = 0; i <= k; ++i)
+          for (int p = 0; p < r; ++p)
+            for (int q = 0; q < r; ++q) {
+              double acc = 0.0;
+              for (int t = 0; t < r; ++t) acc += Hsum[(size_t)i * r * r + p * r + t] * Tn[(size_t)t * r + q];
+              Cc[(size_t)i * r * r + p * r + q] = -acc;
+            }
+        for (int p = 0; p < r; ++p)
+          for (int q = 0; q < r; ++q) Cc[(size_t)(k + 1) * r * r + p * r + q] = Tn[(size_t)p * r + q];
+        T* dc = upload_coef<T>(c, s, Cc, 0);
+        launch_block_combine<T>(Wn, nullptr, T(0), Vb, vs, k + 2, r, dc, r, c->n_rows, Rp, Rp, st);
+      }
+    } else {
+      // strong cancellation: explicit two-pass Gram-Schmidt for this block
+      for (auto& v : H) v = 0.0;
+      H.assign(Hsum.begin(), Hsum.end());
+      for (auto& v : H) v = -v;
+      T* dc = upload_coef<T>(c, s, H, 0);
+      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st);
+      if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wn, r, H, Rp))) return rc;
       for (size_t t = 0; t < H.size(); ++t) Hsum[t] += H[t];
       for (auto& v : H) v = -v;
-      T* dc = upload_coef<T>(c, s, H, pass);
-      launch_block_combine<T>(Wk, Wk, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st);
+      dc = upload_coef<T>(c, s, H, 1);
+      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st);
+      if ((rc = gram_host<T>(c, s, Wn, 0, 1, Wn, r, G, Rp))) return rc;
+      rk = svqb(r, G, thresh, Tn, Sn);
+      if (rk == r) {
+        dc = upload_coef<T>(c, s, Tn, 2);
+        launch_block_combine<T>(Wn, nullptr, T(0), Wn, 0, 1, r, dc, r, c->n_rows, Rp, Rp, st);
+      }
     }
     pc3.stop(4);
     PhaseClock pc4(c, s);
-    // normalise the new block (SVQB)
-    if ((rc = gram_host<T>(c, s, Wk, 0, 1, Wk, r, G, Rp))) return rc;
-    std::vector<double> Tn, Sn;
-    int rk = svqb(r, G, thresh, Tn, Sn);
     bool breakdown = rk < r;
     const int rows = (k + 2) * r;
     std::vector<double> hcol((size_t)rows * r, 0.0);
@@ -318,13 +363,9 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
       for (int p = 0; p < r; ++p)
         for (int q = 0; q < r; ++q)
           hcol[(size_t)q * rows + i * r + p] = Hsum[(size_t)i * r * r + (size_t)p * r + q];
-    if (!breakdown) {
+    if (!breakdown)
       for (int p = 0; p < r; ++p)
         for (int q = 0; q < r; ++q) hcol[(size_t)q * rows + (k + 1) * r + p] = Sn[(size_t)p * r + q];
-      T* dc = upload_coef<T>(c, s, Tn, 2);
-      launch_block_combine<T>(Vb + (size_t)(k + 1) * vs, nullptr, T(0), Wk, 0, 1, r, dc, r, c->n_rows, Rp, Rp,
-                              st);
-    }
     bool ok = ls.add(hcol.data());
     pc4.stop(5);
     used++;
@@ -342,6 +383,39 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   ls.solve(Y);
   T* dc = upload_coef<T>(c, s, Y, 3);
   launch_block_combine<T>(D, nullptr, T(0), Zb, vs, k, r, dc, J, c->n_rows, Rp, Jp, st);
+  return MHDE_OK;
+}
+
+// ------------------------------------------------------------------ polynomial setup
+// d Arnoldi steps of the inner GMRES on a fixed pseudo-random block give a
+// (d+1) x d Hessenberg matrix; its harmonic Ritz values are the roots of the
+// GMRES residual polynomial used as the F-block preconditioner this step.
+template <typename T>
+static int poly_setup(mhde_ctx* c, Sub& s) {
+  const int d = c->opt.poly_degree, C = 4;
+  cudaStream_t st = s.stream;
+  T* zscratch = (T*)s.Pk;                    // output of the setup solve is not used
+  launch_inner_gmres<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), (const T*)c->d_prand, zscratch, 2, d, st);
+  std::vector<double> Hall((size_t)(d + 1) * d * C), H((size_t)(d + 1) * d);
+  SCU(cudaMemcpyAsync(Hall.data(), s.ih, Hall.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SCU(cudaStreamSynchronize(st));
+  for (int l = 0; l <= d; ++l)
+    for (int i = 0; i < d; ++i) H[(size_t)l * d + i] = Hall[((size_t)l * d + i) * C + 0];
+  std::vector<double> c1, c2;
+  if (!gmres_poly_factors(d, H.data(), c1, c2)) {
+    // fall back to squared damped Jacobi factors (1 - w z)^2
+    const double om = c->opt.jacobi_omega;
+    c1.assign(d / 2, 2.0 * om);
+    c2.assign(d / 2, om * om);
+    s.poly_fallbacks++;
+  }
+  std::vector<double> coef(2 * (d / 2));
+  for (int i = 0; i < d / 2; ++i) {
+    coef[2 * i] = c1[i];
+    coef[2 * i + 1] = c2[i];
+  }
+  SCU(cudaMemcpyAsync(s.poly, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SCU(cudaStreamSynchronize(st));
   return MHDE_OK;
 }
 
@@ -363,6 +437,10 @@ int assemble_sub(mhde_ctx* c, int which) {
   launch_rhs_assemble(c, s.S, o.S, c->have_forcing ? (which == 0 ? c->d_F1 : c->d_F2) : nullptr,
                       which == 0 ? c->d_Gv : c->d_Gw, s.Cloc, c->d_ccross, c->d_csame, s.Bv, st);
   SCU(cudaGetLastError());
+  if (c->opt.poly_degree > 0) {
+    int rc = c->opt.precision == MHDE_PREC_FP64 ? poly_setup<double>(c, s) : poly_setup<float>(c, s);
+    if (rc) return rc;
+  }
   pa.stop(0);
   return MHDE_OK;
 }

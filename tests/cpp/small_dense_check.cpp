@@ -1,0 +1,29 @@
+// Host check of the small dense routines of libmhde, driven from
+// tests/test_host_small_dense_cpu.py through stdin/stdout:
+//   "E n a_00 ... a_{n-1,n-1}"    -> eigenvalues of an upper Hessenberg matrix
+//   "P d h_00 ... h_{d,d-1}"      -> quadratic factors of the GMRES polynomial
+#include <cstdio>
+#include <vector>
+
+#include "../../paper_2108_05110_gb300/csrc/mhde_internal.h"
+
+int main() {
+  char mode[8];
+  int n;
+  while (std::scanf("%7s %d", mode, &n) == 2) {
+    if (mode[0] == 'E') {
+      std::vector<double> a((size_t)n * n), wr(n), wi(n);
+      for (auto& v : a) std::scanf("%lf", &v);
+      bool ok = mhde::eig_hessenberg(n, a.data(), wr.data(), wi.data());
+      std::printf("%d\n", ok ? 1 : 0);
+      for (int i = 0; i < n; ++i) std::printf("%.17g %.17g\n", wr[i], wi[i]);
+    } else {
+      std::vector<double> h((size_t)(n + 1) * n), c1, c2;
+      for (auto& v : h) std::scanf("%lf", &v);
+      bool ok = mhde::gmres_poly_factors(n, h.data(), c1, c2);
+      std::printf("%d %d\n", ok ? 1 : 0, (int)c1.size());
+      for (size_t i = 0; i < c1.size(); ++i) std::printf("%.17g %.17g\n", c1[i], c2[i]);
+    }
+  }
+  return 0;
+}
