@@ -45,6 +45,10 @@ def parse():
                    help="cap on the summed workspaces of the batched ensembles")
     p.add_argument("--profile-only", action="store_true",
                    help="run W warm-up and K timed steps and exit (for ncu captures)")
+    p.add_argument("--profile-kernel", type=int, default=-1,
+                   help="with --profile-only: launch only this hot-path kernel group K times "
+                        "(mhde_time_kernel ids: 0 SpMM FP64, 1 SpMM FP32, 2 F assembly, 3 RHS, "
+                        "4 means+l2, 5 preconditioner, 6 Gram)")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--N", type=int, default=WORKLOAD["N"])
     p.add_argument("--J", type=int, default=WORKLOAD["J"])
@@ -315,6 +319,12 @@ def our_arm(args, rank, world, local_rank):
     ensemble_io.feed_initial(sol, ens)
     ensemble_io.feed_step_data(sol, ens, ens.dt)     # constant lid / field data
     sol.advance(args.warmup)
+    if args.profile_only and args.profile_kernel >= 0:
+        ms = sol.time_kernel(0, args.profile_kernel, reps=max(1, args.steps))
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "kernel": args.profile_kernel, "ms": ms}), flush=True)
+        sol.close()
+        return
     if args.profile_only:
         torch.cuda.synchronize()
         sol.advance(args.steps)

@@ -163,10 +163,10 @@ size_t layout(mhde_ctx* c, char* base) {
       const size_t C2 = 2 * Jp;
       s.ibasis = w.take<char>((size_t)(kin + 1) * n2 * C2 * ks);
       s.ipart = w.take<double>((size_t)c->nchunk_in * (KIN_MAX + 2) * C2);
-      s.idot = w.take<double>((size_t)(kin + 2) * C2);
+      s.idot = w.take<double>((size_t)(KIN_MAX + 2) * C2 * 2);      // doubles, then a float copy
       s.ih = w.take<double>((size_t)(kin + 1) * kin * C2);
-      s.ibeta = w.take<double>(2 * C2);
-      s.iy = w.take<double>((size_t)kin * C2);
+      s.ibeta = w.take<double>(4 * C2);                              // beta, 1/norm, float copy of 1/norm
+      s.iy = w.take<double>((size_t)kin * C2 * 2);                   // doubles, then a float copy
       s.zbasis = w.take<char>((size_t)m * vs * ks);
       s.poly = w.take<double>(KIN_MAX + 2);
     }
@@ -256,7 +256,7 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
     return MHDE_EINVAL;
   }
   std::string e = build_fe(mesh, c->fe);
-  if (e.empty()) e = build_amg(c->fe, 256);
+  if (e.empty()) e = build_amg(c->fe, 512);
   if (!e.empty()) {
     // keep the message reachable through a NULL-safe path
     delete c;
@@ -351,6 +351,8 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   CU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CU(upload_quad_tables());
+  CU(init_inner_attributes());
+  CU(init_la_attributes());
   const FeHost& fe = c->fe;
   cudaStream_t st = c->sv;
   CU(cudaMemsetAsync(c->ws, 0, need, st));

@@ -108,6 +108,9 @@ void launch_Np(const mhde_ctx* c, const double* mean_conv, double* slots, double
 template <typename T>
 void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
                         int kin, cudaStream_t st);
+// shared-memory limits of the inner and block kernels (set once, before any capture)
+cudaError_t init_inner_attributes();
+cudaError_t init_la_attributes();
 // GMRES-polynomial approximation z ~ F^{-1} r with the factors in s.poly
 template <typename T>
 void launch_poly_apply(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,

@@ -73,7 +73,7 @@ __global__ void k_fd_spmm(int n2, int nch, const int* __restrict__ rp, const int
 // (l < nl), and part[chunk][nl][col] = sum_rows w^2 when with_norm.  A thread
 // owns 4 consecutive columns of a row (one 16-byte load per vector for FP32),
 // so many rows are in flight per CTA.
-template <typename T>
+template <typename T, int NLM>
 __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, const T* V, size_t vstride,
                                                   const T* w, int rows_per_chunk, int with_norm,
                                                   double* __restrict__ part) {
@@ -82,9 +82,10 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
   const int G = blockDim.x / C4;
   const int c4 = threadIdx.x % C4, g = threadIdx.x / C4;
   const int r0 = blockIdx.x * rows_per_chunk, r1 = min(n_rows, r0 + rows_per_chunk);
-  T acc[KIN_MAX + 2][4];
+  // acc[0..NLM-2]: dots with V_l; acc[NLM-1]: ||w||^2
+  T acc[NLM][4];
 #pragma unroll
-  for (int l = 0; l < KIN_MAX + 2; ++l)
+  for (int l = 0; l < NLM; ++l)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[l][q] = T(0);
   if (g < G) {
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
       T wv[4];
       ld4(w + o, wv);
 #pragma unroll
-      for (int l = 0; l < KIN_MAX + 1; ++l)
+      for (int l = 0; l < NLM - 1; ++l)
         if (l < nl) {
           T vv[4];
           ld4(V + (size_t)l * vstride + o, vv);
@@ -101,24 +102,32 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
           for (int q = 0; q < 4; ++q) acc[l][q] += vv[q] * wv[q];
         }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[KIN_MAX + 1][q] += wv[q] * wv[q];
+      for (int q = 0; q < 4; ++q) acc[NLM - 1][q] += wv[q] * wv[q];
     }
   }
+  // stage every group's partial sums, then one warp per (output, column)
+  // sums the G groups with a fixed shuffle tree (deterministic)
+  const int nout = nl + (with_norm ? 1 : 0);
+  float* redf = reinterpret_cast<float*>(red);
+  if (g < G) {
 #pragma unroll
-  for (int l = 0; l < KIN_MAX + 2; ++l) {
-    const bool active = (l < nl) || (l == KIN_MAX + 1 && with_norm);   // uniform over the block
-    if (!active) continue;
-    const int slot = (l < nl) ? l : nl;
-    if (g < G)
+    for (int l = 0; l < NLM; ++l) {
+      const bool active = (l < nl) || (l == NLM - 1 && with_norm);
+      if (!active) continue;
+      const int slot = (l < nl) ? l : nl;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) red[g * C + 4 * c4 + q] = (double)acc[l][q];
-    __syncthreads();
-    if (threadIdx.x < C) {
-      double sum = 0.0;
-      for (int h = 0; h < G; ++h) sum += red[h * C + threadIdx.x];
-      part[((size_t)blockIdx.x * (KIN_MAX + 2) + slot) * C + threadIdx.x] = sum;
+      for (int q = 0; q < 4; ++q) redf[((size_t)slot * G + g) * C + 4 * c4 + q] = (float)acc[l][q];
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int o = warp; o < nout * C; o += nwarp) {
+    const int slot = o / C, c = o % C;
+    float sum = 0.f;
+    for (int h = lane; h < G; h += 32) sum += redf[((size_t)slot * G + h) * C + c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) part[((size_t)blockIdx.x * (KIN_MAX + 2) + slot) * C + c] = (double)sum;
   }
 }
 
@@ -129,52 +138,54 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
 // from the Pythagorean identity, H[i+1][i] = norm, inv[col] = 1/norm;
 // mode 2: initial norms beta[col], inv[col] = 1/beta; mode 3: single pass,
 // H[l][i] = h and the norm as in mode 1.
-constexpr int RED_T = 128;
+constexpr int RED_T = 32 * (KIN_MAX + 2);
 
 __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl, int kin,
                                                       const double* __restrict__ part, double* __restrict__ dots,
                                                       int mode, int i, double* __restrict__ H,
                                                       double* __restrict__ beta, double* __restrict__ inv) {
-  __shared__ double sh[KIN_MAX + 2][RED_T];
+  __shared__ double sh[KIN_MAX + 2];
   const int c = blockIdx.x;
   const int nout = nl + ((mode == 1 || mode == 3) ? 1 : 0);
-  for (int l = 0; l < nout; ++l) {
+  const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
+  if (l < nout) {
     double s = 0.0;
-    for (int ch = threadIdx.x; ch < nchunk; ch += RED_T) s += part[((size_t)ch * (KIN_MAX + 2) + l) * C + c];
-    sh[l][threadIdx.x] = s;
+    for (int ch = lane; ch < nchunk; ch += 32) s += part[((size_t)ch * (KIN_MAX + 2) + l) * C + c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) sh[l] = s;
   }
   __syncthreads();
-  for (int w = RED_T / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int l = 0; l < nout; ++l) sh[l][threadIdx.x] += sh[l][threadIdx.x + w];
-    __syncthreads();
-  }
   if (threadIdx.x != 0) return;
   double ss = 0.0;
-  for (int l = 0; l < nl; ++l) {
-    const double s = sh[l][0];
-    dots[(size_t)l * C + c] = s;
-    ss += s * s;
-    if (mode == 0 || mode == 3) H[((size_t)l * kin + i) * C + c] = s;
-    if (mode == 1) H[((size_t)l * kin + i) * C + c] += s;
+  float* dotsf = reinterpret_cast<float*>(dots + (size_t)(KIN_MAX + 2) * C);
+  for (int t = 0; t < nl; ++t) {
+    const double sv = sh[t];
+    dots[(size_t)t * C + c] = sv;
+    dotsf[(size_t)t * C + c] = (float)sv;
+    ss += sv * sv;
+    if (mode == 0 || mode == 3) H[((size_t)t * kin + i) * C + c] = sv;
+    if (mode == 1) H[((size_t)t * kin + i) * C + c] += sv;
   }
   if (mode == 1 || mode == 3) {
-    const double n2v = sh[nl][0] - ss;
+    const double n2v = sh[nl] - ss;
     const double nrm = n2v > 0.0 ? sqrt(n2v) : 0.0;
     H[((size_t)(i + 1) * kin + i) * C + c] = nrm;
     inv[c] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    reinterpret_cast<float*>(inv + C)[c] = (float)inv[c];
   } else if (mode == 2) {
-    const double b = sh[0][0] > 0.0 ? sqrt(sh[0][0]) : 0.0;
+    const double b = sh[0] > 0.0 ? sqrt(sh[0]) : 0.0;
     beta[c] = b;
     inv[c] = b > 0.0 ? 1.0 / b : 0.0;
+    reinterpret_cast<float*>(inv + C)[c] = (float)inv[c];
   }
 }
 
 // out[row][col] = (in[row][col] - sum_l V_l[row][col] dots[l][col]) * scale[col]
 // (in and out may alias; nl may be 0); 4 consecutive entries per thread
 template <typename T>
-__global__ void k_col_update(int n_rows, int C, int nl, const T* V, size_t vstride, const double* __restrict__ dots,
-                             const T* in, T* out, const double* __restrict__ scale) {
+__global__ void k_col_update(int n_rows, int C, int nl, const T* V, size_t vstride, const T* __restrict__ dots,
+                             const T* in, T* out, const T* __restrict__ scale) {
   long long t4 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long n = (long long)n_rows * C;
   if (4 * t4 >= n) return;
@@ -186,11 +197,11 @@ __global__ void k_col_update(int n_rows, int C, int nl, const T* V, size_t vstri
     T vv[4];
     ld4(V + (size_t)l * vstride + o, vv);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] -= vv[q] * (T)dots[(size_t)l * C + c0 + q];
+    for (int q = 0; q < 4; ++q) acc[q] -= vv[q] * dots[(size_t)l * C + c0 + q];
   }
   if (scale)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] *= (T)scale[c0 + q];
+    for (int q = 0; q < 4; ++q) acc[q] *= scale[c0 + q];
   st4(out + o, acc);
 }
 
@@ -228,12 +239,14 @@ __global__ void k_col_lsq(int C, int kin, const double* __restrict__ H, const do
     for (int j = i + 1; j < kin; ++j) sum -= h[i][j] * y[(size_t)j * C + c];
     y[(size_t)i * C + c] = h[i][i] != 0.0 ? sum / h[i][i] : 0.0;
   }
+  float* yf = reinterpret_cast<float*>(y + (size_t)kin * C);
+  for (int i = 0; i < kin; ++i) yf[(size_t)i * C + c] = (float)y[(size_t)i * C + c];
 }
 
 // z[row][col] = dinv[row] * sum_l V_l[row][col] y[l][col]; 4 entries per thread
 template <typename T>
 __global__ void k_col_final(int n_rows, int C, int kin, const T* __restrict__ V, size_t vstride,
-                            const double* __restrict__ y, const T* __restrict__ dinv, T* __restrict__ z) {
+                            const T* __restrict__ y, const T* __restrict__ dinv, T* __restrict__ z) {
   long long t4 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long n = (long long)n_rows * C;
   if (4 * t4 >= n) return;
@@ -245,12 +258,48 @@ __global__ void k_col_final(int n_rows, int C, int kin, const T* __restrict__ V,
     T vv[4];
     ld4(V + (size_t)l * vstride + o, vv);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += vv[q] * (T)y[(size_t)l * C + c0 + q];
+    for (int q = 0; q < 4; ++q) acc[q] += vv[q] * y[(size_t)l * C + c0 + q];
   }
   const T d = dinv[row];
 #pragma unroll
   for (int q = 0; q < 4; ++q) acc[q] *= d;
   st4(z + o, acc);
+}
+
+template <typename T>
+static void col_dots(int nchunk, int threads, size_t shm, cudaStream_t st, int n_rows, int C, int nl, const T* V,
+                     size_t vstride, const T* w, int rows_per_chunk, int with_norm, double* part) {
+  if (nl + 1 <= 2)
+    k_col_dots<T, 2><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm, part);
+  else if (nl + 1 <= 4)
+    k_col_dots<T, 4><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm, part);
+  else if (nl + 1 <= 8)
+    k_col_dots<T, 8><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm, part);
+  else if (nl + 1 <= 12)
+    k_col_dots<T, 12><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm, part);
+  else
+    k_col_dots<T, KIN_MAX + 2><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm,
+                                                               part);
+}
+
+template <typename T>
+static cudaError_t dots_attr() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  };
+  set((const void*)k_col_dots<T, 2>);
+  set((const void*)k_col_dots<T, 4>);
+  set((const void*)k_col_dots<T, 8>);
+  set((const void*)k_col_dots<T, 12>);
+  set((const void*)k_col_dots<T, KIN_MAX + 2>);
+  return e;
+}
+
+cudaError_t init_inner_attributes() {
+  cudaError_t e = dots_attr<float>();
+  if (e != cudaSuccess) return e;
+  return dots_attr<double>();
 }
 
 template <typename T>
@@ -262,28 +311,33 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* d
   const int nchunk = c->nchunk_in;
   const int rows_per_chunk = (n2 + nchunk - 1) / nchunk;
   const int threads = (256 / (C / 4)) * (C / 4);          // whole row groups of C/4 threads
-  const size_t shm = (size_t)(threads / (C / 4)) * C * sizeof(double);
+  const size_t shm = (size_t)(kin + 2) * (threads / (C / 4)) * C * sizeof(float);
+
   T* Vb = (T*)s.ibasis;
   const long long nel = (long long)n2 * C;
+  const bool f32 = sizeof(T) == 4;
+  const T* dotsT = f32 ? (const T*)(s.idot + (size_t)(KIN_MAX + 2) * C) : (const T*)s.idot;
+  const T* invT = f32 ? (const T*)(s.ibeta + 2 * C) : (const T*)(s.ibeta + C);
+  const T* yT = f32 ? (const T*)(s.iy + (size_t)kin * C) : (const T*)s.iy;
   count_launch(3 + 4 * kin + 2);
   // beta = ||r||, v_0 = r / beta
-  k_col_dots<T><<<nchunk, threads, shm, st>>>(n2, C, 1, r, 0, r, rows_per_chunk, 0, s.ipart);
+  col_dots<T>(nchunk, threads, shm, st, n2, C, 1, r, 0, r, rows_per_chunk, 0, s.ipart);
   k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, 1, kin, s.ipart, s.idot, 2, 0, s.ih, s.ibeta,
                                          s.ibeta + C);
-  k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, 0, Vb, vstride, s.idot, r, Vb, s.ibeta + C);
+  k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, 0, Vb, vstride, dotsT, r, Vb, invT);
   for (int i = 0; i < kin; ++i) {
     T* vi = Vb + (size_t)i * vstride;
     T* w = Vb + (size_t)(i + 1) * vstride;
     k_fd_spmm<T><<<nb((long long)n2 * nch, 256), 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, vi, w);
     // one classical Gram-Schmidt pass: dots against v_0..v_i and ||w||^2 in a
     // single sweep; the projected norm follows from the Pythagorean identity
-    k_col_dots<T><<<nchunk, threads, shm, st>>>(n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 1, s.ipart);
+    col_dots<T>(nchunk, threads, shm, st, n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 1, s.ipart);
     k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, i + 1, kin, s.ipart, s.idot, 3, i, s.ih, s.ibeta,
                                       s.ibeta + C);
-    k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, s.idot, w, w, s.ibeta + C);
+    k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, dotsT, w, w, invT);
   }
   k_col_lsq<<<C, 32, 0, st>>>(C, kin, s.ih, s.ibeta, s.iy);
-  k_col_final<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, kin, Vb, vstride, s.iy, dinv, z);
+  k_col_final<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, kin, Vb, vstride, yT, dinv, z);
 }
 
 template void launch_inner_gmres<double>(const mhde_ctx*, const Sub&, const double*, const double*,

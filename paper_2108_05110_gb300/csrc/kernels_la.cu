@@ -333,11 +333,11 @@ constexpr int GRAM_TR = 64;
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, size_t vstride, int kblocks,
                                               const T* __restrict__ W, int n_rows, int Jp, int r,
-                                              int rows_per_chunk, double* __restrict__ part) {
+                                              int rows_per_chunk, double* __restrict__ part, int TR) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Vs = reinterpret_cast<T*>(smem_raw);
-  T* Ws = Vs + GRAM_TR * Jp;
-  double* red = reinterpret_cast<double*>(Ws + GRAM_TR * Jp);
+  T* Ws = Vs + TR * Jp;
+  double* red = reinterpret_cast<double*>(Ws + TR * Jp);
   const int nt4 = (r + 3) / 4;
   const int ntile = nt4 * nt4;
   const int G = 256 / ntile;
@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, size_t vs
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-  for (int tr0 = r0; tr0 < r1; tr0 += GRAM_TR) {
-    const int nr = min(GRAM_TR, r1 - tr0);
+  for (int tr0 = r0; tr0 < r1; tr0 += TR) {
+    const int nr = min(TR, r1 - tr0);
     const int nel = nr * Jp;                      // contiguous elements of the tile
     const T* vsrc = Vi + (size_t)tr0 * Jp;
     const T* wsrc = W + (size_t)tr0 * Jp;
@@ -399,6 +399,65 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, size_t vs
 
 // One warp per output entry: lanes stride over the chunks, then a fixed
 // butterfly of shuffles (deterministic order).
+// Pair-owned Gram: CTA (chunk, y) owns the (block i, column p) pairs
+// y*PC .. y*PC+PC-1 (pair = i r + p); a thread keeps the QM-wide row
+// G_i[p][0..QM) of at most PPT pairs in registers, W's rows are staged in
+// shared memory 32 at a time and read as broadcasts, and every V_i value is
+// loaded exactly once.  Writes the same per-chunk partials as k_gram.
+constexpr int GRAM2_TR = 32;
+
+template <typename T, int QM, int PPT>
+__global__ void __launch_bounds__(256) k_gram_pairs(const T* __restrict__ V, size_t vstride, int kblocks,
+                                                    const T* __restrict__ W, int n_rows, int ld, int r,
+                                                    int rows_per_chunk, double* __restrict__ part) {
+  __shared__ __align__(16) T Ws[GRAM2_TR][QM];
+  const int r0 = blockIdx.x * rows_per_chunk;
+  const int r1 = min(n_rows, r0 + rows_per_chunk);
+  const int npairs = kblocks * r;
+  int pi[PPT], pp[PPT];
+  bool own[PPT];
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    const int pair = (blockIdx.y * PPT + s) * blockDim.x + threadIdx.x;
+    own[s] = pair < npairs;
+    pi[s] = own[s] ? pair / r : 0;
+    pp[s] = own[s] ? pair % r : 0;
+  }
+  T acc[PPT][QM];
+#pragma unroll
+  for (int s = 0; s < PPT; ++s)
+#pragma unroll
+    for (int q = 0; q < QM; ++q) acc[s][q] = T(0);
+  for (int t0 = r0; t0 < r1; t0 += GRAM2_TR) {
+    const int nr = min(GRAM2_TR, r1 - t0);
+    for (int e = threadIdx.x; e < GRAM2_TR * QM; e += blockDim.x) {
+      const int rr = e / QM, q = e % QM;
+      Ws[rr][q] = (rr < nr && q < r) ? W[(size_t)(t0 + rr) * ld + q] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+      if (!own[s]) continue;
+      const T* vcol = V + (size_t)pi[s] * vstride + (size_t)t0 * ld + pp[s];
+#pragma unroll 4
+      for (int rr = 0; rr < nr; ++rr) {
+        const T v = vcol[(size_t)rr * ld];
+#pragma unroll
+        for (int q = 0; q < QM; ++q) acc[s][q] += v * Ws[rr][q];
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    if (!own[s]) continue;
+    double* dst = part + (((size_t)blockIdx.x * kblocks) + pi[s]) * r * r + (size_t)pp[s] * r;
+#pragma unroll
+    for (int q = 0; q < QM; ++q)
+      if (q < r) dst[q] = (double)acc[s][q];
+  }
+}
+
 __global__ void k_gram_reduce(int nchunk, int total, const double* __restrict__ part,
                               double* __restrict__ gram) {
   const int o = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -411,12 +470,20 @@ __global__ void k_gram_reduce(int nchunk, int total, const double* __restrict__ 
   if (lane == 0) gram[o] = s;
 }
 
+// rows per staged tile: at least 64 and four per thread group, so narrow
+// blocks (few tiles, many groups) keep every thread busy
+static int gram_tile_rows(int r) {
+  int nt4 = (r + 3) / 4;
+  int G = 256 / (nt4 * nt4);
+  return std::max(GRAM_TR, 4 * G);
+}
+
 template <typename T>
 static size_t gram_smem(int Jp, int r) {
   int nt4 = (r + 3) / 4;
   int ntile = nt4 * nt4;
   int G = 256 / ntile;
-  return 2 * (size_t)GRAM_TR * Jp * sizeof(T) + (size_t)G * ntile * 16 * sizeof(double);
+  return 2 * (size_t)gram_tile_rows(r) * Jp * sizeof(T) + (size_t)G * ntile * 16 * sizeof(double);
 }
 
 template <typename T>
@@ -429,69 +496,124 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
     attr_set = true;
   }
   int rows_per_chunk = (n_rows + nchunk - 1) / nchunk;
-  size_t shmem = gram_smem<T>(Jp, r);
-  k_gram<T><<<dim3(nchunk, kblocks), 256, shmem, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, rows_per_chunk,
-                                                        part);
+  const int npairs = kblocks * r;
+  if (r <= 32 && npairs >= 256 && sizeof(T) == 4) {
+    constexpr int PPT = 2;
+    const unsigned gy = (unsigned)((npairs + 256 * PPT - 1) / (256 * PPT));
+#define MHDE_GP(QMV)                                                                                  \
+  k_gram_pairs<T, QMV, PPT><<<dim3(nchunk, gy), 256, 0, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, \
+                                                              rows_per_chunk, part)
+    if (r <= 4)
+      MHDE_GP(4);
+    else if (r <= 8)
+      MHDE_GP(8);
+    else if (r <= 16)
+      MHDE_GP(16);
+    else if (r <= 24)
+      MHDE_GP(24);
+    else
+      MHDE_GP(32);
+#undef MHDE_GP
+  } else {
+    size_t shmem = gram_smem<T>(Jp, r);
+    k_gram<T><<<dim3(nchunk, kblocks), 256, shmem, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, rows_per_chunk,
+                                                          part, gram_tile_rows(r));
+  }
   int total = kblocks * r * r;
   k_gram_reduce<<<(total + 7) / 8, 256, 0, st>>>(nchunk, total, part, gram);
 }
 
 // ------------------------------------------------------------ block combine
 // out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q].
-// One thread per row keeps the QMAX output columns in registers; the
-// coefficient blocks are staged in shared memory in groups that fit 48 KB and
-// read as broadcast vector loads.
+// A CTA owns 128 consecutive rows: each block's 128 x r_in tile is staged in
+// shared memory with coalesced loads (odd row pitch: no bank conflicts),
+// coefficient blocks are staged in groups and read as broadcasts, and a
+// thread accumulates the QMAX outputs of its row in registers.  out may alias
+// one of the V blocks (each row is read completely before it is written).
+constexpr int COMB_T = 128;
+
 template <typename T, int QMAX>
-__global__ void __launch_bounds__(128) k_block_combine(T* __restrict__ out, const T* __restrict__ in, T alpha,
-                                                       const T* __restrict__ V, size_t vstride, int kblocks,
-                                                       int r_in, const T* __restrict__ C, int r_out,
-                                                       int n_rows, int ldv, int Jp, int kgroup) {
+__global__ void __launch_bounds__(COMB_T) k_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride,
+                                                          int kblocks, int r_in, const T* __restrict__ C, int r_out,
+                                                          int n_rows, int ldv, int Jp, int kgroup, int pitch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Cs = reinterpret_cast<T*>(smem_raw);           // [kgroup * r_in][QMAX]
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  T* Cs = reinterpret_cast<T*>(smem_raw);                       // [kgroup][r_in][QMAX]
+  T* Vt = Cs + (size_t)kgroup * r_in * QMAX;                    // [COMB_T][pitch]
+  const int row0 = blockIdx.x * COMB_T;
+  const int row = row0 + threadIdx.x;
   T acc[QMAX];
 #pragma unroll
   for (int q = 0; q < QMAX; ++q) acc[q] = T(0);
   for (int i0 = 0; i0 < kblocks; i0 += kgroup) {
-    const int nb = min(kgroup, kblocks - i0);
+    const int nbk = min(kgroup, kblocks - i0);
     __syncthreads();
-    for (int e = threadIdx.x; e < nb * r_in * QMAX; e += blockDim.x) {
-      int q = e % QMAX, pi = e / QMAX;             // pi = ib * r_in + p
-      int ib = pi / r_in, p = pi % r_in;
+    for (int e = threadIdx.x; e < nbk * r_in * QMAX; e += COMB_T) {
+      const int q = e % QMAX, pi = e / QMAX;
+      const int ib = pi / r_in, p = pi % r_in;
       Cs[e] = (q < r_out) ? C[((size_t)(i0 + ib) * r_in + p) * r_out + q] : T(0);
     }
-    __syncthreads();
-    if (row < n_rows) {
-      for (int ib = 0; ib < nb; ++ib) {
-        const T* vr = V + (size_t)(i0 + ib) * vstride + (size_t)row * ldv;
-        const T* cb = Cs + (size_t)ib * r_in * QMAX;
-        for (int p = 0; p < r_in; ++p) {
-          const T v = vr[p];
-          const T* cp = cb + p * QMAX;
+    for (int ib = 0; ib < nbk; ++ib) {
+      __syncthreads();
+      const T* Vi = V + (size_t)(i0 + ib) * vstride;
+      for (int e = threadIdx.x; e < COMB_T * r_in; e += COMB_T) {
+        const int rr = e / r_in, p = e % r_in;
+        Vt[rr * pitch + p] = (row0 + rr < n_rows) ? Vi[(size_t)(row0 + rr) * ldv + p] : T(0);
+      }
+      __syncthreads();
+      const T* cb = Cs + (size_t)ib * r_in * QMAX;
+      const T* vr = Vt + threadIdx.x * pitch;
+      for (int p = 0; p < r_in; ++p) {
+        const T v = vr[p];
+        const T* cp = cb + p * QMAX;
 #pragma unroll
-          for (int q = 0; q < QMAX; ++q) acc[q] += v * cp[q];
-        }
+        for (int q = 0; q < QMAX; ++q) acc[q] += v * cp[q];
       }
     }
   }
   if (row >= n_rows) return;
   T* orow = out + (size_t)row * Jp;
   const T* irow = in ? in + (size_t)row * Jp : nullptr;
+  T res[QMAX];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) res[q] = (q < r_out) ? (irow ? alpha * irow[q] : T(0)) + acc[q] : T(0);
 #pragma unroll
   for (int q = 0; q < QMAX; ++q)
-    if (q < Jp) orow[q] = (q < r_out) ? (irow ? alpha * irow[q] : T(0)) + acc[q] : T(0);
+    if (q < Jp) orow[q] = res[q];
   for (int q = QMAX; q < Jp; ++q) orow[q] = T(0);
 }
 
 template <typename T, int QMAX>
 static void combine_q(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
                       const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st) {
+  const int pitch = (r_in % 2 == 0) ? r_in + 1 : r_in + 2;
   const size_t per_block = (size_t)r_in * QMAX * sizeof(T);
-  int kgroup = (int)std::max<size_t>(1, (48 * 1024) / std::max<size_t>(per_block, 1));
+  int kgroup = (int)std::max<size_t>(1, (32 * 1024) / std::max<size_t>(per_block, 1));
   kgroup = std::min(kgroup, std::max(kblocks, 1));
-  size_t shmem = (size_t)kgroup * per_block;
-  k_block_combine<T, QMAX><<<nblk(n_rows, 128), 128, shmem, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C,
-                                                                  r_out, n_rows, ldv, Jp, kgroup);
+  const size_t shmem = (size_t)kgroup * per_block + (size_t)COMB_T * pitch * sizeof(T);
+  k_block_combine<T, QMAX><<<nblk(n_rows, COMB_T), COMB_T, shmem, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C,
+                                                                       r_out, n_rows, ldv, Jp, kgroup, pitch);
+}
+
+template <typename T>
+static cudaError_t combine_attr() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  };
+  set((const void*)k_block_combine<T, 4>);
+  set((const void*)k_block_combine<T, 8>);
+  set((const void*)k_block_combine<T, 16>);
+  set((const void*)k_block_combine<T, 24>);
+  set((const void*)k_block_combine<T, 32>);
+  set((const void*)k_block_combine<T, 48>);
+  set((const void*)k_block_combine<T, 64>);
+  return e;
+}
+
+cudaError_t init_la_attributes() {
+  cudaError_t e = combine_attr<float>();
+  if (e != cudaSuccess) return e;
+  return combine_attr<double>();
 }
 
 template <typename T>
