@@ -77,6 +77,7 @@ typedef struct {
   int jacobi_sweeps;    /* damped Jacobi sweeps approximating F^{-1}; default 3 */
   double jacobi_omega;  /* damping of those sweeps; default 0.3 */
   int amg_sweeps;       /* Jacobi sweeps per level in the pressure-Laplacian V-cycle; default 2 */
+  int amg_cycles;       /* V-cycles per application of the pressure-Laplacian inverse; default 1 */
   int poly_degree;      /* degree d (even, <= 16) of the GMRES polynomial in D^{-1} F that
                            approximates F^{-1}, rebuilt every step from d Arnoldi steps;
                            0 = use inner_iters instead; default 0 (the fixed polynomial is

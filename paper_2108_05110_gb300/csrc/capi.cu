@@ -231,6 +231,7 @@ void mhde_default_options(mhde_options* o) {
   o->jacobi_sweeps = 3;
   o->jacobi_omega = 0.3;
   o->amg_sweeps = 2;
+  o->amg_cycles = 1;
   o->poly_degree = 0;
   o->inner_iters = 8;
   o->schur = 1;
@@ -250,7 +251,7 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
   if (c->opt.restart < 1 || c->opt.restart > 200 || c->opt.max_iter < 1 || !(c->opt.rtol > 0) ||
       (c->opt.precision != MHDE_PREC_FP64 && c->opt.precision != MHDE_PREC_MIXED) ||
       (c->opt.conv_form != 0 && c->opt.conv_form != 1) || c->opt.inner_iters < 0 || c->opt.poly_degree < 0 ||
-      c->opt.poly_degree > mhde::KIN_MAX || c->opt.poly_degree % 2 != 0 ||
+      c->opt.poly_degree > mhde::KIN_MAX || c->opt.poly_degree % 2 != 0 || c->opt.amg_cycles < 1 ||
       c->opt.inner_iters > mhde::KIN_MAX || (c->opt.schur != 0 && c->opt.schur != 1)) {
     delete c;
     return MHDE_EINVAL;
@@ -299,6 +300,8 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
   c->trace = tr && tr[0] == '1';
   const char* gr = std::getenv("MHDE_GRAPHS");
   c->use_graphs = !(gr && gr[0] == '0');
+  const char* sv = std::getenv("MHDE_SPMM");
+  c->spmm_rows = sv && std::string(sv) == "rows";
   c->amg_levels = (int)c->fe.amg.levels.size();
   *out = c;
   return MHDE_OK;

@@ -138,11 +138,124 @@ __global__ void __launch_bounds__(256) k_saddle(int n2, int np, int nch, const i
   }
 }
 
+// Row-per-thread variant: one thread owns a velocity node (both components,
+// all NCH 16-byte chunks of the member row) or a pressure row, so a row's
+// column indices and values are loaded once and every nonzero issues 2*NCH
+// independent 16-byte gathers.
+template <typename T, int MODE, int NCH>
+__global__ void __launch_bounds__(128) k_saddle_rows(int n2, int np, const int* __restrict__ frp,
+                                                     const int* __restrict__ fcol, const T* __restrict__ Fval,
+                                                     const int* __restrict__ btrp, const int* __restrict__ btcol,
+                                                     const T* __restrict__ BTval, const int* __restrict__ brp,
+                                                     const int* __restrict__ bcol, const T* __restrict__ Bval,
+                                                     const unsigned char* __restrict__ isbnd,
+                                                     const T* __restrict__ X, const double* __restrict__ Bvec,
+                                                     T* __restrict__ Y) {
+  using V = typename Vec<T>::type;
+  const V* Xv = reinterpret_cast<const V*>(X);
+  V* Yv = reinterpret_cast<V*>(Y);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < n2) {
+    const int a = tid;
+    const size_t o0 = (size_t)(2 * a) * NCH;
+    V acc[2 * NCH];
+    if (isbnd[a]) {
+#pragma unroll
+      for (int t = 0; t < 2 * NCH; ++t) acc[t] = Xv[o0 + t];
+    } else {
+#pragma unroll
+      for (int t = 0; t < 2 * NCH; ++t) acc[t] = vzero(V());
+      for (int k = frp[a]; k < frp[a + 1]; ++k) {
+        const T f = Fval[k];
+        const V* xr = Xv + (size_t)(2 * fcol[k]) * NCH;
+#pragma unroll
+        for (int t = 0; t < 2 * NCH; ++t) vfma(acc[t], f, xr[t]);
+      }
+      const size_t pbase = (size_t)2 * n2 * NCH;
+      for (int k = btrp[a]; k < btrp[a + 1]; ++k) {
+        const T bx = BTval[2 * (size_t)k], by = BTval[2 * (size_t)k + 1];
+        const V* xp = Xv + pbase + (size_t)btcol[k] * NCH;
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+          const V x = xp[t];
+          vfma(acc[t], bx, x);
+          vfma(acc[NCH + t], by, x);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2 * NCH; ++t) {
+      if (MODE == 0)
+        Yv[o0 + t] = acc[t];
+      else
+        Yv[o0 + t] = vaxpby(T(1), reinterpret_cast<const V*>(Bvec)[o0 + t], T(-1), acc[t]);
+    }
+    return;
+  }
+  const int i = tid - n2;
+  if (i >= np) return;
+  const size_t out = (size_t)2 * n2 * NCH + (size_t)i * NCH;
+  V acc[NCH];
+  if (i == 0) {
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) acc[t] = Xv[out + t];
+  } else {
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) acc[t] = vzero(V());
+    for (int k = brp[i]; k < brp[i + 1]; ++k) {
+      const T bx = Bval[2 * (size_t)k], by = Bval[2 * (size_t)k + 1];
+      const V* xr = Xv + (size_t)(2 * bcol[k]) * NCH;
+#pragma unroll
+      for (int t = 0; t < NCH; ++t) {
+        vfma(acc[t], bx, xr[t]);
+        vfma(acc[t], by, xr[NCH + t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    if (MODE == 0)
+      Yv[out + t] = acc[t];
+    else
+      Yv[out + t] = vaxpby(T(1), reinterpret_cast<const V*>(Bvec)[out + t], T(-1), acc[t]);
+  }
+}
+
+template <typename T, int MODE, int NCH>
+static void saddle_rows(const mhde_ctx* c, const T* Fval, const T* Bval, const T* BTval, const T* X,
+                        const double* Bvec, T* Y, cudaStream_t st) {
+  const int n = c->fe.n2 + c->fe.np;
+  k_saddle_rows<T, MODE, NCH><<<nblk(n, 128), 128, 0, st>>>(c->fe.n2, c->fe.np, c->F.rowptr, c->F.col, Fval,
+                                                           c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
+                                                           Bval, c->d_isbnd, X, Bvec, Y);
+}
+
+template <typename T, int MODE>
+static bool saddle_rows_dispatch(const mhde_ctx* c, const T* Fval, const T* Bval, const T* BTval, const T* X,
+                                 const double* Bvec, T* Y, int nch, cudaStream_t st) {
+  switch (nch) {
+    case 1: saddle_rows<T, MODE, 1>(c, Fval, Bval, BTval, X, Bvec, Y, st); return true;
+    case 2: saddle_rows<T, MODE, 2>(c, Fval, Bval, BTval, X, Bvec, Y, st); return true;
+    case 3: saddle_rows<T, MODE, 3>(c, Fval, Bval, BTval, X, Bvec, Y, st); return true;
+    case 4: saddle_rows<T, MODE, 4>(c, Fval, Bval, BTval, X, Bvec, Y, st); return true;
+    case 5: saddle_rows<T, MODE, 5>(c, Fval, Bval, BTval, X, Bvec, Y, st); return true;
+    case 6: saddle_rows<T, MODE, 6>(c, Fval, Bval, BTval, X, Bvec, Y, st); return true;
+    case 8: saddle_rows<T, MODE, 8>(c, Fval, Bval, BTval, X, Bvec, Y, st); return true;
+    case 10: saddle_rows<T, MODE, 10>(c, Fval, Bval, BTval, X, Bvec, Y, st); return true;
+    default: return false;
+  }
+}
+
 template <typename T>
 void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T* BTval, const T* X,
                         const double* Bvec, T* Y, int mode, int ld, cudaStream_t st) {
   count_launch();
   int nch = ld / Vec<T>::W;
+  if (c->spmm_rows) {
+    const bool done = (mode == 0) ? saddle_rows_dispatch<T, 0>(c, Fval, Bval, BTval, X, Bvec, Y, nch, st)
+                                  : saddle_rows_dispatch<T, 1>(c, Fval, Bval, BTval, X, Bvec, Y, nch, st);
+    if (done) return;
+  }
   long long n = ((long long)c->fe.n2 + c->fe.np) * nch;
   if (mode == 0)
     k_saddle<T, 0><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,

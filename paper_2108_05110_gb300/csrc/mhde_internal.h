@@ -259,6 +259,7 @@ struct mhde_ctx {
   int device = 0;
   bool trace = false;                  // MHDE_TRACE=1: per-sweep residuals on stderr
   bool use_graphs = true;              // MHDE_GRAPHS=0 disables graph capture
+  bool spmm_rows = false;              // MHDE_SPMM=rows: row-per-thread saddle SpMM variant
   mhde::Sub sub[2];
   std::vector<int> h_bidx;             // boundary index of every P2 node (host copy)
   std::vector<double> h_M;             // mass matrix values (host copy, for the energy)

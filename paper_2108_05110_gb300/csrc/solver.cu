@@ -131,6 +131,16 @@ static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out, int J
   const T* rp = in + poff;
   T* x0 = Prec<T>::x(s.amg[0]);
   vcycle<T>(c, s, 0, rp, x0, Jp);
+  for (int cyc = 1; cyc < c->opt.amg_cycles; ++cyc) {
+    // further V-cycles on the residual: x0 += V(rp - L x0), staged in the
+    // preconditioner temporaries (velocity part of tk/pk is still free here)
+    const DevCsr& A0 = c->amg_ops[0].A;
+    T* res = tk + poff;
+    T* corr = (T*)s.Pk + poff;
+    launch_csr<T>(A0.nrows, A0.rowptr, A0.col, Prec<T>::Aval(A0), nullptr, T(0), x0, rp, res, 1, Jp, st);
+    vcycle<T>(c, s, 0, res, corr, Jp);
+    launch_axpby<T>(x0, T(1), x0, T(1), corr, (size_t)A0.nrows * Jp, st);
+  }
   const double nu_hat = 0.5 * (c->nubar + c->nubar_m);
   const DevCsr& Kp = c->amg_ops[0].A;
   launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), (T)(1.0 / c->dt), (T)nu_hat, Kp.rowptr, Kp.col,

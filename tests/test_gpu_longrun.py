@@ -31,10 +31,12 @@ def reference():
     return ens, snaps
 
 
-@pytest.mark.parametrize("precision,tol", [(PREC_MIXED, 1e-8), (PREC_FP64, 1e-10)])
-def test_hundred_steps(reference, precision, tol):
+@pytest.mark.parametrize("precision,tol,rtol", [(PREC_MIXED, 1e-8, 1e-12), (PREC_FP64, 1e-10, 1e-13)])
+def test_hundred_steps(reference, precision, tol, rtol):
+    # per-step solver residuals accumulate over the run: the FP64 path keeps
+    # its 1e-10 gate over 100 steps with rtol = 1e-13 (1e-12 gives ~1.4e-10)
     ens, snaps = reference
-    sol = ensemble_io.solver_for(ens, precision=precision)
+    sol = ensemble_io.solver_for(ens, precision=precision, rtol=rtol)
     ensemble_io.feed_initial(sol, ens)
     ensemble_io.feed_step_data(sol, ens, ens.dt)
     for n in range(1, NSTEPS + 1):
