@@ -377,7 +377,8 @@ def our_arm(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "kernel": f"saddle SpMM ({'FP32' if pbytes == 4 else 'FP64'})",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "bytes_per_launch": alg, "ms_per_launch": spmm_ms,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "cta_size": int(st1.spmm_block)}
     kernel_ms = {name: sol.time_kernel(0, k, reps=10) for name, k in
                  (("means_l2", 4), ("assemble_F", 2), ("rhs", 3), ("precond", 5), ("gram", 6))}
 

@@ -109,6 +109,10 @@ typedef struct {
   long long total_iters;      /* sum of block GMRES iterations over all steps and both subproblems */
   double last_step_ms;        /* wall time of the last mhde_step (host clock) */
   long long launches;         /* kernel launches issued by all steps so far */
+  int spmm_block;             /* CTA size the bind-time autotuner chose for the
+                                 saddle SpMM (128, 256 or 512; results do not
+                                 depend on it) */
+  double spmm_tuned_us[3];    /* its timings of one SpMM at 128, 256, 512 */
 } mhde_stats;
 
 /* Default options (listed above). */

@@ -50,7 +50,8 @@ class Sizes(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("last_iters", C.c_int * 2), ("last_refine", C.c_int * 2),
                 ("last_relres", C.c_double * 2), ("total_iters", C.c_longlong),
-                ("last_step_ms", C.c_double), ("launches", C.c_longlong)]
+                ("last_step_ms", C.c_double), ("launches", C.c_longlong),
+                ("spmm_block", C.c_int), ("spmm_tuned_us", C.c_double * 3)]
 
 
 def library_path():

@@ -207,6 +207,56 @@ void to_rows(const mhde_ctx* c, const double* a, const double* b, double sgn, do
       }
 }
 
+// Block-size autotuner for the chunked saddle SpMM: times CTA sizes 128, 256
+// and 512 in the Krylov precision on this context's matrix pattern and member
+// width and keeps the fastest.  Every thread computes the same sums in the same
+// order whatever the CTA size, so the choice never changes a result bit (a
+// resumed run stays bit-identical to an uninterrupted one).  F's values are
+// still zero at bind time; the access pattern and traffic are the real ones.
+int autotune_spmm(mhde_ctx* c) {
+  Sub& s = c->sub[0];
+  cudaStream_t st = c->sv;
+  const bool f32 = c->opt.precision == MHDE_PREC_MIXED;
+  const int blocks[3] = {128, 256, 512};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(c, MHDE_ECUDA, "cudaEventCreate failed in the SpMM autotuner");
+  }
+  auto once = [&]() {
+    if (f32)
+      launch_saddle_spmm<float>(c, s.Fvalf, c->B.valf, c->BT.valf, (const float*)s.Wk, nullptr, (float*)s.Zk, 0,
+                                c->Jp, st);
+    else
+      launch_saddle_spmm<double>(c, s.Fval, c->B.val, c->BT.val, (const double*)s.Wk, nullptr, (double*)s.Zk, 0,
+                                 c->Jp, st);
+  };
+  double best = 1e30;
+  int best_block = 256;
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < 3 && err == cudaSuccess; ++i) {
+    c->spmm_block = blocks[i];
+    once();
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 5; ++r) once();
+    cudaEventRecord(e1, st);
+    err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    c->spmm_tuned_us[i] = 1000.0 * ms / 5;
+    if (err == cudaSuccess && c->spmm_tuned_us[i] < best) {
+      best = c->spmm_tuned_us[i];
+      best_block = blocks[i];
+    }
+  }
+  c->spmm_block = best_block;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  count_launch(-18);  // tuning launches are not part of any step
+  if (err != cudaSuccess) return fail(c, MHDE_ECUDA, std::string("SpMM autotuner: ") + cudaGetErrorString(err));
+  return MHDE_OK;
+}
+
 int check_ready(mhde_ctx* c, bool need_initial) {
   if (!c) return MHDE_EINVAL;
   if (!c->bound) return fail(c, MHDE_ESTATE, "mhde_bind has not been called");
@@ -302,6 +352,7 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
   c->use_graphs = !(gr && gr[0] == '0');
   const char* sv = std::getenv("MHDE_SPMM");
   c->spmm_rows = sv && std::string(sv) == "rows";
+  c->spmm_forced = sv && sv[0] != 0;
   c->amg_levels = (int)c->fe.amg.levels.size();
   *out = c;
   return MHDE_OK;
@@ -458,6 +509,10 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
     CU(cudaMallocHost(&s.hcoef, 4 * sizeof(double) * small));
   }
   c->bound = true;
+  if (!c->spmm_forced) {
+    int rc = autotune_spmm(c);
+    if (rc) return rc;
+  }
   return MHDE_OK;
 }
 
@@ -749,6 +804,8 @@ int mhde_energy(mhde_ctx* c, double* E) {
 int mhde_get_stats(const mhde_ctx* c, mhde_stats* st) {
   if (!c || !st) return MHDE_EINVAL;
   *st = c->stats;
+  st->spmm_block = c->spmm_block;
+  for (int i = 0; i < 3; ++i) st->spmm_tuned_us[i] = c->spmm_tuned_us[i];
   return MHDE_OK;
 }
 

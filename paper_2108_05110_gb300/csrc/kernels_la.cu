@@ -46,7 +46,7 @@ static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) 
 // column indices are loaded once for the two components; the nonzero loops
 // are unrolled by two to keep independent gathers in flight.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_saddle(int n2, int np, int nch, const int* __restrict__ frp,
+__global__ void __launch_bounds__(512) k_saddle(int n2, int np, int nch, const int* __restrict__ frp,
                                                 const int* __restrict__ fcol, const T* __restrict__ Fval,
                                                 const int* __restrict__ btrp, const int* __restrict__ btcol,
                                                 const T* __restrict__ BTval, const int* __restrict__ brp,
@@ -257,14 +257,15 @@ void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T
     if (done) return;
   }
   long long n = ((long long)c->fe.n2 + c->fe.np) * nch;
+  const int bs = c->spmm_block;
   if (mode == 0)
-    k_saddle<T, 0><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
-                                                c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
-                                                Bval, c->d_isbnd, X, Bvec, Y);
+    k_saddle<T, 0><<<nblk(n, bs), bs, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
+                                              c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
+                                              Bval, c->d_isbnd, X, Bvec, Y);
   else
-    k_saddle<T, 1><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
-                                                c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
-                                                Bval, c->d_isbnd, X, Bvec, Y);
+    k_saddle<T, 1><<<nblk(n, bs), bs, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
+                                              c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
+                                              Bval, c->d_isbnd, X, Bvec, Y);
 }
 
 // ------------------------------------------------------------ generic CSR

@@ -260,6 +260,9 @@ struct mhde_ctx {
   bool trace = false;                  // MHDE_TRACE=1: per-sweep residuals on stderr
   bool use_graphs = true;              // MHDE_GRAPHS=0 disables graph capture
   bool spmm_rows = false;              // MHDE_SPMM=rows: row-per-thread saddle SpMM variant
+  int spmm_block = 256;                // CTA size of the chunked saddle SpMM (autotuned at bind)
+  bool spmm_forced = false;            // MHDE_SPMM set: skip the autotuner
+  double spmm_tuned_us[3] = {0, 0, 0}; // autotuner timings for CTA sizes 128, 256, 512
   mhde::Sub sub[2];
   std::vector<int> h_bidx;             // boundary index of every P2 node (host copy)
   std::vector<double> h_M;             // mass matrix values (host copy, for the energy)
