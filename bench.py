@@ -380,7 +380,8 @@ def our_arm(args, rank, world, local_rank):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "cta_size": int(st1.spmm_block)}
     kernel_ms = {name: sol.time_kernel(0, k, reps=10) for name, k in
-                 (("means_l2", 4), ("assemble_F", 2), ("rhs", 3), ("precond", 5), ("gram", 6))}
+                 (("means_l2", 4), ("assemble_F", 2), ("rhs", 3), ("precond", 5), ("gram", 6),
+                  ("combine", 7))}
 
     # end to end through the public API with host buffers
     xy = sol._nodes

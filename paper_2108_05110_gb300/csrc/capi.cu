@@ -152,7 +152,7 @@ size_t layout(mhde_ctx* c, char* base) {
     s.Rk = w.take<char>(vs * ks);
     s.Dk = w.take<char>(vs * ks);
     s.part = w.take<double>((size_t)c->nchunk * (m + 1) * c->J * c->J);
-    s.gram = w.take<double>((size_t)(m + 1) * c->J * c->J);
+    s.gram = w.take<double>((size_t)(m + 2) * c->J * c->J + 8);   // m + 1 blocks, then two traces
     s.coef = w.take<char>(4 * (size_t)(m + 1) * c->J * c->J * 8);
     s.colsq = w.take<double>((size_t)c->nchunk * Jp);
     s.dscale = w.take<double>(2 * Jp);
@@ -346,6 +346,8 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
   }
   c->nchunk = std::max(1, std::min(304, (c->n_rows + 255) / 256));
   c->nchunk_in = std::max(1, std::min(1024, (c->fe.n2 + 127) / 128));
+  const char* se = std::getenv("MHDE_SERIAL");
+  c->serial = se && se[0] == '1';
   const char* tr = std::getenv("MHDE_TRACE");
   c->trace = tr && tr[0] == '1';
   const char* gr = std::getenv("MHDE_GRAPHS");
@@ -501,7 +503,7 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   c->h_M.resize(fe.F.nnz());
   CU(cudaMemcpy(c->h_M.data(), c->d_M, sizeof(double) * fe.F.nnz(), cudaMemcpyDeviceToHost));
   // pinned host staging
-  const size_t small = (size_t)(c->opt.restart + 1) * c->J * c->J;
+  const size_t small = (size_t)(c->opt.restart + 2) * c->J * c->J + 8;
   for (int which = 0; which < 2; ++which) {
     Sub& s = c->sub[which];
     CU(cudaMallocHost((void**)&s.hbuf, sizeof(double) * small));
@@ -612,10 +614,16 @@ int mhde_step(mhde_ctx* c) {
   CU(cudaGetLastError());
   CU(cudaEventRecord(c->ev_fork, c->sv));
   CU(cudaStreamWaitEvent(c->sw, c->ev_fork, 0));
-  // the two subproblems run concurrently on their own streams
-  std::thread tw([c]() { run_sub(c, 1); });
-  run_sub(c, 0);
-  tw.join();
+  // the two subproblems run concurrently on their own streams (one after the
+  // other with MHDE_SERIAL=1, for per-phase timing without interference)
+  if (c->serial) {
+    run_sub(c, 0);
+    run_sub(c, 1);
+  } else {
+    std::thread tw([c]() { run_sub(c, 1); });
+    run_sub(c, 0);
+    tw.join();
+  }
   for (int which = 0; which < 2; ++which) {
     if (c->sub[which].status != MHDE_OK) {
       c->err = std::string(which == 0 ? "v" : "w") + " subproblem: " + c->sub[which].err;
@@ -976,7 +984,7 @@ int mhde_probe_spmm(mhde_ctx* c, int which, int precision, const double* X, doub
 int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
   int rc = probe_assemble(c, which);
   if (rc) return rc;
-  if (!ms || reps < 1 || kernel < 0 || kernel > 6) return fail(c, MHDE_EINVAL, "bad kernel id, reps or ms");
+  if (!ms || reps < 1 || kernel < 0 || kernel > 7) return fail(c, MHDE_EINVAL, "bad kernel id, reps or ms");
   Sub& s = c->sub[which];
   cudaStream_t st = s.stream;
   const size_t vs = (size_t)c->n_rows * c->Jp;
@@ -990,12 +998,13 @@ int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
   if (fp64 && (kernel == 5 || kernel == 6))
     CU(cudaMemcpyAsync(s.Wk, xd, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const int kb = std::max(1, c->opt.restart / 2);
-  if (kernel == 6) {
+  if (kernel == 6 || kernel == 7) {
     // fill kb basis blocks with copies of the input
     for (int i = 0; i < kb; ++i)
       CU(cudaMemcpyAsync((char*)s.basis + (size_t)i * vs * ksize(c), s.Wk, vs * ksize(c),
                          cudaMemcpyDeviceToDevice, st));
   }
+  if (kernel == 7) CU(cudaMemsetAsync(s.coef, 0, (size_t)kb * c->J * c->J * sizeof(double), st));
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
@@ -1036,6 +1045,9 @@ int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
         break;
       case 6:
         gram_any(c, which, s.basis, vs, kb, s.Wk);
+        break;
+      case 7:
+        combine_any(c, which, s.basis, vs, kb, s.Zk);
         break;
     }
   };

@@ -517,81 +517,103 @@ void BlockLS::init(int r_, int J_, int m_, const double* S0) {
   J = J_;
   m = m_;
   k = 0;
-  ldr = (m + 1) * r;
-  R.assign((size_t)ldr * m * r, 0.0);
-  hv.assign((size_t)m * r * 2 * r, 0.0);
+  ldr = m * r;
+  // every entry of R and hv that is read is written first
+  R.resize((size_t)ldr * ldr);
+  hv.resize((size_t)m * r * 2 * r);
   htau.assign((size_t)m * r, 0.0);
-  g.assign((size_t)ldr * J, 0.0);
+  g.assign((size_t)(m + 1) * r * J, 0.0);
   for (int i = 0; i < r; ++i)
-    for (int j = 0; j < J; ++j) g[(size_t)j * ldr + i] = S0[i * J + j];
+    for (int j = 0; j < J; ++j) g[(size_t)i * J + j] = S0[(size_t)i * J + j];
+  c.resize((size_t)(m + 1) * r * r);
+  s.resize((size_t)std::max(r, J));
 }
 
+// Householder QR of the block Hessenberg matrix, one block column at a time:
+// the previous reflectors are applied to the new column, then r new ones
+// (each spanning 2r rows) annihilate its subdiagonal block and are applied to
+// the right-hand sides.  Every inner loop runs over the r columns of the
+// block (or the J right-hand sides), contiguous in memory.
 bool BlockLS::add(const double* h) {
   const int rows = (k + 2) * r;
-  std::vector<double> c((size_t)rows * r);
-  for (int t = 0; t < r; ++t)
-    for (int i = 0; i < rows; ++i) c[(size_t)t * rows + i] = h[(size_t)t * rows + i];
-  // previous reflectors
+  std::copy(h, h + (size_t)rows * r, c.begin());
+  double* sv = s.data();
   for (int col = 0; col < k * r; ++col) {
-    int blk = col / r;
-    int lo = col, hi = (blk + 2) * r;       // rows [lo, hi)
-    const double* v = &hv[(size_t)col * 2 * r];
-    double tau = htau[col];
+    const double tau = htau[col];
     if (tau == 0.0) continue;
-    for (int t = 0; t < r; ++t) {
-      double* x = &c[(size_t)t * rows];
-      double s = 0.0;
-      for (int i = lo; i < hi; ++i) s += v[i - lo] * x[i];
-      s *= tau;
-      for (int i = lo; i < hi; ++i) x[i] -= s * v[i - lo];
+    const int lo = col, len = (col / r + 2) * r - col;
+    const double* v = &hv[(size_t)col * 2 * r];
+    for (int t = 0; t < r; ++t) sv[t] = 0.0;
+    for (int i = 0; i < len; ++i) {
+      const double a = v[i];
+      const double* row = &c[(size_t)(lo + i) * r];
+      for (int t = 0; t < r; ++t) sv[t] += a * row[t];
+    }
+    for (int t = 0; t < r; ++t) sv[t] *= tau;
+    for (int i = 0; i < len; ++i) {
+      const double a = v[i];
+      double* row = &c[(size_t)(lo + i) * r];
+      for (int t = 0; t < r; ++t) row[t] -= a * sv[t];
     }
   }
-  // new reflectors for this block column
   bool ok = true;
   for (int t = 0; t < r; ++t) {
-    int col = k * r + t;
-    int lo = col, hi = (k + 2) * r;
-    double* x = &c[(size_t)t * rows];
-    double alpha = x[lo], nrm2 = 0.0;
-    for (int i = lo; i < hi; ++i) nrm2 += x[i] * x[i];
-    double nrm = std::sqrt(nrm2);
+    const int col = k * r + t;
+    const int lo = col, hi = (k + 2) * r, len = hi - lo;
     double* v = &hv[(size_t)col * 2 * r];
     for (int i = 0; i < 2 * r; ++i) v[i] = 0.0;
+    const double alpha = c[(size_t)lo * r + t];
+    double nrm2 = 0.0;
+    for (int i = lo; i < hi; ++i) nrm2 += c[(size_t)i * r + t] * c[(size_t)i * r + t];
+    const double nrm = std::sqrt(nrm2);
     if (nrm == 0.0) {
       htau[col] = 0.0;
       ok = false;
       continue;
     }
-    double beta = (alpha >= 0) ? -nrm : nrm;
+    const double beta = (alpha >= 0) ? -nrm : nrm;
+    const double denom = alpha - beta;
     v[0] = 1.0;
-    double denom = alpha - beta;
-    for (int i = lo + 1; i < hi; ++i) v[i - lo] = x[i] / denom;
-    double tau = (beta - alpha) / beta;
+    for (int i = lo + 1; i < hi; ++i) v[i - lo] = c[(size_t)i * r + t] / denom;
+    const double tau = (beta - alpha) / beta;
     htau[col] = tau;
-    x[lo] = beta;
-    for (int i = lo + 1; i < hi; ++i) x[i] = 0.0;
-    for (int t2 = t + 1; t2 < r; ++t2) {
-      double* y = &c[(size_t)t2 * rows];
-      double s = 0.0;
-      for (int i = lo; i < hi; ++i) s += v[i - lo] * y[i];
-      s *= tau;
-      for (int i = lo; i < hi; ++i) y[i] -= s * v[i - lo];
+    c[(size_t)lo * r + t] = beta;
+    for (int i = lo + 1; i < hi; ++i) c[(size_t)i * r + t] = 0.0;
+    // the remaining columns of this block
+    if (t + 1 < r) {
+      for (int t2 = t + 1; t2 < r; ++t2) sv[t2] = 0.0;
+      for (int i = 0; i < len; ++i) {
+        const double a = v[i];
+        const double* row = &c[(size_t)(lo + i) * r];
+        for (int t2 = t + 1; t2 < r; ++t2) sv[t2] += a * row[t2];
+      }
+      for (int t2 = t + 1; t2 < r; ++t2) sv[t2] *= tau;
+      for (int i = 0; i < len; ++i) {
+        const double a = v[i];
+        double* row = &c[(size_t)(lo + i) * r];
+        for (int t2 = t + 1; t2 < r; ++t2) row[t2] -= a * sv[t2];
+      }
     }
-    for (int j = 0; j < J; ++j) {
-      double* y = &g[(size_t)j * ldr];
-      double s = 0.0;
-      for (int i = lo; i < hi; ++i) s += v[i - lo] * y[i];
-      s *= tau;
-      for (int i = lo; i < hi; ++i) y[i] -= s * v[i - lo];
+    // the right-hand sides
+    for (int j = 0; j < J; ++j) sv[j] = 0.0;
+    for (int i = 0; i < len; ++i) {
+      const double a = v[i];
+      const double* row = &g[(size_t)(lo + i) * J];
+      for (int j = 0; j < J; ++j) sv[j] += a * row[j];
+    }
+    for (int j = 0; j < J; ++j) sv[j] *= tau;
+    for (int i = 0; i < len; ++i) {
+      const double a = v[i];
+      double* row = &g[(size_t)(lo + i) * J];
+      for (int j = 0; j < J; ++j) row[j] -= a * sv[j];
     }
   }
-  for (int t = 0; t < r; ++t)
-    for (int i = 0; i < (k + 1) * r; ++i)
-      R[(size_t)(k * r + t) * ldr + i] = c[(size_t)t * rows + i];
+  for (int i = 0; i < (k + 1) * r; ++i)
+    std::copy(&c[(size_t)i * r], &c[(size_t)i * r] + r, &R[(size_t)i * ldr + (size_t)k * r]);
   double dmax = 0.0;
   for (int i = 0; i < (k + 1) * r; ++i) dmax = std::max(dmax, std::fabs(R[(size_t)i * ldr + i]));
   for (int t = 0; t < r; ++t) {
-    double d = std::fabs(R[(size_t)(k * r + t) * ldr + k * r + t]);
+    const double d = std::fabs(R[(size_t)(k * r + t) * ldr + k * r + t]);
     if (!(d > 1e-14 * dmax)) ok = false;
   }
   k++;
@@ -599,21 +621,26 @@ bool BlockLS::add(const double* h) {
 }
 
 double BlockLS::resid(int j) const {
-  double s = 0.0;
-  for (int i = k * r; i < (k + 1) * r; ++i) s += g[(size_t)j * ldr + i] * g[(size_t)j * ldr + i];
-  return std::sqrt(s);
+  double acc = 0.0;
+  for (int i = k * r; i < (k + 1) * r; ++i) acc += g[(size_t)i * J + j] * g[(size_t)i * J + j];
+  return std::sqrt(acc);
 }
 
+// Back substitution for all right-hand sides at once (inner loop over J).
 void BlockLS::solve(std::vector<double>& Y) const {
   const int n = k * r;
   Y.assign((size_t)n * J, 0.0);
-  for (int j = 0; j < J; ++j) {
-    for (int i = n - 1; i >= 0; --i) {
-      double s = g[(size_t)j * ldr + i];
-      for (int c = i + 1; c < n; ++c) s -= R[(size_t)c * ldr + i] * Y[(size_t)c * J + j];
-      double d = R[(size_t)i * ldr + i];
-      Y[(size_t)i * J + j] = (d != 0.0) ? s / d : 0.0;
+  for (int i = n - 1; i >= 0; --i) {
+    double* y = &Y[(size_t)i * J];
+    for (int j = 0; j < J; ++j) y[j] = g[(size_t)i * J + j];
+    const double* Ri = &R[(size_t)i * ldr];
+    for (int cc = i + 1; cc < n; ++cc) {
+      const double a = Ri[cc];
+      const double* yc = &Y[(size_t)cc * J];
+      for (int j = 0; j < J; ++j) y[j] -= a * yc[j];
     }
+    const double d = Ri[i];
+    for (int j = 0; j < J; ++j) y[j] = (d != 0.0) ? y[j] / d : 0.0;
   }
 }
 

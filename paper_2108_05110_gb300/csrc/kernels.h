@@ -76,6 +76,12 @@ void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
                  int nchunk, double* part, double* gram, cudaStream_t st);
+// G = [H_0 .. H_k, W^T W] (r x r blocks) -> block k+1 := W^T W - sum_i H_i^T H_i,
+// then trace(W^T W) and the projected trace at G[(k+2) r r], G[(k+2) r r + 1]
+void launch_proj_gram(double* G, int k, int r, cudaStream_t st);
+// C_i = -H_i T (i <= k), C_{k+1} = T, converted to the Krylov precision
+template <typename T>
+void launch_make_coef(const double* G, const double* Tm, int k, int r, T* C, cudaStream_t st);
 // out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q], q < r_out; 0 beyond
 // (V rows have stride ldv, in/out rows stride Jp)
 template <typename T>
@@ -122,5 +128,6 @@ int solve_sub(mhde_ctx* c, int which);
 // benchmark helpers in the context's Krylov precision
 void precond_apply_any(mhde_ctx* c, int which, const void* in, void* out);
 void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W);
+void combine_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, void* out);
 
 }  // namespace mhde

@@ -7,6 +7,7 @@
 // a row are broadcast to the threads sharing that row.
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -33,6 +34,23 @@ __device__ __forceinline__ double2 vaxpby(double a, const double2& x, double b, 
 }
 __device__ __forceinline__ float4 vaxpby(float a, const float4& x, float b, const float4& y) {
   return make_float4(a * x.x + b * y.x, a * x.y + b * y.y, a * x.z + b * y.z, a * x.w + b * y.w);
+}
+
+// four consecutive entries of a row (16-byte aligned for float, 32-byte for double)
+__device__ __forceinline__ void row_ld4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void row_ld4(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void row_st4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void row_st4(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -308,25 +326,49 @@ void launch_csr(int nrows, const int* rowptr, const int* col, const T* val, cons
   k_csr<T><<<nblk(n, 256), 256, 0, st>>>(nrows, nch, rowptr, col, val, dinv, omega, x, b, y, mode);
 }
 
+__device__ __forceinline__ void warp_sum(double2& a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
+  }
+}
+__device__ __forceinline__ void warp_sum(float4& a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
+    a.z += __shfl_xor_sync(0xffffffffu, a.z, off);
+    a.w += __shfl_xor_sync(0xffffffffu, a.w, off);
+  }
+}
+
+// y = A x for a dense n x n matrix (the coarsest AMG level's inverse): one
+// warp per (row, 16-byte chunk); lanes stride over k with coalesced reads of
+// the row and finish with a fixed butterfly of shuffles (deterministic).
 template <typename T>
-__global__ void k_dense_apply(int n, int nch, const T* __restrict__ A, const T* __restrict__ x,
-                              T* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_dense_apply(int n, int nch, const T* __restrict__ A,
+                                                     const T* __restrict__ x, T* __restrict__ y) {
   using V = typename Vec<T>::type;
-  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= (long long)n * nch) return;
-  int r = (int)(tid / nch), ch = (int)(tid % nch);
+  const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)n * nch) return;          // whole warps exit together
+  const int r = (int)(wid / nch), ch = (int)(wid % nch);
   const V* xv = reinterpret_cast<const V*>(x);
+  const T* arow = A + (size_t)r * n;
   V acc = vzero(V());
-  for (int k = 0; k < n; ++k) vfma(acc, A[(size_t)r * n + k], xv[(size_t)k * nch + ch]);
-  reinterpret_cast<V*>(y)[(size_t)r * nch + ch] = acc;
+#pragma unroll 4
+  for (int k = lane; k < n; k += 32) vfma(acc, arow[k], xv[(size_t)k * nch + ch]);
+  warp_sum(acc);
+  if (lane == 0) reinterpret_cast<V*>(y)[(size_t)r * nch + ch] = acc;
 }
 
 template <typename T>
 void launch_dense_apply(int n, const T* Ainv, const T* x, T* y, int Jp, cudaStream_t st) {
   count_launch();
   int nch = Jp / Vec<T>::W;
-  long long m = (long long)n * nch;
-  k_dense_apply<T><<<nblk(m, 128), 128, 0, st>>>(n, nch, Ainv, x, y);
+  long long threads = (long long)n * nch * 32;
+  k_dense_apply<T><<<nblk(threads, 256), 256, 0, st>>>(n, nch, Ainv, x, y);
 }
 
 // ------------------------------------------------------------ preconditioner pieces
@@ -511,8 +553,6 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, size_t vs
   }
 }
 
-// One warp per output entry: lanes stride over the chunks, then a fixed
-// butterfly of shuffles (deterministic order).
 // Pair-owned Gram: CTA (chunk, y) owns the (block i, column p) pairs
 // y*PC .. y*PC+PC-1 (pair = i r + p); a thread keeps the QM-wide row
 // G_i[p][0..QM) of at most PPT pairs in registers, W's rows are staged in
@@ -572,16 +612,188 @@ __global__ void __launch_bounds__(256) k_gram_pairs(const T* __restrict__ V, siz
   }
 }
 
-__global__ void k_gram_reduce(int nchunk, int total, const double* __restrict__ part,
-                              double* __restrict__ gram) {
-  const int o = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (o >= total) return;
+// Sum of the per-chunk partials: a CTA owns 32 consecutive outputs; each of
+// its 8 warps sums every 8th chunk for them (coalesced 256-byte reads), then
+// the 8 partial sums are added in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_gram_reduce(int nparts, int total, const double* __restrict__ part,
+                                                     double* __restrict__ gram) {
+  __shared__ double sh[8][33];
+  const int lo = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lo;
   double s = 0.0;
-  for (int c = lane; c < nchunk; c += 32) s += part[(size_t)c * total + o];
+  if (o < total) {
+#pragma unroll 4
+    for (int c = g; c < nparts; c += 8) s += part[(size_t)c * total + o];
+  }
+  sh[g][lo] = s;
+  __syncthreads();
+  if (g == 0 && o < total) {
+    double v = 0.0;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) gram[o] = s;
+    for (int h = 0; h < 8; ++h) v += sh[h][lo];
+    gram[o] = v;
+  }
+}
+
+// Staged Gram (FP32): a CTA owns a range of rows and streams it through a
+// GS_NST-deep ring of shared-memory stages with cp.async; one stage holds TR
+// rows of every basis block and of W (each block's rows are contiguous in
+// memory, so every copy is a coalesced 16-byte piece).  A thread owns one item
+// (basis block i, 4-column group p4) and keeps its 4 x W products in
+// registers; the W row is a shared-memory broadcast.  A block's tile is
+// padded so that consecutive items read consecutive 16-byte words (no bank
+// conflicts).  With few items a CTA runs S row slices, each writing its own
+// partial, so every sum has a fixed order.
+constexpr int GS_T = 256;
+constexpr int GS_NST = 3;
+constexpr size_t GS_SMEM = 192 * 1024;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int W>
+__global__ void __launch_bounds__(GS_T) k_gram_staged(const float* __restrict__ V, size_t vstride, int kblocks,
+                                                      const float* __restrict__ Wm, int n_rows, int ld, int r,
+                                                      int rows_per_chunk, int S, int TR, int tstride,
+                                                      double* __restrict__ part) {
+  extern __shared__ __align__(16) float gsm[];
+  const int stage_floats = kblocks * tstride + TR * ld;
+  const int P4 = (r + 3) / 4;
+  const int items = kblocks * P4;
+  const int slice = threadIdx.x / items, item = threadIdx.x % items;
+  const bool active = slice < S;
+  const int i = item / P4, p4 = item % P4;
+  const int r0 = blockIdx.x * rows_per_chunk, r1 = min(n_rows, r0 + rows_per_chunk);
+  const int ntiles = r1 > r0 ? (r1 - r0 + TR - 1) / TR : 0;
+  auto issue = [&](int tile) {
+    if (tile < ntiles) {
+      float* st = gsm + (size_t)(tile % GS_NST) * stage_floats;
+      const int t0 = r0 + tile * TR;
+      const int nseg = min(TR, r1 - t0) * ld / 4;      // 16-byte pieces of one block's rows
+      const int total = (kblocks + 1) * nseg;
+      for (int e = threadIdx.x; e < total; e += GS_T) {
+        const int b = e / nseg, off = e - b * nseg;
+        const float* src = (b < kblocks ? V + (size_t)b * vstride : Wm) + (size_t)t0 * ld + 4 * off;
+        cp_async16(st + (size_t)b * tstride + 4 * off, src);
+      }
+    }
+    cp_async_commit();                                  // one group per tile, possibly empty
+  };
+  float acc[4][W];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int q = 0; q < W; ++q) acc[e][q] = 0.f;
+#pragma unroll
+  for (int s = 0; s < GS_NST - 1; ++s) issue(s);
+  for (int tile = 0; tile < ntiles; ++tile) {
+    cp_async_wait<GS_NST - 2>();                        // this thread's copies of `tile` landed
+    __syncthreads();                                    // everyone's did; stage tile-1 is free
+    issue(tile + GS_NST - 1);
+    if (active) {
+      const float* st = gsm + (size_t)(tile % GS_NST) * stage_floats;
+      const int nr = min(TR, r1 - (r0 + tile * TR));
+      const float* vt = st + (size_t)i * tstride + 4 * p4;
+      const float* wt = st + (size_t)kblocks * tstride;
+#pragma unroll 2
+      for (int rr = slice; rr < nr; rr += S) {
+        float v[4];
+        row_ld4(vt + rr * ld, v);
+#pragma unroll
+        for (int q4 = 0; q4 < W / 4; ++q4) {
+          float w[4];
+          row_ld4(wt + rr * ld + 4 * q4, w);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[e][4 * q4 + u] = fmaf(v[e], w[u], acc[e][4 * q4 + u]);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (!active) return;
+  double* dst = part + ((size_t)(blockIdx.x * S + slice) * kblocks + i) * r * r;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int pr = 4 * p4 + e;
+    if (pr >= r) break;
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+      if (q < r) dst[(size_t)pr * r + q] = (double)acc[e][q];
+  }
+}
+
+// Stage geometry of the staged Gram: rows per stage (a multiple of 8, at most
+// 128) so that GS_NST stages fit in GS_SMEM, and the padded block-tile stride.
+static bool gram_staged_plan(int kblocks, int ld, int r, int& TR, int& tstride, size_t& smem) {
+  const int P4 = (r + 3) / 4;
+  for (TR = 128; TR >= 8; TR -= 8) {
+    const int pad = ((4 * P4 - TR * ld) % 32 + 32) % 32;
+    tstride = TR * ld + pad;
+    smem = (size_t)GS_NST * ((size_t)kblocks * tstride + (size_t)TR * ld) * sizeof(float);
+    if (smem <= GS_SMEM) return true;
+  }
+  return false;
+}
+
+template <int W>
+static void gram_staged(const float* V, size_t vstride, int kblocks, const float* Wm, int n_rows, int ld, int r,
+                        int nchunk, int nsm, int TR, int tstride, size_t smem, double* part, cudaStream_t st,
+                        int& nparts) {
+  const int items = kblocks * ((r + 3) / 4);
+  const int S = std::max(1, std::min(GS_T / items, nchunk));
+  const int nctas = std::max(1, std::min(nchunk / S, nsm));
+  const int rows_per_chunk = (n_rows + nctas - 1) / nctas;
+  nparts = nctas * S;
+  k_gram_staged<W><<<nctas, GS_T, smem, st>>>(V, vstride, kblocks, Wm, n_rows, ld, r, rows_per_chunk, S, TR,
+                                             tstride, part);
+}
+
+// Per-device one-time setup of the Gram kernels (shared-memory limits and the
+// SM count that sizes the staged grid), done under a mutex because the two
+// subproblems call in from their own host threads.
+struct GramDevice {
+  bool ready = false;
+  int nsm = 1;
+  cudaError_t err = cudaSuccess;
+};
+static std::mutex g_gram_mutex;
+static GramDevice g_gram_dev[64];
+
+static const GramDevice& gram_setup() {
+  static GramDevice none;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    none.err = cudaErrorInvalidDevice;
+    return none;
+  }
+  std::lock_guard<std::mutex> lock(g_gram_mutex);
+  GramDevice& d = g_gram_dev[dev];
+  if (d.ready) return d;
+  cudaError_t e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (d.nsm <= 0) d.nsm = 1;
+  auto set = [&](const void* f, int bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  set((const void*)k_gram_staged<4>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<8>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<12>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<16>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<20>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<24>, (int)GS_SMEM);
+  set((const void*)k_gram<float>, 160 * 1024);
+  set((const void*)k_gram<double>, 160 * 1024);
+  d.err = e;
+  d.ready = true;
+  return d;
 }
 
 // rows per staged tile: at least 64 and four per thread group, so narrow
@@ -600,154 +812,258 @@ static size_t gram_smem(int Jp, int r) {
   return 2 * (size_t)gram_tile_rows(r) * Jp * sizeof(T) + (size_t)G * ntile * 16 * sizeof(double);
 }
 
+// Partial sums go to part[nchunk][kblocks][r][r] at most (nchunk bounds the
+// scratch the caller provides), then one reduction.
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
                  int nchunk, double* part, double* gram, cudaStream_t st) {
   count_launch(2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr_set = true;
-  }
-  int rows_per_chunk = (n_rows + nchunk - 1) / nchunk;
-  const int npairs = kblocks * r;
-  if (r <= 32 && npairs >= 256 && sizeof(T) == 4) {
-    constexpr int PPT = 2;
-    const unsigned gy = (unsigned)((npairs + 256 * PPT - 1) / (256 * PPT));
+  const GramDevice& gd = gram_setup();               // on failure the unstaged kernels run instead
+  const int items = kblocks * ((r + 3) / 4);
+  const int w = (r + 3) / 4 * 4;
+  int nparts = nchunk;
+  int TR = 0, tstride = 0;
+  size_t smem = 0;
+  const bool staged = gd.err == cudaSuccess && sizeof(T) == 4 && items <= GS_T && w <= 24 &&
+                      gram_staged_plan(kblocks, Jp, r, TR, tstride, smem);
+  if (staged) {
+    const float* Vf = reinterpret_cast<const float*>(V);
+    const float* Wf = reinterpret_cast<const float*>(W);
+#define MHDE_GS(WV) \
+  gram_staged<WV>(Vf, vstride, kblocks, Wf, n_rows, Jp, r, nchunk, gd.nsm, TR, tstride, smem, part, st, nparts)
+    switch (w) {
+      case 4: MHDE_GS(4); break;
+      case 8: MHDE_GS(8); break;
+      case 12: MHDE_GS(12); break;
+      case 16: MHDE_GS(16); break;
+      case 20: MHDE_GS(20); break;
+      default: MHDE_GS(24); break;
+    }
+#undef MHDE_GS
+  } else {
+    const int rows_per_chunk = (n_rows + nchunk - 1) / nchunk;
+    const int npairs = kblocks * r;
+    if (r <= 32 && npairs >= 256 && sizeof(T) == 4) {
+      constexpr int PPT = 2;
+      const unsigned gy = (unsigned)((npairs + 256 * PPT - 1) / (256 * PPT));
 #define MHDE_GP(QMV)                                                                                  \
   k_gram_pairs<T, QMV, PPT><<<dim3(nchunk, gy), 256, 0, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, \
                                                               rows_per_chunk, part)
-    if (r <= 4)
-      MHDE_GP(4);
-    else if (r <= 8)
-      MHDE_GP(8);
-    else if (r <= 16)
-      MHDE_GP(16);
-    else if (r <= 24)
-      MHDE_GP(24);
-    else
-      MHDE_GP(32);
+      if (r <= 4)
+        MHDE_GP(4);
+      else if (r <= 8)
+        MHDE_GP(8);
+      else if (r <= 16)
+        MHDE_GP(16);
+      else if (r <= 24)
+        MHDE_GP(24);
+      else
+        MHDE_GP(32);
 #undef MHDE_GP
+    } else {
+      size_t shmem = gram_smem<T>(Jp, r);
+      k_gram<T><<<dim3(nchunk, kblocks), 256, shmem, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, rows_per_chunk,
+                                                            part, gram_tile_rows(r));
+    }
+  }
+  const int total = kblocks * r * r;
+  k_gram_reduce<<<(total + 31) / 32, 256, 0, st>>>(nparts, total, part, gram);
+}
+
+// ------------------------------------------------------------ one-reduce Gram-Schmidt helpers
+// G holds H_0 .. H_k (H_i = V_i^T W) and W^T W as r x r blocks.  Block k + 1
+// becomes the projected Gram W^T W - sum_i H_i^T H_i (each entry one fixed-order
+// sum over i, t), followed by trace(W^T W) and the projected trace.  One CTA.
+__global__ void k_proj_gram(double* G, int k, int r) {
+  const int rr = r * r;
+  double* Gw = G + (size_t)(k + 1) * rr;
+  __shared__ double trw;
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int p = 0; p < r; ++p) acc += Gw[p * r + p];
+    trw = acc;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < rr; o += blockDim.x) {
+    const int p = o / r, q = o % r;
+    double acc = 0.0;
+    for (int i = 0; i <= k; ++i) {
+      const double* Hi = G + (size_t)i * rr;
+      for (int t = 0; t < r; ++t) acc = fma(Hi[t * r + p], Hi[t * r + q], acc);
+    }
+    Gw[o] -= acc;                                  // each thread reads only its own entry of the block
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int p = 0; p < r; ++p) acc += Gw[p * r + p];
+    G[(size_t)(k + 2) * rr] = trw;
+    G[(size_t)(k + 2) * rr + 1] = acc;
+  }
+}
+
+void launch_proj_gram(double* G, int k, int r, cudaStream_t st) {
+  count_launch();
+  const int threads = std::min(1024, std::max(32, (r * r + 31) / 32 * 32));
+  k_proj_gram<<<1, threads, 0, st>>>(G, k, r);
+}
+
+// Coefficients of V_{k+1} = (W - sum_i V_i H_i) T for the block combination:
+// C_i = -H_i T (i <= k) and C_{k+1} = T, in the Krylov precision.
+template <typename T>
+__global__ void k_make_coef(const double* __restrict__ G, const double* __restrict__ Tm, int k, int r,
+                            T* __restrict__ C) {
+  const int rr = r * r;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= (k + 2) * rr) return;
+  const int i = o / rr, pq = o % rr, p = pq / r, q = pq % r;
+  double v;
+  if (i <= k) {
+    const double* Hi = G + (size_t)i * rr;
+    double acc = 0.0;
+    for (int t = 0; t < r; ++t) acc = fma(Hi[p * r + t], Tm[t * r + q], acc);
+    v = -acc;
   } else {
-    size_t shmem = gram_smem<T>(Jp, r);
-    k_gram<T><<<dim3(nchunk, kblocks), 256, shmem, st>>>(V, vstride, kblocks, W, n_rows, Jp, r, rows_per_chunk,
-                                                          part, gram_tile_rows(r));
+    v = Tm[pq];
   }
-  int total = kblocks * r * r;
-  k_gram_reduce<<<(total + 7) / 8, 256, 0, st>>>(nchunk, total, part, gram);
-}
-
-// ------------------------------------------------------------ block combine
-// out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q].
-// A CTA owns 128 consecutive rows: each block's 128 x r_in tile is staged in
-// shared memory with coalesced loads (odd row pitch: no bank conflicts),
-// coefficient blocks are staged in groups and read as broadcasts, and a
-// thread accumulates the QMAX outputs of its row in registers.  out may alias
-// one of the V blocks (each row is read completely before it is written).
-constexpr int COMB_T = 128;
-
-template <typename T, int QMAX>
-__global__ void __launch_bounds__(COMB_T) k_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride,
-                                                          int kblocks, int r_in, const T* __restrict__ C, int r_out,
-                                                          int n_rows, int ldv, int Jp, int kgroup, int pitch) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Cs = reinterpret_cast<T*>(smem_raw);                       // [kgroup][r_in][QMAX]
-  T* Vt = Cs + (size_t)kgroup * r_in * QMAX;                    // [COMB_T][pitch]
-  const int row0 = blockIdx.x * COMB_T;
-  const int row = row0 + threadIdx.x;
-  T acc[QMAX];
-#pragma unroll
-  for (int q = 0; q < QMAX; ++q) acc[q] = T(0);
-  for (int i0 = 0; i0 < kblocks; i0 += kgroup) {
-    const int nbk = min(kgroup, kblocks - i0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nbk * r_in * QMAX; e += COMB_T) {
-      const int q = e % QMAX, pi = e / QMAX;
-      const int ib = pi / r_in, p = pi % r_in;
-      Cs[e] = (q < r_out) ? C[((size_t)(i0 + ib) * r_in + p) * r_out + q] : T(0);
-    }
-    for (int ib = 0; ib < nbk; ++ib) {
-      __syncthreads();
-      const T* Vi = V + (size_t)(i0 + ib) * vstride;
-      for (int e = threadIdx.x; e < COMB_T * r_in; e += COMB_T) {
-        const int rr = e / r_in, p = e % r_in;
-        Vt[rr * pitch + p] = (row0 + rr < n_rows) ? Vi[(size_t)(row0 + rr) * ldv + p] : T(0);
-      }
-      __syncthreads();
-      const T* cb = Cs + (size_t)ib * r_in * QMAX;
-      const T* vr = Vt + threadIdx.x * pitch;
-      for (int p = 0; p < r_in; ++p) {
-        const T v = vr[p];
-        const T* cp = cb + p * QMAX;
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) acc[q] += v * cp[q];
-      }
-    }
-  }
-  if (row >= n_rows) return;
-  T* orow = out + (size_t)row * Jp;
-  const T* irow = in ? in + (size_t)row * Jp : nullptr;
-  T res[QMAX];
-#pragma unroll
-  for (int q = 0; q < QMAX; ++q) res[q] = (q < r_out) ? (irow ? alpha * irow[q] : T(0)) + acc[q] : T(0);
-#pragma unroll
-  for (int q = 0; q < QMAX; ++q)
-    if (q < Jp) orow[q] = res[q];
-  for (int q = QMAX; q < Jp; ++q) orow[q] = T(0);
-}
-
-template <typename T, int QMAX>
-static void combine_q(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
-                      const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st) {
-  const int pitch = (r_in % 2 == 0) ? r_in + 1 : r_in + 2;
-  const size_t per_block = (size_t)r_in * QMAX * sizeof(T);
-  int kgroup = (int)std::max<size_t>(1, (32 * 1024) / std::max<size_t>(per_block, 1));
-  kgroup = std::min(kgroup, std::max(kblocks, 1));
-  const size_t shmem = (size_t)kgroup * per_block + (size_t)COMB_T * pitch * sizeof(T);
-  k_block_combine<T, QMAX><<<nblk(n_rows, COMB_T), COMB_T, shmem, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C,
-                                                                       r_out, n_rows, ldv, Jp, kgroup, pitch);
+  C[o] = (T)v;
 }
 
 template <typename T>
-static cudaError_t combine_attr() {
-  cudaError_t e = cudaSuccess;
-  auto set = [&](const void* f) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-  };
-  set((const void*)k_block_combine<T, 4>);
-  set((const void*)k_block_combine<T, 8>);
-  set((const void*)k_block_combine<T, 16>);
-  set((const void*)k_block_combine<T, 24>);
-  set((const void*)k_block_combine<T, 32>);
-  set((const void*)k_block_combine<T, 48>);
-  set((const void*)k_block_combine<T, 64>);
-  return e;
+void launch_make_coef(const double* G, const double* Tm, int k, int r, T* C, cudaStream_t st) {
+  count_launch();
+  const int n = (k + 2) * r * r;
+  k_make_coef<T><<<nblk(n, 256), 256, 0, st>>>(G, Tm, k, r, C);
 }
 
-cudaError_t init_la_attributes() {
-  cudaError_t e = combine_attr<float>();
-  if (e != cudaSuccess) return e;
-  return combine_attr<double>();
+// ------------------------------------------------------------ block combine
+// out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q]  (q < r_out;
+// 0 for r_out <= q < ldo).  A thread owns RPT rows: it reads each V_i row with
+// 16-byte vector loads straight into registers (no staging, no barrier per
+// block) and keeps the W outputs of each row in registers; the coefficient
+// blocks are staged in shared memory in groups, zero-padded to W x W, and
+// read as broadcasts.  The sum runs over i, then p, in a fixed order.  out
+// may alias one V block or in: a row is read completely by its own thread
+// before that thread writes it.
+constexpr int COMB_T = 128;
+constexpr size_t COMB_SMEM = 48 * 1024;
+
+
+template <typename T, int W, int RPT>
+__global__ void __launch_bounds__(COMB_T) k_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride,
+                                                          int kblocks, int r_in, const T* __restrict__ C,
+                                                          int r_out, int n_rows, int ldv, int ldo, int kgroup) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Cs = reinterpret_cast<T*>(smem_raw);                       // [kgroup][W][W]
+  const int base = blockIdx.x * (COMB_T * RPT) + threadIdx.x;
+  const int np4 = (r_in + 3) / 4;
+  T acc[RPT][W];
+#pragma unroll
+  for (int s = 0; s < RPT; ++s)
+#pragma unroll
+    for (int q = 0; q < W; ++q) acc[s][q] = T(0);
+  for (int i0 = 0; i0 < kblocks; i0 += kgroup) {
+    const int nbk = min(kgroup, kblocks - i0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nbk * W * W; e += COMB_T) {
+      const int q = e % W, p = (e / W) % W, ib = e / (W * W);
+      Cs[e] = (p < r_in && q < r_out) ? C[((size_t)(i0 + ib) * r_in + p) * r_out + q] : T(0);
+    }
+    __syncthreads();
+    for (int ib = 0; ib < nbk; ++ib) {
+      const T* Vi = V + (size_t)(i0 + ib) * vstride;
+      const T* cb = Cs + (size_t)ib * W * W;
+#pragma unroll
+      for (int p4 = 0; p4 < W / 4; ++p4) {
+        if (p4 >= np4) break;
+        T v[RPT][4];
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+          const int row = base + s * COMB_T;
+          if (row < n_rows) {
+            row_ld4(Vi + (size_t)row * ldv + 4 * p4, v[s]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (4 * p4 + e >= r_in) v[s][e] = T(0);          // padding columns
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[s][e] = T(0);
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const T* cp = cb + (4 * p4 + e) * W;
+#pragma unroll
+          for (int q4 = 0; q4 < W / 4; ++q4) {
+            T c[4];
+            row_ld4(cp + 4 * q4, c);
+#pragma unroll
+            for (int s = 0; s < RPT; ++s)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc[s][4 * q4 + u] = fma(v[s][e], c[u], acc[s][4 * q4 + u]);
+          }
+        }
+      }
+    }
+  }
+  const int ldo4 = ldo / 4;
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) {
+    const int row = base + s * COMB_T;
+    if (row >= n_rows) continue;
+    T* orow = out + (size_t)row * ldo;
+    const T* irow = in ? in + (size_t)row * ldo : nullptr;
+#pragma unroll
+    for (int q4 = 0; q4 < W / 4; ++q4) {
+      if (q4 >= ldo4) break;
+      T res[4];
+      if (irow) {
+        row_ld4(irow + 4 * q4, res);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) res[u] = alpha * res[u] + acc[s][4 * q4 + u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) res[u] = acc[s][4 * q4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * q4 + u >= r_out) res[u] = T(0);
+      row_st4(orow + 4 * q4, res);
+    }
+    const T z[4] = {T(0), T(0), T(0), T(0)};
+    for (int q4 = W / 4; q4 < ldo4; ++q4) row_st4(orow + 4 * q4, z);
+  }
 }
+
+template <typename T, int W>
+static void combine_w(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
+                      const T* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st) {
+  constexpr int RPT = (sizeof(T) == 4 && W <= 24) ? 2 : 1;
+  const size_t per_block = (size_t)W * W * sizeof(T);
+  const int kgroup = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(kblocks, 1), COMB_SMEM / per_block));
+  const size_t shmem = (size_t)kgroup * per_block;
+  k_block_combine<T, W, RPT><<<nblk(n_rows, COMB_T * RPT), COMB_T, shmem, st>>>(
+      out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, ldo, kgroup);
+}
+
+cudaError_t init_la_attributes() { return gram_setup().err; }
 
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
                           int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st) {
   count_launch();
-  if (r_out <= 4)
-    combine_q<T, 4>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
-  else if (r_out <= 8)
-    combine_q<T, 8>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
-  else if (r_out <= 16)
-    combine_q<T, 16>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
-  else if (r_out <= 24)
-    combine_q<T, 24>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
-  else if (r_out <= 32)
-    combine_q<T, 32>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
-  else if (r_out <= 48)
-    combine_q<T, 48>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
-  else
-    combine_q<T, 64>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st);
+  const int w = std::max((r_in + 3) / 4, (r_out + 3) / 4) * 4;
+#define MHDE_CW(WV) combine_w<T, WV>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st)
+  if (w <= 4) MHDE_CW(4);
+  else if (w <= 8) MHDE_CW(8);
+  else if (w <= 12) MHDE_CW(12);
+  else if (w <= 16) MHDE_CW(16);
+  else if (w <= 20) MHDE_CW(20);
+  else if (w <= 24) MHDE_CW(24);
+  else if (w <= 32) MHDE_CW(32);
+  else if (w <= 48) MHDE_CW(48);
+  else MHDE_CW(64);
+#undef MHDE_CW
 }
 
 // out[row][q] = (T) sum_p X[row][p] C[p][q] for q < r (0 beyond), X and C in FP64:
@@ -897,6 +1213,7 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
   template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, int, cudaStream_t); \
   template void launch_gram<T>(const T*, size_t, int, const T*, int, int, int, int, double*, double*, \
                                cudaStream_t);                                                        \
+  template void launch_make_coef<T>(const double*, const double*, int, int, T*, cudaStream_t);       \
   template void launch_block_combine<T>(T*, const T*, T, const T*, size_t, int, int, const T*, int,  \
                                         int, int, int, cudaStream_t);                                \
   template void launch_colsq<T>(const T*, int, int, int, double*, cudaStream_t);                     \

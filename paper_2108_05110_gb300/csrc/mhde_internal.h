@@ -100,13 +100,14 @@ bool gmres_poly_factors(int d, const double* H, std::vector<double>& c1, std::ve
 // block width r and the right-hand side E1 S0 (S0 is r x J).
 struct BlockLS {
   int r = 0, J = 0, m = 0, k = 0;
-  std::vector<double> R;       // ((m+1) r) x (m r), column-major, leading dim ldr
-  int ldr = 0;
-  std::vector<double> hv;      // Householder vectors, 2r per column, column c at c*2r
+  int ldr = 0;                 // m r: row length of R
+  std::vector<double> R;       // (m r) x (m r), row-major, upper triangular
+  std::vector<double> hv;      // Householder vectors, 2r per reflector
   std::vector<double> htau;    // [m r]
-  std::vector<double> g;       // ((m+1) r) x J column-major, leading dim ldr
+  std::vector<double> g;       // ((m+1) r) x J, row-major: the rotated right-hand sides
+  std::vector<double> c, s;    // work: the new block column, dot products
   void init(int r_, int J_, int m_, const double* S0 /* r x J row-major */);
-  // h: ((k+2) r) x r column-major (leading dim (k+2) r) = new block column.
+  // h: ((k+2) r) x r row-major = the new block column [H_0; ...; H_k; S_{k+1}].
   // Returns false on a (numerically) singular diagonal.
   bool add(const double* h);
   // residual norm of right-hand-side column j after the last add
@@ -137,6 +138,7 @@ struct DevAmgLevel {
 
 struct Sub {                       // one subproblem (v: which = 0, w: which = 1)
   int which = 0;
+  BlockLS ls;                      // block least-squares state of the current GMRES cycle
   cudaStream_t stream = nullptr;
   double* Fval = nullptr;          // [nnzF]
   float* Fvalf = nullptr;
@@ -259,6 +261,7 @@ struct mhde_ctx {
   int device = 0;
   bool trace = false;                  // MHDE_TRACE=1: per-sweep residuals on stderr
   bool use_graphs = true;              // MHDE_GRAPHS=0 disables graph capture
+  bool serial = false;                 // MHDE_SERIAL=1: solve the two subproblems one after the other
   bool spmm_rows = false;              // MHDE_SPMM=rows: row-per-thread saddle SpMM variant
   int spmm_block = 256;                // CTA size of the chunked saddle SpMM (autotuned at bind)
   bool spmm_forced = false;            // MHDE_SPMM set: skip the autotuner

@@ -219,20 +219,37 @@ static int col_norms(const mhde_ctx* c, Sub& s, const T* X, std::vector<double>&
   return MHDE_OK;
 }
 
+// Row chunks of a block Gram: as many as the partial-sum buffer holds (up to
+// 8 per SM), so that small blocks still fill the GPU.
+static int gram_chunks(const mhde_ctx* c, int k, int r) {
+  const size_t cap = (size_t)c->nchunk * (c->opt.restart + 1) * c->J * c->J;
+  const size_t per = (size_t)k * r * r;
+  return (int)std::max<size_t>(1, std::min<size_t>({cap / per, (size_t)1216, (size_t)((c->n_rows + 63) / 64)}));
+}
+
 // Gram of V_0..V_{k-1} against W (r columns) -> host array [k][r][r].
 template <typename T>
 static int gram_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int k, const T* W, int r,
                      std::vector<double>& out, int ld) {
-  // as many row chunks as the partial-sum buffer holds (up to 8 per SM), so
-  // that small blocks still fill the GPU
-  const size_t cap = (size_t)c->nchunk * (c->opt.restart + 1) * c->J * c->J;
-  const size_t per = (size_t)k * r * r;
-  const int nchunk = (int)std::max<size_t>(
-      1, std::min<size_t>({cap / per, (size_t)1216, (size_t)((c->n_rows + 63) / 64)}));
-  launch_gram<T>(V, vstride, k, W, c->n_rows, ld, r, nchunk, s.part, s.gram, s.stream);
+  launch_gram<T>(V, vstride, k, W, c->n_rows, ld, r, gram_chunks(c, k, r), s.part, s.gram, s.stream);
   SCU(cudaMemcpyAsync(s.hbuf, s.gram, sizeof(double) * k * r * r, cudaMemcpyDeviceToHost, s.stream));
   SCU(cudaStreamSynchronize(s.stream));
   out.assign(s.hbuf, s.hbuf + (size_t)k * r * r);
+  return MHDE_OK;
+}
+
+// Gram of V_0..V_k and W against W (k + 2 blocks), then the projected Gram
+// W^T W - sum_i H_i^T H_i in place of the last block and trace(W^T W),
+// trace(projected) after it -> host array of (k + 2) r r + 2 values.
+template <typename T>
+static int gram_proj_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int k, const T* W, int r, int ld,
+                          std::vector<double>& out) {
+  launch_gram<T>(V, vstride, k + 2, W, c->n_rows, ld, r, gram_chunks(c, k + 2, r), s.part, s.gram, s.stream);
+  launch_proj_gram(s.gram, k, r, s.stream);
+  const size_t n = (size_t)(k + 2) * r * r + 2;
+  SCU(cudaMemcpyAsync(s.hbuf, s.gram, sizeof(double) * n, cudaMemcpyDeviceToHost, s.stream));
+  SCU(cudaStreamSynchronize(s.stream));
+  out.assign(s.hbuf, s.hbuf + n);
   return MHDE_OK;
 }
 
@@ -295,65 +312,54 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   const int Rp = (r + 3) / 4 * 4;
   double* dC0 = upload_coef<double>(c, s, C0, 3);
   launch_combine_from_f64<T>(Vb, s.Res, dC0, J, r, c->n_rows, Jp, Rp, st);
-  BlockLS ls;
+  BlockLS& ls = s.ls;                            // kept in the subproblem: no reallocation per cycle
   ls.init(r, J, m, S0.data());
-  std::vector<double> G, H, Y, Hsum;
+  std::vector<double> G, H, Y, Hsum, Gp;
   int k = 0;
   T* Zb = (T*)s.zbasis;
+  T* dcoef = (T*)s.coef;                         // combination coefficients (staging slot 0)
+  bool ahead = false;                            // this block's preconditioner and operator are queued
   for (; k < m && used < maxit; ++k) {
     T* Vk = Vb + (size_t)k * vs;
     T* Zk_ = Zb + (size_t)k * vs;                 // flexible GMRES keeps every preconditioned block
     T* Wn = Vb + (size_t)(k + 1) * vs;            // W = A Z_k is built in the next basis slot
-    PhaseClock pc1(c, s);
-    apply_prec<T>(c, s, Vk, Zk_, Rp);
-    pc1.stop(2);
-    PhaseClock pc2(c, s);
-    launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk_, nullptr, Wn, 0, Rp, st);
-    pc2.stop(3);
+    if (!ahead) {
+      PhaseClock pc1(c, s);
+      apply_prec<T>(c, s, Vk, Zk_, Rp);
+      pc1.stop(2);
+      PhaseClock pc2(c, s);
+      launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zk_, nullptr, Wn, 0, Rp, st);
+      pc2.stop(3);
+    }
+    ahead = false;
     PhaseClock pc3(c, s);
     // one reduction: [V_0 .. V_k, W]^T W gives the projections H_i = V_i^T W
-    // and W^T W; the projected block's Gram follows from W^T W - H^T H
-    if ((rc = gram_host<T>(c, s, Vb, vs, k + 2, Wn, r, G, Rp))) return rc;
-    Hsum.assign(G.begin(), G.begin() + (size_t)(k + 1) * r * r);
-    std::vector<double> Gp(G.begin() + (size_t)(k + 1) * r * r, G.end());
-    double trW = 0.0, trP = 0.0;
-    for (int p = 0; p < r; ++p) trW += Gp[(size_t)p * r + p];
-    for (int i = 0; i <= k; ++i)
-      for (int p = 0; p < r; ++p)
-        for (int q = 0; q < r; ++q) {
-          double acc = 0.0;
-          for (int t = 0; t < r; ++t) acc += Hsum[(size_t)i * r * r + t * r + p] * Hsum[(size_t)i * r * r + t * r + q];
-          Gp[(size_t)p * r + q] -= acc;
-        }
-    for (int p = 0; p < r; ++p) trP += Gp[(size_t)p * r + p];
+    // and W^T W; the projected block's Gram W^T W - H^T H is formed on the
+    // device, so the host receives H, the projected Gram and both traces
+    if ((rc = gram_proj_host<T>(c, s, Vb, vs, k, Wn, r, Rp, G))) return rc;
+    const size_t rr = (size_t)r * r;
+    Hsum.assign(G.begin(), G.begin() + (size_t)(k + 1) * rr);
+    Gp.assign(G.begin() + (size_t)(k + 1) * rr, G.begin() + (size_t)(k + 2) * rr);
+    const double trW = G[(size_t)(k + 2) * rr], trP = G[(size_t)(k + 2) * rr + 1];
     std::vector<double> Tn, Sn;
     int rk;
     if (trP > 1e-3 * trW) {
       rk = svqb(r, Gp, thresh, Tn, Sn);
       if (rk == r) {
-        // V_{k+1} = (W - sum_i V_i H_i) T  in one pass, in place
-        std::vector<double> Cc((size_t)(k + 2) * r * r, 0.0);
-        for (int i = 0; i <= k; ++i)
-          for (int p = 0; p < r; ++p)
-            for (int q = 0; q < r; ++q) {
-              double acc = 0.0;
-              for (int t = 0; t < r; ++t) acc += Hsum[(size_t)i * r * r + p * r + t] * Tn[(size_t)t * r + q];
-              Cc[(size_t)i * r * r + p * r + q] = -acc;
-            }
-        for (int p = 0; p < r; ++p)
-          for (int q = 0; q < r; ++q) Cc[(size_t)(k + 1) * r * r + p * r + q] = Tn[(size_t)p * r + q];
-        T* dc = upload_coef<T>(c, s, Cc, 0);
-        launch_block_combine<T>(Wn, nullptr, T(0), Vb, vs, k + 2, r, dc, r, c->n_rows, Rp, Rp, st);
+        // V_{k+1} = (W - sum_i V_i H_i) T  in one pass, in place; the
+        // coefficients -H_i T and T are formed on the device
+        const double* dT = upload_coef<double>(c, s, Tn, 1);
+        launch_make_coef<T>(s.gram, dT, k, r, dcoef, st);
+        launch_block_combine<T>(Wn, nullptr, T(0), Vb, vs, k + 2, r, dcoef, r, c->n_rows, Rp, Rp, st);
       }
     } else {
       // strong cancellation: explicit two-pass Gram-Schmidt for this block
-      for (auto& v : H) v = 0.0;
       H.assign(Hsum.begin(), Hsum.end());
       for (auto& v : H) v = -v;
       T* dc = upload_coef<T>(c, s, H, 0);
       launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st);
       if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wn, r, H, Rp))) return rc;
-      for (size_t t = 0; t < H.size(); ++t) Hsum[t] += H[t];
+      for (size_t t2 = 0; t2 < H.size(); ++t2) Hsum[t2] += H[t2];
       for (auto& v : H) v = -v;
       dc = upload_coef<T>(c, s, H, 1);
       launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st);
@@ -365,18 +371,24 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
       }
     }
     pc3.stop(4);
+    const bool breakdown = rk < r;
+    // queue the next block's preconditioner and operator before the host
+    // updates the least-squares problem, so that the two overlap; if this
+    // block turns out to be the last, that work is simply not used
+    if (!breakdown && k + 1 < m && used + 1 < maxit && !c->trace) {
+      T* Vn = Wn;
+      T* Zn = Zb + (size_t)(k + 1) * vs;
+      apply_prec<T>(c, s, Vn, Zn, Rp);
+      launch_saddle_spmm<T>(c, Prec<T>::F(s), Prec<T>::B(c), Prec<T>::BT(c), Zn, nullptr,
+                            Vb + (size_t)(k + 2) * vs, 0, Rp, st);
+      ahead = true;
+    }
     PhaseClock pc4(c, s);
-    bool breakdown = rk < r;
-    const int rows = (k + 2) * r;
-    std::vector<double> hcol((size_t)rows * r, 0.0);
-    for (int i = 0; i <= k; ++i)
-      for (int p = 0; p < r; ++p)
-        for (int q = 0; q < r; ++q)
-          hcol[(size_t)q * rows + i * r + p] = Hsum[(size_t)i * r * r + (size_t)p * r + q];
-    if (!breakdown)
-      for (int p = 0; p < r; ++p)
-        for (int q = 0; q < r; ++q) hcol[(size_t)q * rows + (k + 1) * r + p] = Sn[(size_t)p * r + q];
-    bool ok = ls.add(hcol.data());
+    // new block column of the Hessenberg matrix, row-major: [H_0; ...; H_k; S]
+    std::vector<double> hblk((size_t)(k + 2) * rr, 0.0);
+    std::copy(Hsum.begin(), Hsum.begin() + (size_t)(k + 1) * rr, hblk.begin());
+    if (!breakdown) std::copy(Sn.begin(), Sn.begin() + rr, hblk.begin() + (size_t)(k + 1) * rr);
+    bool ok = ls.add(hblk.data());
     pc4.stop(5);
     used++;
     double worst = 0.0;
@@ -534,12 +546,25 @@ void precond_apply_any(mhde_ctx* c, int which, const void* in, void* out) {
 
 void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W) {
   Sub& s = c->sub[which];
+  const int nchunk = gram_chunks(c, k, c->J);
   if (c->opt.precision == MHDE_PREC_FP64)
-    launch_gram<double>((const double*)V, vstride, k, (const double*)W, c->n_rows, c->Jp, c->J, c->nchunk,
-                        s.part, s.gram, s.stream);
+    launch_gram<double>((const double*)V, vstride, k, (const double*)W, c->n_rows, c->Jp, c->J, nchunk, s.part,
+                        s.gram, s.stream);
   else
-    launch_gram<float>((const float*)V, vstride, k, (const float*)W, c->n_rows, c->Jp, c->J, c->nchunk,
-                       s.part, s.gram, s.stream);
+    launch_gram<float>((const float*)V, vstride, k, (const float*)W, c->n_rows, c->Jp, c->J, nchunk, s.part,
+                       s.gram, s.stream);
+}
+
+// out = sum_i V_i C_i over k blocks of J columns with the coefficients in
+// staging slot 0 (kernel timing)
+void combine_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, void* out) {
+  Sub& s = c->sub[which];
+  if (c->opt.precision == MHDE_PREC_FP64)
+    launch_block_combine<double>((double*)out, nullptr, 0.0, (const double*)V, vstride, k, c->J,
+                                 (const double*)s.coef, c->J, c->n_rows, c->Jp, c->Jp, s.stream);
+  else
+    launch_block_combine<float>((float*)out, nullptr, 0.f, (const float*)V, vstride, k, c->J, (const float*)s.coef,
+                                c->J, c->n_rows, c->Jp, c->Jp, s.stream);
 }
 
 int solve_sub(mhde_ctx* c, int which) {

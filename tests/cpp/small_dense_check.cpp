@@ -2,6 +2,9 @@
 // tests/test_host_small_dense_cpu.py through stdin/stdout:
 //   "E n a_00 ... a_{n-1,n-1}"    -> eigenvalues of an upper Hessenberg matrix
 //   "P d h_00 ... h_{d,d-1}"      -> quadratic factors of the GMRES polynomial
+//   "L r J m S0 h_0 ... h_{m-1}"  -> block least squares (BlockLS): after each
+//                                    block column its ok flag and the J residual
+//                                    norms, then the solution (m r x J)
 #include <cstdio>
 #include <vector>
 
@@ -11,7 +14,26 @@ int main() {
   char mode[8];
   int n;
   while (std::scanf("%7s %d", mode, &n) == 2) {
-    if (mode[0] == 'E') {
+    if (mode[0] == 'L') {
+      const int r = n;
+      int J = 0, m = 0;
+      if (std::scanf("%d %d", &J, &m) != 2) return 1;
+      std::vector<double> S0((size_t)r * J);
+      for (auto& v : S0) std::scanf("%lf", &v);
+      mhde::BlockLS ls;
+      ls.init(r, J, m, S0.data());
+      for (int k = 0; k < m; ++k) {
+        std::vector<double> h((size_t)(k + 2) * r * r);
+        for (auto& v : h) std::scanf("%lf", &v);
+        const bool ok = ls.add(h.data());
+        std::printf("%d", ok ? 1 : 0);
+        for (int j = 0; j < J; ++j) std::printf(" %.17g", ls.resid(j));
+        std::printf("\n");
+      }
+      std::vector<double> Y;
+      ls.solve(Y);
+      for (double v : Y) std::printf("%.17g\n", v);
+    } else if (mode[0] == 'E') {
       std::vector<double> a((size_t)n * n), wr(n), wi(n);
       for (auto& v : a) std::scanf("%lf", &v);
       bool ok = mhde::eig_hessenberg(n, a.data(), wr.data(), wi.data());

@@ -1,5 +1,6 @@
-"""CPU check of the library's host-side small dense eigensolver (used to turn
-an Arnoldi Hessenberg matrix into GMRES-polynomial roots) against numpy."""
+"""CPU checks of the library's host-side small dense routines against numpy:
+the Hessenberg eigensolver (GMRES-polynomial roots) and the block least-squares
+update of the block GMRES iteration."""
 import os
 import shutil
 import subprocess
@@ -91,3 +92,34 @@ def test_gmres_polynomial_factors_vanish_at_harmonic_ritz_values(checker):
         for t in theta:
             assert abs(pi(t)) < 1e-8
         assert abs(pi(0.0) - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("r,J,m", [(1, 1, 6), (3, 5, 4), (4, 4, 7), (20, 20, 6)])
+def test_block_least_squares_matches_numpy_lstsq(checker, r, J, m):
+    """BlockLS: Householder QR of the block Hessenberg matrix, one block column
+    at a time.  After every column the residual norms of
+    min || E_1 S0 - Hbar_k Y || must equal numpy's, and the final Y must match
+    numpy.linalg.lstsq on the assembled ((m+1) r) x (m r) problem."""
+    rng = np.random.default_rng(11 + r + J + m)
+    S0 = rng.standard_normal((r, J))
+    blocks = [rng.standard_normal(((k + 2) * r, r)) for k in range(m)]
+    text = f"L {r} {J} {m}\n" + " ".join(repr(float(v)) for v in S0.ravel()) + "\n"
+    text += "".join(" ".join(repr(float(v)) for v in b.ravel()) + "\n" for b in blocks)
+    out = subprocess.run([checker], input=text, capture_output=True, text=True, check=True).stdout.split()
+    Hbar = np.zeros(((m + 1) * r, m * r))
+    for k, b in enumerate(blocks):
+        Hbar[:(k + 2) * r, k * r:(k + 1) * r] = b
+    B = np.zeros(((m + 1) * r, J))
+    B[:r] = S0
+    pos = 0
+    for k in range(m):
+        ok = int(out[pos]); pos += 1
+        res = np.array([float(v) for v in out[pos:pos + J]]); pos += J
+        H = Hbar[:(k + 2) * r, :(k + 1) * r]
+        Y = np.linalg.lstsq(H, B[:(k + 2) * r], rcond=None)[0]
+        want = np.linalg.norm(B[:(k + 2) * r] - H @ Y, axis=0)
+        assert ok == 1
+        assert np.allclose(res, want, rtol=1e-9, atol=1e-12 * np.linalg.norm(S0))
+    Y = np.array([float(v) for v in out[pos:pos + m * r * J]]).reshape(m * r, J)
+    Yref = np.linalg.lstsq(Hbar, B, rcond=None)[0]
+    assert np.allclose(Y, Yref, rtol=1e-8, atol=1e-10 * np.abs(Yref).max())
