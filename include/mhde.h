@@ -76,7 +76,7 @@ typedef struct {
   int max_refine;       /* cap on FP64 refinement sweeps (one block GMRES cycle each); default 60 */
   int jacobi_sweeps;    /* damped Jacobi sweeps approximating F^{-1}; default 3 */
   double jacobi_omega;  /* damping of those sweeps; default 0.3 */
-  int amg_sweeps;       /* Jacobi sweeps per level in the pressure-Laplacian V-cycle; default 2 */
+  int amg_sweeps;       /* Jacobi sweeps per level in the pressure-Laplacian V-cycle; default 1 */
   int amg_cycles;       /* V-cycles per application of the pressure-Laplacian inverse; default 1 */
   int poly_degree;      /* degree d (even, <= 16) of the GMRES polynomial in D^{-1} F that
                            approximates F^{-1}, rebuilt every step from d Arnoldi steps;
@@ -84,7 +84,10 @@ typedef struct {
                            cheaper per application but lost robustness as the cavity flow
                            developed, so the inner GMRES is the default) */
   int inner_iters;      /* k of the inner per-column GMRES(k) on F (flexible outer GMRES), used
-                           when poly_degree = 0; 0 = damped Jacobi sweeps instead; default 8 */
+                           when poly_degree = 0; 0 = damped Jacobi sweeps instead; default 6
+                           (on the 128x128 cavity ensemble 6 inner steps and one smoothing
+                           sweep per AMG level cost more outer iterations than 8 and 2 but
+                           less time per step) */
   int schur;            /* pressure Schur approximation: 0 Cahouet-Chabard, 1 pressure
                            convection-diffusion (adds the mean-field P1 convection); default 1 */
   int strict;           /* 1: reject alpha_j <= 0 or mu <= 1/2 with MHDE_ESTAB; default 0 */

@@ -280,10 +280,10 @@ void mhde_default_options(mhde_options* o) {
   o->max_refine = 60;
   o->jacobi_sweeps = 3;
   o->jacobi_omega = 0.3;
-  o->amg_sweeps = 2;
+  o->amg_sweeps = 1;
   o->amg_cycles = 1;
   o->poly_degree = 0;
-  o->inner_iters = 8;
+  o->inner_iters = 6;
   o->schur = 1;
   o->strict = 0;
 }
