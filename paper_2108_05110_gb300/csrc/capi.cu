@@ -152,7 +152,7 @@ size_t layout(mhde_ctx* c, char* base) {
     s.Rk = w.take<char>(vs * ks);
     s.Dk = w.take<char>(vs * ks);
     s.part = w.take<double>((size_t)c->nchunk * (m + 1) * c->J * c->J);
-    s.gram = w.take<double>((size_t)(m + 2) * c->J * c->J + 8);   // m + 1 blocks, then two traces
+    s.gram = w.take<double>((size_t)(m + 2) * c->J * c->J);       // m + 1 blocks, then the projected Gram
     s.coef = w.take<char>(4 * (size_t)(m + 1) * c->J * c->J * 8);
     s.colsq = w.take<double>((size_t)c->nchunk * Jp);
     s.dscale = w.take<double>(2 * Jp);
@@ -503,7 +503,7 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   c->h_M.resize(fe.F.nnz());
   CU(cudaMemcpy(c->h_M.data(), c->d_M, sizeof(double) * fe.F.nnz(), cudaMemcpyDeviceToHost));
   // pinned host staging
-  const size_t small = (size_t)(c->opt.restart + 2) * c->J * c->J + 8;
+  const size_t small = (size_t)(c->opt.restart + 2) * c->J * c->J;
   for (int which = 0; which < 2; ++which) {
     Sub& s = c->sub[which];
     CU(cudaMallocHost((void**)&s.hbuf, sizeof(double) * small));

@@ -76,8 +76,7 @@ void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
                  int nchunk, double* part, double* gram, cudaStream_t st);
-// G = [H_0 .. H_k, W^T W] (r x r blocks) -> block k+1 := W^T W - sum_i H_i^T H_i,
-// then trace(W^T W) and the projected trace at G[(k+2) r r], G[(k+2) r r + 1]
+// G = [H_0 .. H_k, W^T W] (r x r blocks) -> block k+2 := W^T W - sum_i H_i^T H_i
 void launch_proj_gram(double* G, int k, int r, cudaStream_t st);
 // C_i = -H_i T (i <= k), C_{k+1} = T, converted to the Krylov precision
 template <typename T>

@@ -69,8 +69,8 @@ __global__ void k_fd_spmm(int n2, int nch, const int* __restrict__ rp, const int
   reinterpret_cast<V*>(w)[(size_t)a * nch + ch] = acc;
 }
 
-// Partial column dots: part[chunk][l][col] = sum_rows V_l[row][col] w[row][col]
-// (l < nl), and part[chunk][nl][col] = sum_rows w^2 when with_norm.  A thread
+// Partial column dots: part[l][col][chunk] = sum_rows V_l[row][col] w[row][col]
+// (l < nl), and part[nl][col][chunk] = sum_rows w^2 when with_norm.  A thread
 // owns 4 consecutive columns of a row (one 16-byte load per vector for FP32),
 // so many rows are in flight per CTA.
 template <typename T, int NLM>
@@ -105,8 +105,10 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
       for (int q = 0; q < 4; ++q) acc[NLM - 1][q] += wv[q] * wv[q];
     }
   }
-  // stage every group's partial sums, then one warp per (output, column)
-  // sums the G groups with a fixed shuffle tree (deterministic)
+  // stage every group's partial sums, then one thread per (output, column)
+  // adds the G groups in a fixed order (deterministic); the chunk's partial
+  // goes to part[(slot C + col) nchunk + chunk], chunk-contiguous so that the
+  // reduction over chunks reads coalesced
   const int nout = nl + (with_norm ? 1 : 0);
   float* redf = reinterpret_cast<float*>(red);
   if (g < G) {
@@ -120,15 +122,43 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
     }
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int o = warp; o < nout * C; o += nwarp) {
-    const int slot = o / C, c = o % C;
+  for (int o = threadIdx.x; o < nout * C; o += blockDim.x) {
+    const int slot = o / C, c = o - slot * C;
     float sum = 0.f;
-    for (int h = lane; h < G; h += 32) sum += redf[((size_t)slot * G + h) * C + c];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-    if (lane == 0) part[((size_t)blockIdx.x * (KIN_MAX + 2) + slot) * C + c] = (double)sum;
+    for (int h = 0; h < G; ++h) sum += redf[((size_t)slot * G + h) * C + c];
+    part[(size_t)o * gridDim.x + blockIdx.x] = (double)sum;
   }
+}
+
+// Per-column least squares min || beta e_1 - H y || by Givens rotations for
+// column c (one thread; h, g: shared scratch of (KIN_MAX+1) x KIN_MAX and
+// KIN_MAX+1 doubles).  y is written as doubles, then a float copy.
+__device__ void col_lsq(int C, int kin, int c, const double* __restrict__ H, double beta, double (*h)[KIN_MAX],
+                        double* g, double* __restrict__ y) {
+  for (int l = 0; l <= kin; ++l)
+    for (int i = 0; i < kin; ++i) h[l][i] = (l <= i + 1) ? H[((size_t)l * kin + i) * C + c] : 0.0;
+  for (int l = 0; l <= kin; ++l) g[l] = 0.0;
+  g[0] = beta;
+  for (int i = 0; i < kin; ++i) {
+    const double a = h[i][i], b = h[i + 1][i];
+    const double rr = sqrt(a * a + b * b);
+    const double cs = rr > 0.0 ? a / rr : 1.0, sn = rr > 0.0 ? b / rr : 0.0;
+    for (int j = i; j < kin; ++j) {
+      const double t1 = h[i][j], t2 = h[i + 1][j];
+      h[i][j] = cs * t1 + sn * t2;
+      h[i + 1][j] = -sn * t1 + cs * t2;
+    }
+    const double t1 = g[i], t2 = g[i + 1];
+    g[i] = cs * t1 + sn * t2;
+    g[i + 1] = -sn * t1 + cs * t2;
+  }
+  for (int i = kin - 1; i >= 0; --i) {
+    double sum = g[i];
+    for (int j = i + 1; j < kin; ++j) sum -= h[i][j] * y[(size_t)j * C + c];
+    y[(size_t)i * C + c] = h[i][i] != 0.0 ? sum / h[i][i] : 0.0;
+  }
+  float* yf = reinterpret_cast<float*>(y + (size_t)kin * C);
+  for (int i = 0; i < kin; ++i) yf[(size_t)i * C + c] = (float)y[(size_t)i * C + c];
 }
 
 // Reduce the partial dots over chunks and update the Hessenberg column i.
@@ -137,20 +167,26 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
 // Gram-Schmidt pass, H[l][i] = h; mode 1: second pass, H[l][i] += h, norm
 // from the Pythagorean identity, H[i+1][i] = norm, inv[col] = 1/norm;
 // mode 2: initial norms beta[col], inv[col] = 1/beta; mode 3: single pass,
-// H[l][i] = h and the norm as in mode 1.
+// H[l][i] = h and the norm as in mode 1.  With y given, the launch of the last
+// step (i = kin - 1) also solves the column's least-squares problem into y.
 constexpr int RED_T = 32 * (KIN_MAX + 2);
 
 __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl, int kin,
                                                       const double* __restrict__ part, double* __restrict__ dots,
                                                       int mode, int i, double* __restrict__ H,
-                                                      double* __restrict__ beta, double* __restrict__ inv) {
+                                                      double* __restrict__ beta, double* __restrict__ inv,
+                                                      double* __restrict__ y) {
   __shared__ double sh[KIN_MAX + 2];
+  __shared__ double lh[KIN_MAX + 1][KIN_MAX];
+  __shared__ double lg[KIN_MAX + 1];
   const int c = blockIdx.x;
   const int nout = nl + ((mode == 1 || mode == 3) ? 1 : 0);
   const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
   if (l < nout) {
     double s = 0.0;
-    for (int ch = lane; ch < nchunk; ch += 32) s += part[((size_t)ch * (KIN_MAX + 2) + l) * C + c];
+    const double* pl = part + ((size_t)l * C + c) * nchunk;
+#pragma unroll 4
+    for (int ch = lane; ch < nchunk; ch += 32) s += pl[ch];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) sh[l] = s;
@@ -173,6 +209,8 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
     H[((size_t)(i + 1) * kin + i) * C + c] = nrm;
     inv[c] = nrm > 0.0 ? 1.0 / nrm : 0.0;
     reinterpret_cast<float*>(inv + C)[c] = (float)inv[c];
+    // after the last Arnoldi step, this column's least-squares problem
+    if (y && i == kin - 1) col_lsq(C, kin, c, H, beta[c], lh, lg, y);
   } else if (mode == 2) {
     const double b = sh[0] > 0.0 ? sqrt(sh[0]) : 0.0;
     beta[c] = b;
@@ -203,44 +241,6 @@ __global__ void k_col_update(int n_rows, int C, int nl, const T* V, size_t vstri
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] *= scale[c0 + q];
   st4(out + o, acc);
-}
-
-// Per-column least squares min || beta e_1 - H y || by Givens rotations.
-// One CTA per column: the Hessenberg matrix is staged in shared memory by
-// the CTA and reduced by its first thread.
-__global__ void k_col_lsq(int C, int kin, const double* __restrict__ H, const double* __restrict__ beta,
-                          double* __restrict__ y) {
-  __shared__ double h[KIN_MAX + 1][KIN_MAX];
-  __shared__ double g[KIN_MAX + 1];
-  const int c = blockIdx.x;
-  for (int e = threadIdx.x; e < (kin + 1) * kin; e += blockDim.x) {
-    int l = e / kin, i = e % kin;
-    h[l][i] = (l <= i + 1) ? H[((size_t)l * kin + i) * C + c] : 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int l = 0; l <= kin; ++l) g[l] = 0.0;
-  g[0] = beta[c];
-  for (int i = 0; i < kin; ++i) {
-    double a = h[i][i], b = h[i + 1][i];
-    double r = sqrt(a * a + b * b);
-    double cs = r > 0.0 ? a / r : 1.0, sn = r > 0.0 ? b / r : 0.0;
-    for (int j = i; j < kin; ++j) {
-      double t1 = h[i][j], t2 = h[i + 1][j];
-      h[i][j] = cs * t1 + sn * t2;
-      h[i + 1][j] = -sn * t1 + cs * t2;
-    }
-    double t1 = g[i], t2 = g[i + 1];
-    g[i] = cs * t1 + sn * t2;
-    g[i + 1] = -sn * t1 + cs * t2;
-  }
-  for (int i = kin - 1; i >= 0; --i) {
-    double sum = g[i];
-    for (int j = i + 1; j < kin; ++j) sum -= h[i][j] * y[(size_t)j * C + c];
-    y[(size_t)i * C + c] = h[i][i] != 0.0 ? sum / h[i][i] : 0.0;
-  }
-  float* yf = reinterpret_cast<float*>(y + (size_t)kin * C);
-  for (int i = 0; i < kin; ++i) yf[(size_t)i * C + c] = (float)y[(size_t)i * C + c];
 }
 
 // z[row][col] = dinv[row] * sum_l V_l[row][col] y[l][col]; 4 entries per thread
@@ -319,11 +319,11 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* d
   const T* dotsT = f32 ? (const T*)(s.idot + (size_t)(KIN_MAX + 2) * C) : (const T*)s.idot;
   const T* invT = f32 ? (const T*)(s.ibeta + 2 * C) : (const T*)(s.ibeta + C);
   const T* yT = f32 ? (const T*)(s.iy + (size_t)kin * C) : (const T*)s.iy;
-  count_launch(3 + 4 * kin + 2);
+  count_launch(3 + 4 * kin + 1);
   // beta = ||r||, v_0 = r / beta
   col_dots<T>(nchunk, threads, shm, st, n2, C, 1, r, 0, r, rows_per_chunk, 0, s.ipart);
-  k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, 1, kin, s.ipart, s.idot, 2, 0, s.ih, s.ibeta,
-                                         s.ibeta + C);
+  k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, 1, kin, s.ipart, s.idot, 2, 0, s.ih, s.ibeta, s.ibeta + C,
+                                    nullptr);
   k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, 0, Vb, vstride, dotsT, r, Vb, invT);
   for (int i = 0; i < kin; ++i) {
     T* vi = Vb + (size_t)i * vstride;
@@ -333,10 +333,9 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* d
     // single sweep; the projected norm follows from the Pythagorean identity
     col_dots<T>(nchunk, threads, shm, st, n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 1, s.ipart);
     k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, i + 1, kin, s.ipart, s.idot, 3, i, s.ih, s.ibeta,
-                                      s.ibeta + C);
+                                      s.ibeta + C, s.iy);
     k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, dotsT, w, w, invT);
   }
-  k_col_lsq<<<C, 32, 0, st>>>(C, kin, s.ih, s.ibeta, s.iy);
   k_col_final<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, kin, Vb, vstride, yT, dinv, z);
 }
 

@@ -871,41 +871,32 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
 }
 
 // ------------------------------------------------------------ one-reduce Gram-Schmidt helpers
-// G holds H_0 .. H_k (H_i = V_i^T W) and W^T W as r x r blocks.  Block k + 1
-// becomes the projected Gram W^T W - sum_i H_i^T H_i (each entry one fixed-order
-// sum over i, t), followed by trace(W^T W) and the projected trace.  One CTA.
-__global__ void k_proj_gram(double* G, int k, int r) {
+// G holds H_0 .. H_k (H_i = V_i^T W) and W^T W as r x r blocks.  Block k + 2
+// receives the projected Gram W^T W - sum_i H_i^T H_i: one warp per entry, its
+// lanes striding over the (i, t) terms, then a fixed butterfly of shuffles
+// (deterministic).
+__global__ void __launch_bounds__(256) k_proj_gram(double* G, int k, int r) {
   const int rr = r * r;
-  double* Gw = G + (size_t)(k + 1) * rr;
-  __shared__ double trw;
-  if (threadIdx.x == 0) {
-    double acc = 0.0;
-    for (int p = 0; p < r; ++p) acc += Gw[p * r + p];
-    trw = acc;
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= rr) return;                            // whole warps exit together
+  const int p = o / r, q = o % r;
+  const int nterm = (k + 1) * r;
+  double acc = 0.0;
+  for (int e = lane; e < nterm; e += 32) {
+    const int i = e / r, t = e - i * r;
+    const double* Hi = G + (size_t)i * rr + (size_t)t * r;
+    acc = fma(Hi[p], Hi[q], acc);
   }
-  __syncthreads();
-  for (int o = threadIdx.x; o < rr; o += blockDim.x) {
-    const int p = o / r, q = o % r;
-    double acc = 0.0;
-    for (int i = 0; i <= k; ++i) {
-      const double* Hi = G + (size_t)i * rr;
-      for (int t = 0; t < r; ++t) acc = fma(Hi[t * r + p], Hi[t * r + q], acc);
-    }
-    Gw[o] -= acc;                                  // each thread reads only its own entry of the block
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double acc = 0.0;
-    for (int p = 0; p < r; ++p) acc += Gw[p * r + p];
-    G[(size_t)(k + 2) * rr] = trw;
-    G[(size_t)(k + 2) * rr + 1] = acc;
-  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) G[(size_t)(k + 2) * rr + o] = G[(size_t)(k + 1) * rr + o] - acc;
 }
 
 void launch_proj_gram(double* G, int k, int r, cudaStream_t st) {
   count_launch();
-  const int threads = std::min(1024, std::max(32, (r * r + 31) / 32 * 32));
-  k_proj_gram<<<1, threads, 0, st>>>(G, k, r);
+  const long long threads = (long long)r * r * 32;
+  k_proj_gram<<<nblk(threads, 256), 256, 0, st>>>(G, k, r);
 }
 
 // Coefficients of V_{k+1} = (W - sum_i V_i H_i) T for the block combination:
@@ -973,35 +964,36 @@ __global__ void __launch_bounds__(COMB_T) k_block_combine(T* out, const T* in, T
     for (int ib = 0; ib < nbk; ++ib) {
       const T* Vi = V + (size_t)(i0 + ib) * vstride;
       const T* cb = Cs + (size_t)ib * W * W;
+      // every load of this block's rows is issued before the first use, so
+      // the thread has all of them in flight at once
+      T v[RPT][W];
 #pragma unroll
-      for (int p4 = 0; p4 < W / 4; ++p4) {
-        if (p4 >= np4) break;
-        T v[RPT][4];
+      for (int s = 0; s < RPT; ++s) {
+        const int row = base + s * COMB_T;
 #pragma unroll
-        for (int s = 0; s < RPT; ++s) {
-          const int row = base + s * COMB_T;
-          if (row < n_rows) {
-            row_ld4(Vi + (size_t)row * ldv + 4 * p4, v[s]);
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (4 * p4 + e >= r_in) v[s][e] = T(0);          // padding columns
+        for (int p4 = 0; p4 < W / 4; ++p4) {
+          if (p4 < np4 && row < n_rows) {
+            row_ld4(Vi + (size_t)row * ldv + 4 * p4, &v[s][4 * p4]);
           } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[s][e] = T(0);
+            for (int e = 0; e < 4; ++e) v[s][4 * p4 + e] = T(0);
           }
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const T* cp = cb + (4 * p4 + e) * W;
+        for (int p = 0; p < W; ++p)
+          if (p >= r_in) v[s][p] = T(0);                  // padding columns
+      }
 #pragma unroll
-          for (int q4 = 0; q4 < W / 4; ++q4) {
-            T c[4];
-            row_ld4(cp + 4 * q4, c);
+      for (int p = 0; p < W; ++p) {
+        const T* cp = cb + p * W;
 #pragma unroll
-            for (int s = 0; s < RPT; ++s)
+        for (int q4 = 0; q4 < W / 4; ++q4) {
+          T c[4];
+          row_ld4(cp + 4 * q4, c);
 #pragma unroll
-              for (int u = 0; u < 4; ++u) acc[s][4 * q4 + u] = fma(v[s][e], c[u], acc[s][4 * q4 + u]);
-          }
+          for (int s = 0; s < RPT; ++s)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[s][4 * q4 + u] = fma(v[s][p], c[u], acc[s][4 * q4 + u]);
         }
       }
     }

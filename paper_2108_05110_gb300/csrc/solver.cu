@@ -239,14 +239,13 @@ static int gram_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int 
 }
 
 // Gram of V_0..V_k and W against W (k + 2 blocks), then the projected Gram
-// W^T W - sum_i H_i^T H_i in place of the last block and trace(W^T W),
-// trace(projected) after it -> host array of (k + 2) r r + 2 values.
+// W^T W - sum_i H_i^T H_i as block k + 2 -> host array of (k + 3) r r values.
 template <typename T>
 static int gram_proj_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int k, const T* W, int r, int ld,
                           std::vector<double>& out) {
   launch_gram<T>(V, vstride, k + 2, W, c->n_rows, ld, r, gram_chunks(c, k + 2, r), s.part, s.gram, s.stream);
   launch_proj_gram(s.gram, k, r, s.stream);
-  const size_t n = (size_t)(k + 2) * r * r + 2;
+  const size_t n = (size_t)(k + 3) * r * r;
   SCU(cudaMemcpyAsync(s.hbuf, s.gram, sizeof(double) * n, cudaMemcpyDeviceToHost, s.stream));
   SCU(cudaStreamSynchronize(s.stream));
   out.assign(s.hbuf, s.hbuf + n);
@@ -339,8 +338,12 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
     if ((rc = gram_proj_host<T>(c, s, Vb, vs, k, Wn, r, Rp, G))) return rc;
     const size_t rr = (size_t)r * r;
     Hsum.assign(G.begin(), G.begin() + (size_t)(k + 1) * rr);
-    Gp.assign(G.begin() + (size_t)(k + 1) * rr, G.begin() + (size_t)(k + 2) * rr);
-    const double trW = G[(size_t)(k + 2) * rr], trP = G[(size_t)(k + 2) * rr + 1];
+    Gp.assign(G.begin() + (size_t)(k + 2) * rr, G.begin() + (size_t)(k + 3) * rr);
+    double trW = 0.0, trP = 0.0;
+    for (int p = 0; p < r; ++p) {
+      trW += G[(size_t)(k + 1) * rr + (size_t)p * r + p];
+      trP += Gp[(size_t)p * r + p];
+    }
     std::vector<double> Tn, Sn;
     int rk;
     if (trP > 1e-3 * trW) {
