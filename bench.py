@@ -300,6 +300,19 @@ def spmm_bytes(sz, prec_bytes):
     return matrix + vectors
 
 
+def gram_bytes(sz, restart, prec_bytes):
+    """Algorithmic bytes of the block Gram timed by kernel id 8: restart/2
+    basis blocks and W (n_rows x J_pad each) read once, the (k+1) J x J Gram
+    (FP64) written once."""
+    k1 = max(1, restart // 2) + 1
+    return k1 * sz.n_rows * sz.J_pad * prec_bytes + k1 * sz.J * sz.J * 8
+
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_gram_staged<20> launch
+# on the 128x128, J=20 workload with 16 blocks (191.30 MB + 3.89 MB)
+GRAM_TRAFFIC = 195.2e6
+
+
 def our_arm(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -362,23 +375,36 @@ def our_arm(args, rank, world, local_rank):
     launches = int(st1.launches - st0.launches)
     iters = int(st1.total_iters - st0.total_iters)
 
-    # dominant kernel: the saddle SpMM of the Krylov precision, timed alone
-    kid = 1 if prec == PREC_MIXED else 0
-    spmm_ms = sol.time_kernel(0, kid, reps=50)
+    # dominant kernel (largest share of the step's device time in the ncu
+    # launch list): the partial sums of the block Gram, timed alone on
+    # restart/2 basis blocks plus W, J columns each
     pbytes = 4 if prec == PREC_MIXED else 8
-    alg = spmm_bytes(sol.sizes, pbytes)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = alg / (spmm_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"saddle SpMM ({'FP32' if pbytes == 4 else 'FP64'})",
+    gram_ms = sol.time_kernel(0, 8, reps=50)
+    alg = gram_bytes(sol.sizes, sol.options.restart, pbytes)
+    achieved = alg / (gram_ms / 1000.0) / 1e9
+    # DRAM bytes of one launch of this kernel at this size (ncu capture summarised
+    # in profiles/k_gram_staged_f32_cavity128_J20.md); only for the default workload
+    traffic = GRAM_TRAFFIC if (prec == PREC_MIXED and args.N == WORKLOAD["N"] and args.J == WORKLOAD["J"]
+                               and sol.options.restart == 30) else None
+    kname = "k_gram_staged, FP32" if pbytes == 4 else "k_gram, FP64"
+    roofline = {"bound": "hbm", "kernel": f"block Gram partial sums ({kname}), "
+                f"{sol.options.restart // 2 + 1} blocks x {args.J} columns",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "bytes_per_launch": alg, "ms_per_launch": spmm_ms,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "cta_size": int(st1.spmm_block)}
+                "traffic": traffic, "bytes_per_launch": alg, "ms_per_launch": gram_ms,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    # the Krylov operator (saddle SpMM), for reference
+    kid = 1 if prec == PREC_MIXED else 0
+    spmm_ms = sol.time_kernel(0, kid, reps=50)
+    salg = spmm_bytes(sol.sizes, pbytes)
+    spmm_line = {"kernel": f"saddle SpMM ({'FP32' if pbytes == 4 else 'FP64'})", "bytes_per_launch": salg,
+                 "ms_per_launch": spmm_ms, "achieved": salg / (spmm_ms / 1000.0) / 1e9,
+                 "frac": salg / (spmm_ms / 1000.0) / 1e9 / peak, "cta_size": int(st1.spmm_block)}
     kernel_ms = {name: sol.time_kernel(0, k, reps=10) for name, k in
                  (("means_l2", 4), ("assemble_F", 2), ("rhs", 3), ("precond", 5), ("gram", 6),
                   ("combine", 7))}
@@ -415,7 +441,7 @@ def our_arm(args, rank, world, local_rank):
                 "roofline": roofline, "clocks": clock_info, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "krylov_iters_per_step": iters / args.steps, "kernel_ms": kernel_ms,
+                "krylov_iters_per_step": iters / args.steps, "kernel_ms": kernel_ms, "spmm": spmm_line,
                 "wall_ms_per_step": 1000.0 * wall / args.steps}
         if cpu_secs is not None:
             line["cpu_baseline"] = cpu_baseline_block(cpu_secs)

@@ -239,7 +239,8 @@ int mhde_probe_spmm(mhde_ctx* ctx, int which, int precision, const double* X, do
  * (element kernel + node gather), 4 ensemble means + mixing-length field,
  * 5 block preconditioner (Krylov precision), 6 block Gram of restart/2
  * basis blocks against one block (Krylov precision), 7 block combination
- * sum_i V_i C_i of restart/2 basis blocks (Krylov precision). */
+ * sum_i V_i C_i of restart/2 basis blocks (Krylov precision), 8 the partial
+ * sums of kernel 6 alone (its dominant launch, without the final reduction). */
 int mhde_time_kernel(mhde_ctx* ctx, int which, int kernel, int reps, double* ms);
 
 /* ------------------------------------------------------------------------

@@ -984,7 +984,7 @@ int mhde_probe_spmm(mhde_ctx* c, int which, int precision, const double* X, doub
 int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
   int rc = probe_assemble(c, which);
   if (rc) return rc;
-  if (!ms || reps < 1 || kernel < 0 || kernel > 7) return fail(c, MHDE_EINVAL, "bad kernel id, reps or ms");
+  if (!ms || reps < 1 || kernel < 0 || kernel > 8) return fail(c, MHDE_EINVAL, "bad kernel id, reps or ms");
   Sub& s = c->sub[which];
   cudaStream_t st = s.stream;
   const size_t vs = (size_t)c->n_rows * c->Jp;
@@ -994,11 +994,12 @@ int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
   double* yd = s.X;
   CU(cudaMemcpyAsync(xd, s.S, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const bool fp64 = c->opt.precision == MHDE_PREC_FP64;
-  if (kernel == 1 || (!fp64 && (kernel == 5 || kernel == 6))) launch_d2f(xd, (float*)s.Wk, vs, st);
-  if (fp64 && (kernel == 5 || kernel == 6))
+  const bool block_input = kernel == 5 || kernel == 6 || kernel == 7 || kernel == 8;
+  if (kernel == 1 || (!fp64 && block_input)) launch_d2f(xd, (float*)s.Wk, vs, st);
+  if (fp64 && block_input)
     CU(cudaMemcpyAsync(s.Wk, xd, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const int kb = std::max(1, c->opt.restart / 2);
-  if (kernel == 6 || kernel == 7) {
+  if (kernel == 6 || kernel == 7 || kernel == 8) {
     // fill kb basis blocks with copies of the input
     for (int i = 0; i < kb; ++i)
       CU(cudaMemcpyAsync((char*)s.basis + (size_t)i * vs * ksize(c), s.Wk, vs * ksize(c),
@@ -1048,6 +1049,9 @@ int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
         break;
       case 7:
         combine_any(c, which, s.basis, vs, kb, s.Zk);
+        break;
+      case 8:
+        gram_any(c, which, s.basis, vs, kb, s.Wk, false);
         break;
     }
   };

@@ -75,7 +75,7 @@ void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp
 // Gram partial sums: part[chunk][i][p][q] = sum_rows V_i[row][p] W[row][q]
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
-                 int nchunk, double* part, double* gram, cudaStream_t st);
+                 int nchunk, double* part, double* gram, cudaStream_t st, bool reduce = true);
 // G = [H_0 .. H_k, W^T W] (r x r blocks) -> block k+2 := W^T W - sum_i H_i^T H_i
 void launch_proj_gram(double* G, int k, int r, cudaStream_t st);
 // C_i = -H_i T (i <= k), C_{k+1} = T, converted to the Krylov precision
@@ -126,7 +126,7 @@ int assemble_sub(mhde_ctx* c, int which);
 int solve_sub(mhde_ctx* c, int which);
 // benchmark helpers in the context's Krylov precision
 void precond_apply_any(mhde_ctx* c, int which, const void* in, void* out);
-void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W);
+void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W, bool reduce = true);
 void combine_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, void* out);
 
 }  // namespace mhde

@@ -816,8 +816,8 @@ static size_t gram_smem(int Jp, int r) {
 // scratch the caller provides), then one reduction.
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
-                 int nchunk, double* part, double* gram, cudaStream_t st) {
-  count_launch(2);
+                 int nchunk, double* part, double* gram, cudaStream_t st, bool reduce) {
+  count_launch(reduce ? 2 : 1);
   const GramDevice& gd = gram_setup();               // on failure the unstaged kernels run instead
   const int items = kblocks * ((r + 3) / 4);
   const int w = (r + 3) / 4 * 4;
@@ -866,6 +866,7 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
                                                             part, gram_tile_rows(r));
     }
   }
+  if (!reduce) return;                               // partial sums only (kernel timing)
   const int total = kblocks * r * r;
   k_gram_reduce<<<(total + 31) / 32, 256, 0, st>>>(nparts, total, part, gram);
 }
@@ -1204,7 +1205,7 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
                                     const T*, T*, cudaStream_t);                                        \
   template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, int, cudaStream_t); \
   template void launch_gram<T>(const T*, size_t, int, const T*, int, int, int, int, double*, double*, \
-                               cudaStream_t);                                                        \
+                               cudaStream_t, bool);                                                  \
   template void launch_make_coef<T>(const double*, const double*, int, int, T*, cudaStream_t);       \
   template void launch_block_combine<T>(T*, const T*, T, const T*, size_t, int, int, const T*, int,  \
                                         int, int, int, cudaStream_t);                                \

@@ -547,15 +547,15 @@ void precond_apply_any(mhde_ctx* c, int which, const void* in, void* out) {
     apply_prec<float>(c, s, (const float*)in, (float*)out, c->Jp);
 }
 
-void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W) {
+void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W, bool reduce) {
   Sub& s = c->sub[which];
   const int nchunk = gram_chunks(c, k, c->J);
   if (c->opt.precision == MHDE_PREC_FP64)
     launch_gram<double>((const double*)V, vstride, k, (const double*)W, c->n_rows, c->Jp, c->J, nchunk, s.part,
-                        s.gram, s.stream);
+                        s.gram, s.stream, reduce);
   else
     launch_gram<float>((const float*)V, vstride, k, (const float*)W, c->n_rows, c->Jp, c->J, nchunk, s.part,
-                       s.gram, s.stream);
+                       s.gram, s.stream, reduce);
 }
 
 // out = sum_i V_i C_i over k blocks of J columns with the coefficients in
