@@ -233,9 +233,12 @@ def lid_cavity(N=128, J=20, s=1.0, dt=0.01, nsteps=200, Re=15000.0, seed=2, spre
         out[:, :, 1] = 1.0
         return out
 
+    # the amplitudes are read when u0 / B0 are called, so a caller may change
+    # info["eps_u"] / info["eps_B"] in place (finite-difference perturbations)
     return Ensemble(name=f"lid-cavity-N{N}-J{J}-s{s:g}", mesh=mesh, nu=nu, nu_m=nu_m, s=float(s),
                     dt=float(dt), nsteps=int(nsteps), u0=u0, B0=B0, u_bc=u_bc, B_bc=B_bc,
-                    info={"N": N, "Re": Re, "seed": seed})
+                    info={"N": N, "Re": Re, "seed": seed, "eps_u": eps_u, "eps_B": eps_B,
+                          "perturbation_shape": _stream_perturbation})
 
 
 def channel(J=50, dt=0.05, nsteps=400, s=0.01, nu=1.0 / 600, nu_m=1.0 / 600, seed=3,
