@@ -149,6 +149,12 @@ int mhde_p2_nodes(const mhde_ctx* ctx, double* xy, unsigned char* is_boundary);
  * step counter and the pressures to 0. */
 int mhde_set_initial(mhde_ctx* ctx, const double* u0, const double* B0);
 
+/* Replace the member viscosities nu_j, nu_m,j ([J] each, > 0; host) of a
+ * context, with the derived means and splits (Section 1: nubar, nu'_j).  The
+ * stability condition of Section 3.1 is checked as in mhde_create.  The
+ * state is kept.  Errors: MHDE_EINVAL, MHDE_ESTAB (strict only). */
+int mhde_set_viscosity(mhde_ctx* ctx, const double* nu, const double* nu_m);
+
 /* Body force f_j and curl g_j at t^{n+1} as P2 nodal values [J][n2][2]
  * (host); the discrete forcing is M times the nodal interpolant.  NULL means
  * zero.  Values persist for later steps until set again. */
@@ -202,6 +208,32 @@ int mhde_get_stats(const mhde_ctx* ctx, mhde_stats* stats);
 int mhde_state_bytes(const mhde_ctx* ctx, size_t* bytes);
 int mhde_save_state(mhde_ctx* ctx, void* host_buffer);
 int mhde_load_state(mhde_ctx* ctx, const void* host_buffer);
+
+/* ------------------------------------------------------------------------
+ * Discrete adjoint (gradient of the ensemble-mean energy).
+ *
+ * L = E_h^K = 1/2 (||<v_h>^K||^2 + ||<w_h>^K||^2) (Section 4.2) after K =
+ * nsteps steps of Algorithm 1 from the context's current state, with the
+ * forcing and Dirichlet data currently set held fixed over the K steps.
+ * mhde_energy_adjoint runs the K steps (the context ends at step +K, as after
+ * mhde_advance), returns L, and by the discrete adjoint of the step its
+ * gradient with respect to nu_j and nu_m,j ([J] each, host, may be NULL) and
+ * to the starting fields u_j, B_j as P2 nodal values ([J][n2][2] each, host,
+ * may be NULL; at the start v = u + sqrt(s) B, w = u - sqrt(s) B).  The
+ * reverse sweep keeps a checkpoint of the state every checkpoint_every steps
+ * and recomputes each segment from it.  Each reverse step solves the
+ * transposed shared matrix of both subproblems for all members with the
+ * block solver of the forward step (same precision and tolerance).  The
+ * gradient of the max in the mixing length l^2 = max_j |z'_j|^2 is taken at
+ * the member attaining it.
+ * Workspace: mhde_adjoint_workspace_size() bytes of device memory from the
+ * caller (any alignment; the library aligns it), used only during the call.
+ * Errors: MHDE_EINVAL, MHDE_ESTATE (not bound / no initial state),
+ * MHDE_EWORKSPACE, MHDE_ENOCONV (a forward or adjoint solve failed; the
+ * context is then left mid-run), MHDE_ECUDA. */
+int mhde_adjoint_workspace_size(const mhde_ctx* ctx, int nsteps, int checkpoint_every, size_t* bytes);
+int mhde_energy_adjoint(mhde_ctx* ctx, int nsteps, int checkpoint_every, void* workspace, size_t workspace_bytes,
+                        double* loss, double* grad_nu, double* grad_nu_m, double* grad_u0, double* grad_B0);
 
 const char* mhde_last_error(const mhde_ctx* ctx);
 void mhde_destroy(mhde_ctx* ctx);

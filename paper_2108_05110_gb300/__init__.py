@@ -7,3 +7,9 @@ from .binding import (  # noqa: F401
     Library, load_library, Options, Sizes, Stats, MhdeError, EnsembleSolver, library_path,
     declared_functions, block_gram, block_gram_noalloc, advance_many, PREC_FP64, PREC_MIXED,
 )
+
+
+def energy_function():
+    """The torch.autograd.Function of the ensemble energy (imports torch)."""
+    from .autograd import EnsembleEnergy
+    return EnsembleEnergy

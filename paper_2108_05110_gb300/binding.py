@@ -72,6 +72,9 @@ SIGNATURES = {
     "mhde_p2_nodes": (C.c_int, [_P, _D, _U8]),
     "mhde_set_initial": (C.c_int, [_P, _D, _D]),
     "mhde_set_forcing": (C.c_int, [_P, _D, _D]),
+    "mhde_set_viscosity": (C.c_int, [_P, _D, _D]),
+    "mhde_adjoint_workspace_size": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "mhde_energy_adjoint": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, _D, _D, _D, _D, _D]),
     "mhde_set_dirichlet": (C.c_int, [_P, _D, _D]),
     "mhde_step": (C.c_int, [_P]),
     "mhde_advance": (C.c_int, [_P, C.c_int]),
@@ -309,6 +312,33 @@ class EnsembleSolver:
         shp = (self.J, self.n2, 2)
         u, B = _f64(u_bc, shp), _f64(B_bc, shp)
         self._check(self.lib.mhde_set_dirichlet(self.ctx, _dptr(u), _dptr(B)), "mhde_set_dirichlet")
+
+    def set_viscosity(self, nu, nu_m):
+        nu = np.ascontiguousarray(nu, dtype=np.float64).reshape(self.J)
+        nu_m = np.ascontiguousarray(nu_m, dtype=np.float64).reshape(self.J)
+        self._check(self.lib.mhde_set_viscosity(self.ctx, _dptr(nu), _dptr(nu_m)), "mhde_set_viscosity")
+
+    # ------------------------------------------------------------------ adjoint
+    def energy_adjoint(self, nsteps, checkpoint_every=5):
+        """L = E_h after ``nsteps`` steps from the current state and its
+        gradient (mhde_energy_adjoint): dict with loss, grad_nu, grad_nu_m
+        [J] and grad_u0, grad_B0 [J, n2, 2].  The device workspace is a torch
+        tensor held for the call."""
+        import torch
+        nbytes = C.c_size_t()
+        self._check(self.lib.mhde_adjoint_workspace_size(self.ctx, int(nsteps), int(checkpoint_every),
+                                                         C.byref(nbytes)), "mhde_adjoint_workspace_size")
+        ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.workspace.device)
+        loss = C.c_double()
+        gnu, gnum = np.empty(self.J), np.empty(self.J)
+        gu, gB = np.empty((self.J, self.n2, 2)), np.empty((self.J, self.n2, 2))
+        torch.cuda.synchronize(self.workspace.device)
+        self._check(self.lib.mhde_energy_adjoint(self.ctx, int(nsteps), int(checkpoint_every),
+                                                 C.c_void_p(ws.data_ptr()), nbytes.value, C.byref(loss),
+                                                 _dptr(gnu), _dptr(gnum), _dptr(gu), _dptr(gB)),
+                    "mhde_energy_adjoint")
+        del ws
+        return {"loss": loss.value, "grad_nu": gnu, "grad_nu_m": gnum, "grad_u0": gu, "grad_B0": gB}
 
     # ------------------------------------------------------------------ stepping
     def step(self):

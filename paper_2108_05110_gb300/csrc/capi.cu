@@ -407,6 +407,7 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   CU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CU(upload_quad_tables());
+  CU(upload_adjoint_tables());
   CU(init_inner_attributes());
   CU(init_la_attributes());
   const FeHost& fe = c->fe;
@@ -543,6 +544,49 @@ int mhde_set_initial(mhde_ctx* c, const double* u0, const double* B0) {
   c->have_prev = false;
   c->steps = 0;
   c->stats = mhde_stats();
+  return MHDE_OK;
+}
+
+int mhde_set_viscosity(mhde_ctx* c, const double* nu, const double* nu_m) {
+  if (!c) return MHDE_EINVAL;
+  if (!nu || !nu_m) return fail(c, MHDE_EINVAL, "nu or nu_m is NULL");
+  const int J = c->J;
+  for (int j = 0; j < J; ++j)
+    if (!(nu[j] > 0.0) || !(nu_m[j] > 0.0)) return fail(c, MHDE_EINVAL, "viscosities must be positive");
+  double nb = 0.0, nbm = 0.0;
+  for (int j = 0; j < J; ++j) {
+    nb += nu[j];
+    nbm += nu_m[j];
+  }
+  nb /= J;
+  nbm /= J;
+  std::vector<double> cc(c->Jp, 0.0), cs(c->Jp, 0.0);
+  bool stable = c->opt.mu > 0.5;
+  for (int j = 0; j < J; ++j) {
+    cc[j] = nu[j] - nu_m[j];
+    cs[j] = (nu[j] - nb) + (nu_m[j] - nbm);
+    if (!(nb + nbm - std::fabs(cc[j]) - std::fabs(cs[j]) > 0.0)) stable = false;
+  }
+  if (!stable && c->opt.strict) return fail(c, MHDE_ESTAB, "alpha_j <= 0 or mu <= 1/2");
+  c->nu.assign(nu, nu + J);
+  c->nu_m.assign(nu_m, nu_m + J);
+  c->nubar = nb;
+  c->nubar_m = nbm;
+  for (int j = 0; j < J; ++j) {
+    c->c_cross[j] = cc[j];
+    c->c_same[j] = cs[j];
+  }
+  if (c->bound) {
+    CU(cudaStreamSynchronize(c->sv));
+    CU(cudaStreamSynchronize(c->sw));
+    CU(cudaMemcpy(c->d_ccross, cc.data(), cc.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->d_csame, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // the captured preconditioner graphs carry (nubar + nubar_m)/2 as a launch argument
+    for (int which = 0; which < 2; ++which) {
+      for (auto& kv : c->sub[which].prec_graphs) cudaGraphExecDestroy(kv.second.first);
+      c->sub[which].prec_graphs.clear();
+    }
+  }
   return MHDE_OK;
 }
 

@@ -24,6 +24,7 @@ struct QuadTables {             // degree-5 rule and P2 basis tables (host copy)
 };
 void quad_tables(QuadTables& q);
 cudaError_t upload_quad_tables();
+cudaError_t upload_adjoint_tables();
 
 // ---- finite element kernels (FP64) ----------------------------------------
 void launch_const_local(int nt, const double* geom, double* Mloc, double* Kloc, double* Bloc,
@@ -123,7 +124,20 @@ void launch_poly_apply(const mhde_ctx* c, const Sub& s, const T* Fv, const T* di
 
 // solver entry points (solver.cu)
 int assemble_sub(mhde_ctx* c, int which);
-int solve_sub(mhde_ctx* c, int which);
+// zero_guess: start from X = 0 (transposed adjoint solves) instead of the
+// extrapolation of the last two states
+int solve_sub(mhde_ctx* c, int which, bool zero_guess = false);
+
+// discrete adjoint (kernels_adj.cu)
+void launch_transpose_values(long long nnz, const int* tpos, const double* F, double* FT, float* FTf,
+                             cudaStream_t st);
+void launch_scale_pair(long long n, double s, double* x, float* xf, cudaStream_t st);
+void launch_energy_seed(const mhde_ctx* c, const double* mean, double* seed, cudaStream_t st);
+void launch_adj_rhs(const mhde_ctx* c, const double* seed, double* B, cudaStream_t st);
+void launch_adj_contract(const mhde_ctx* c, const double* Z, const double* Y, const double* meanY,
+                         const double* X, const double* Yh, double* slotZ, double* slotY, double* slotM,
+                         int* kstar, double* kap, double* lamZ, double* lamY, double* tmp, double* prod,
+                         int nchunk, double* part, cudaStream_t st);
 // benchmark helpers in the context's Krylov precision
 void precond_apply_any(mhde_ctx* c, int which, const void* in, void* out);
 void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, const void* W, bool reduce = true);

@@ -471,14 +471,16 @@ int assemble_sub(mhde_ctx* c, int which) {
 }
 
 template <typename T>
-static int solve_sub_t(mhde_ctx* c, int which) {
+static int solve_sub_t(mhde_ctx* c, int which, bool zero_guess) {
   Sub& s = c->sub[which];
   cudaStream_t st = s.stream;
   const int J = c->J;
   const size_t vs = (size_t)c->n_rows * c->Jp;
   int rc;
   // initial guess: linear extrapolation in time of the last two states
-  if (c->have_prev)
+  if (zero_guess)
+    SCU(cudaMemsetAsync(s.X, 0, vs * sizeof(double), st));
+  else if (c->have_prev)
     launch_axpby<double>(s.X, 2.0, s.S, -1.0, s.Sprev, vs, st);
   else
     SCU(cudaMemcpyAsync(s.X, s.S, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -570,9 +572,9 @@ void combine_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, v
                                 c->J, c->n_rows, c->Jp, c->Jp, s.stream);
 }
 
-int solve_sub(mhde_ctx* c, int which) {
-  if (c->opt.precision == MHDE_PREC_FP64) return solve_sub_t<double>(c, which);
-  return solve_sub_t<float>(c, which);
+int solve_sub(mhde_ctx* c, int which, bool zero_guess) {
+  if (c->opt.precision == MHDE_PREC_FP64) return solve_sub_t<double>(c, which, zero_guess);
+  return solve_sub_t<float>(c, which, zero_guess);
 }
 
 }  // namespace mhde
