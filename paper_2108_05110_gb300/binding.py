@@ -5,9 +5,11 @@ CUDA kernels.  PyTorch provides the device workspace (one uint8 tensor) and
 the two CUDA streams of the v and w subproblems.  There is no CPU fallback:
 a missing library or a missing GPU raises.
 """
+import atexit
 import ctypes as C
 import os
 import re
+import weakref
 
 import numpy as np
 
@@ -212,6 +214,22 @@ def block_gram_noalloc(V, W, kblocks, r, G=None, stream=None):
     return G
 
 
+_LIVE = weakref.WeakSet()
+
+
+def _close_live_solvers():
+    """Destroy the contexts still open at interpreter exit, before the CUDA
+    runtime and torch's streams are torn down."""
+    for s in list(_LIVE):
+        try:
+            s.close()
+        except Exception:
+            pass
+
+
+atexit.register(_close_live_solvers)
+
+
 class EnsembleSolver:
     """One ensemble (mesh, J members) on one GPU, through the C ABI.
 
@@ -237,6 +255,7 @@ class EnsembleSolver:
         if rc != 0:
             raise MhdeError(rc, "mhde_create")
         self.ctx = ctx
+        _LIVE.add(self)
         self.sizes = Sizes()
         self._check(self.lib.mhde_get_sizes(self.ctx, C.byref(self.sizes)), "mhde_get_sizes")
         self.bound = False

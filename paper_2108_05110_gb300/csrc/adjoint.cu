@@ -133,6 +133,7 @@ int reverse_step(mhde_ctx* c, AdjBuffers& b, const double* Sv, const double* Sw,
     launch_transpose_values(nnz, b.tpos, s.Fval, b.FT, b.FTf, s.stream);
     ACU(cudaMemcpyAsync(s.Fval, b.FT, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s.stream));
     ACU(cudaMemcpyAsync(s.Fvalf, b.FTf, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s.stream));
+    launch_fd_values(c, s, s.stream);               // the inner solve's F^T D^{-1}
     if (c->opt.schur == 1) launch_scale_pair((long long)c->fe.Kp.nnz(), -1.0, s.Np, s.Npf, s.stream);
     launch_adj_rhs(c, which == 0 ? b.seedV : b.seedW, s.Bv, s.stream);
     ACU(cudaGetLastError());

@@ -136,6 +136,8 @@ size_t layout(mhde_ctx* c, char* base) {
     s.Fvalf = w.take<float>(nf);
     s.Fdinv = w.take<double>(n2);
     s.Fdinvf = w.take<float>(n2);
+    s.FD = w.take<double>(fe.F.nnz());
+    s.FDf = w.take<float>(fe.F.nnz());
     s.Floc = w.take<double>(nt * 36);
     s.Cloc = w.take<double>(nt * 6 * 2 * Jp);
     s.Bv = w.take<double>(vs);
@@ -1069,6 +1071,7 @@ int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
                        c->opt.conv_form, s.Floc, st);
         launch_F_gather(c, s.Floc, 1.0 / c->dt, 0.5 * (c->nubar + c->nubar_m), s.Fval, s.Fvalf, s.Fdinv,
                         s.Fdinvf, st);
+        launch_fd_values(c, s, st);
         break;
       }
       case 3: {

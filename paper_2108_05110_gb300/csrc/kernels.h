@@ -112,7 +112,7 @@ void launch_Np(const mhde_ctx* c, const double* mean_conv, double* slots, double
                cudaStream_t st);
 // inner per-column GMRES(k) on F (velocity block), z ~ F^{-1} r
 template <typename T>
-void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
+void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* dinv, const T* r, T* z, int ld,
                         int kin, cudaStream_t st);
 // shared-memory limits of the inner and block kernels (set once, before any capture)
 cudaError_t init_inner_attributes();
@@ -129,6 +129,7 @@ int assemble_sub(mhde_ctx* c, int which);
 int solve_sub(mhde_ctx* c, int which, bool zero_guess = false);
 
 // discrete adjoint (kernels_adj.cu)
+void launch_fd_values(const mhde_ctx* c, Sub& s, cudaStream_t st);
 void launch_transpose_values(long long nnz, const int* tpos, const double* F, double* FT, float* FTf,
                              cudaStream_t st);
 void launch_scale_pair(long long n, double s, double* x, float* xf, cudaStream_t st);

@@ -343,6 +343,26 @@ void launch_F_gather(const mhde_ctx* c, const double* Floc, double inv_dt, doubl
                                            Fdinv, Fdinvf);
 }
 
+// FD[k] = F[k] dinv[col[k]] (the inner solve's right-preconditioned operator
+// F D^{-1}, formed once per assembly instead of per application); the float
+// copy is the product of the float values, as the inner kernels formed it.
+__global__ void k_fd_values(long long nnz, const int* __restrict__ col, const double* __restrict__ F,
+                            const float* __restrict__ Ff, const double* __restrict__ dinv,
+                            const float* __restrict__ dinvf, double* __restrict__ FD, float* __restrict__ FDf) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  const int c = col[k];
+  FD[k] = F[k] * dinv[c];
+  FDf[k] = Ff[k] * dinvf[c];
+}
+
+void launch_fd_values(const mhde_ctx* c, Sub& s, cudaStream_t st) {
+  count_launch();
+  const long long nnz = c->F.nnz;
+  k_fd_values<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, c->F.col, s.Fval, s.Fvalf, s.Fdinv, s.Fdinvf,
+                                                             s.FD, s.FDf);
+}
+
 // ------------------------------------------------------------ PCD pressure convection
 // Element slots [e][3][3]: (a . grad psi_k, psi_i) with psi = lambda (P1).
 __global__ void k_Np_local(int nt, const int* __restrict__ dofs, const double* __restrict__ geom,

@@ -51,21 +51,27 @@ __device__ __forceinline__ void st4(double* p, const double v[4]) {
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
-// w[a][:] = sum_k F_ak dinv_k v[col_k][:]
+// w[a][:] = sum_k FD_ak v[col_k][:], FD = F D^{-1} (formed at assembly); two
+// nonzeros per iteration keep two gathers in flight
 template <typename T>
 __global__ void k_fd_spmm(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
-                          const T* __restrict__ F, const T* __restrict__ dinv, const T* __restrict__ v,
-                          T* __restrict__ w) {
+                          const T* __restrict__ FD, const T* __restrict__ v, T* __restrict__ w) {
   using V = typename IVec<T>::type;
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (tid >= (long long)n2 * nch) return;
   int a = (int)(tid / nch), ch = (int)(tid % nch);
   const V* vv = reinterpret_cast<const V*>(v);
   V acc = izero(V());
-  for (int k = rp[a]; k < rp[a + 1]; ++k) {
-    int c = col[k];
-    ifma(acc, F[k] * dinv[c], vv[(size_t)c * nch + ch]);
+  int k = rp[a];
+  const int e = rp[a + 1];
+  for (; k + 1 < e; k += 2) {
+    const int c0 = col[k], c1 = col[k + 1];
+    const T f0 = FD[k], f1 = FD[k + 1];
+    const V x0 = vv[(size_t)c0 * nch + ch], x1 = vv[(size_t)c1 * nch + ch];
+    ifma(acc, f0, x0);
+    ifma(acc, f1, x1);
   }
+  if (k < e) ifma(acc, FD[k], vv[(size_t)col[k] * nch + ch]);
   reinterpret_cast<V*>(w)[(size_t)a * nch + ch] = acc;
 }
 
@@ -303,7 +309,7 @@ cudaError_t init_inner_attributes() {
 }
 
 template <typename T>
-void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
+void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* dinv, const T* r, T* z, int ld,
                         int kin, cudaStream_t st) {
   const int n2 = c->fe.n2, C = 2 * ld;
   const int nch = C / IVec<T>::W;
@@ -328,7 +334,7 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* Fv, const T* d
   for (int i = 0; i < kin; ++i) {
     T* vi = Vb + (size_t)i * vstride;
     T* w = Vb + (size_t)(i + 1) * vstride;
-    k_fd_spmm<T><<<nb((long long)n2 * nch, 256), 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, vi, w);
+    k_fd_spmm<T><<<nb((long long)n2 * nch, 256), 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, FDv, vi, w);
     // one classical Gram-Schmidt pass: dots against v_0..v_i and ||w||^2 in a
     // single sweep; the projected norm follows from the Pythagorean identity
     col_dots<T>(nchunk, threads, shm, st, n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 1, s.ipart);

@@ -144,6 +144,8 @@ struct Sub {                       // one subproblem (v: which = 0, w: which = 1
   float* Fvalf = nullptr;
   double* Fdinv = nullptr;         // [n2]
   float* Fdinvf = nullptr;
+  double* FD = nullptr;            // [nnzF] F[k] * dinv[col[k]]: the inner solve's operator F D^{-1}
+  float* FDf = nullptr;
   double* Floc = nullptr;          // [nt][36] element slot buffer
   double* Cloc = nullptr;          // [nt][6][2][Jp] convection slot buffer of the RHS
   double* Bv = nullptr;            // right-hand sides [n_rows][Jp]

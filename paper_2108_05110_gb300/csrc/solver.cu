@@ -11,6 +11,7 @@
 // M_p the lumped pressure mass.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -51,6 +52,7 @@ template <typename T> struct Prec;
 template <> struct Prec<double> {
   static const double* F(const Sub& s) { return s.Fval; }
   static const double* Fd(const Sub& s) { return s.Fdinv; }
+  static const double* FD(const Sub& s) { return s.FD; }
   static const double* B(const mhde_ctx* c) { return c->B.val; }
   static const double* BT(const mhde_ctx* c) { return c->BT.val; }
   static const double* mp(const mhde_ctx* c) { return c->d_mp; }
@@ -66,6 +68,7 @@ template <> struct Prec<double> {
 template <> struct Prec<float> {
   static const float* F(const Sub& s) { return s.Fvalf; }
   static const float* Fd(const Sub& s) { return s.Fdinvf; }
+  static const float* FD(const Sub& s) { return s.FDf; }
   static const float* B(const mhde_ctx* c) { return c->B.valf; }
   static const float* BT(const mhde_ctx* c) { return c->BT.valf; }
   static const float* mp(const mhde_ctx* c) { return c->d_mpf; }
@@ -151,7 +154,7 @@ static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out, int J
     return;
   }
   if (c->opt.inner_iters > 0) {
-    launch_inner_gmres<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), tk, out, Jp, c->opt.inner_iters, st);
+    launch_inner_gmres<T>(c, s, Prec<T>::FD(s), Prec<T>::Fd(s), tk, out, Jp, c->opt.inner_iters, st);
     return;
   }
   const int nsw = std::max(1, c->opt.jacobi_sweeps);
@@ -170,6 +173,8 @@ static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out, int J
 // and scalars do not change for the lifetime of the context (matrix values are
 // read at execution time), so each (in, out) pair is captured once into a
 // CUDA graph and replayed.
+static std::mutex g_capture_mutex;
+
 template <typename T>
 static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out, int ld) {
   if (!c->use_graphs) {
@@ -179,6 +184,9 @@ static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out, int ld) {
   auto key = std::make_tuple((const void*)in, (const void*)out, ld);
   auto it = s.prec_graphs.find(key);
   if (it == s.prec_graphs.end()) {
+    // one capture at a time in the process: many contexts stepped from many
+    // host threads (mhde_advance_many) otherwise capture concurrently
+    std::lock_guard<std::mutex> lock(g_capture_mutex);
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -420,7 +428,7 @@ static int poly_setup(mhde_ctx* c, Sub& s) {
   const int d = c->opt.poly_degree, C = 4;
   cudaStream_t st = s.stream;
   T* zscratch = (T*)s.Pk;                    // output of the setup solve is not used
-  launch_inner_gmres<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), (const T*)c->d_prand, zscratch, 2, d, st);
+  launch_inner_gmres<T>(c, s, Prec<T>::FD(s), Prec<T>::Fd(s), (const T*)c->d_prand, zscratch, 2, d, st);
   std::vector<double> Hall((size_t)(d + 1) * d * C), H((size_t)(d + 1) * d);
   SCU(cudaMemcpyAsync(Hall.data(), s.ih, Hall.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   SCU(cudaStreamSynchronize(st));
@@ -456,6 +464,7 @@ int assemble_sub(mhde_ctx* c, int which) {
   launch_F_local(c->fe.nt, c->d_dofs, c->d_geom, mean_conv, l2, 2.0 * c->opt.mu * c->dt,
                  c->opt.conv_form, s.Floc, st);
   launch_F_gather(c, s.Floc, 1.0 / c->dt, nu_hat, s.Fval, s.Fvalf, s.Fdinv, s.Fdinvf, st);
+  launch_fd_values(c, s, st);
   if (c->opt.schur == 1) launch_Np(c, mean_conv, s.Floc, s.Np, s.Npf, st);   // slots reuse Floc
   launch_rhs_conv_local(c->fe.nt, c->J, c->Jp, c->d_dofs, c->d_geom, s.S, o.S, mean_conv,
                         c->opt.conv_form, s.Cloc, st);
