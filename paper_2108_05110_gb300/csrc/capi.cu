@@ -642,6 +642,11 @@ static int run_sub(mhde_ctx* c, int which) {
     if (e != cudaSuccess) {
       s.err = std::string("stream: ") + cudaGetErrorString(e);
       rc = MHDE_ECUDA;
+    } else if (take_async_error(s.stream) != 0) {
+      // a Gram launch gave up waiting for a TMA stage (bounded wait): the
+      // solve used incomplete projections, so the step is not accepted
+      s.err = "a block Gram launch timed out waiting for its shared-memory stage";
+      rc = MHDE_ECUDA;
     }
   }
   s.status = rc;

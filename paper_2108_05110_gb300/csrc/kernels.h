@@ -79,6 +79,9 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
                  int nchunk, double* part, double* gram, cudaStream_t st, bool reduce = true);
 // G = [H_0 .. H_k, W^T W] (r x r blocks) -> block k+2 := W^T W - sum_i H_i^T H_i
 void launch_proj_gram(double* G, int k, int r, cudaStream_t st);
+// 1 if a staged-Gram launch gave up waiting for a TMA stage since the last
+// call (the flag is then cleared), 0 if not, -1 on a CUDA error
+int take_async_error(cudaStream_t st);
 // C_i = -H_i T (i <= k), C_{k+1} = T, converted to the Krylov precision
 template <typename T>
 void launch_make_coef(const double* G, const double* Tm, int k, int r, T* C, cudaStream_t st);

@@ -636,34 +636,65 @@ __global__ void __launch_bounds__(256) k_gram_reduce(int nparts, int total, cons
 }
 
 // Staged Gram (FP32): a CTA owns a range of rows and streams it through a
-// GS_NST-deep ring of shared-memory stages with cp.async; one stage holds TR
-// rows of every basis block and of W (each block's rows are contiguous in
-// memory, so every copy is a coalesced 16-byte piece).  A thread owns one item
-// (basis block i, 4-column group p4) and keeps its 4 x W products in
-// registers; the W row is a shared-memory broadcast.  A block's tile is
-// padded so that consecutive items read consecutive 16-byte words (no bank
-// conflicts).  With few items a CTA runs S row slices, each writing its own
-// partial, so every sum has a fixed order.
+// GS_NST-deep ring of shared-memory stages.  One stage holds TR rows of every
+// basis block and of W; each block's rows are one contiguous span in memory,
+// so one thread fills a stage with one TMA bulk copy per block
+// (cp.async.bulk, completion counted in bytes on the stage's mbarrier).  A
+// thread owns one item (basis block i, 4-column group p4) and keeps its 4 x W
+// products in registers; the W row is a shared-memory broadcast.  A block's
+// tile is padded so that consecutive items read consecutive 16-byte words (no
+// bank conflicts).  With few items a CTA runs S row slices, each writing its
+// own partial, so every sum has a fixed order.
+//
+// Every wait on a stage's mbarrier is bounded: past GS_SPIN_LIMIT polls the
+// thread records the failure in g_async_err, waits (again bounded) for the
+// CTA's copies still in flight, and the kernel returns without its partials.
 constexpr int GS_T = 256;
 constexpr int GS_NST = 3;
 constexpr size_t GS_SMEM = 192 * 1024;
+constexpr size_t GS_BAR_BYTES = 64;                   // mbarriers in front of the stages
+constexpr long long GS_SPIN_LIMIT = 1ll << 24;
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ int g_async_err = 0;
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait for phase `parity` of the barrier; false after the limit
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  for (long long it = 0; it < GS_SPIN_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 template <int W>
-__global__ void __launch_bounds__(GS_T) k_gram_staged(const float* __restrict__ V, size_t vstride, int kblocks,
+__global__ void __launch_bounds__(GS_T, 1) k_gram_staged(const float* __restrict__ V, size_t vstride, int kblocks,
                                                       const float* __restrict__ Wm, int n_rows, int ld, int r,
                                                       int rows_per_chunk, int S, int TR, int tstride,
                                                       double* __restrict__ part) {
-  extern __shared__ __align__(16) float gsm[];
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
+  float* gsm = reinterpret_cast<float*>(gsm_raw + GS_BAR_BYTES);
+  const unsigned bar0 = smem_u32(gsm_raw);            // GS_NST 8-byte barriers
   const int stage_floats = kblocks * tstride + TR * ld;
   const int P4 = (r + 3) / 4;
   const int items = kblocks * P4;
@@ -672,31 +703,46 @@ __global__ void __launch_bounds__(GS_T) k_gram_staged(const float* __restrict__ 
   const int i = item / P4, p4 = item % P4;
   const int r0 = blockIdx.x * rows_per_chunk, r1 = min(n_rows, r0 + rows_per_chunk);
   const int ntiles = r1 > r0 ? (r1 - r0 + TR - 1) / TR : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GS_NST; ++s) mbar_init(bar0 + 8 * s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  __syncthreads();
+  // one thread fills a stage: (kblocks + 1) contiguous spans of nr * ld floats
   auto issue = [&](int tile) {
-    if (tile < ntiles) {
-      float* st = gsm + (size_t)(tile % GS_NST) * stage_floats;
-      const int t0 = r0 + tile * TR;
-      const int nseg = min(TR, r1 - t0) * ld / 4;      // 16-byte pieces of one block's rows
-      const int total = (kblocks + 1) * nseg;
-      for (int e = threadIdx.x; e < total; e += GS_T) {
-        const int b = e / nseg, off = e - b * nseg;
-        const float* src = (b < kblocks ? V + (size_t)b * vstride : Wm) + (size_t)t0 * ld + 4 * off;
-        cp_async16(st + (size_t)b * tstride + 4 * off, src);
-      }
+    if (tile >= ntiles) return;
+    const int s = tile % GS_NST;
+    float* st = gsm + (size_t)s * stage_floats;
+    const int t0 = r0 + tile * TR;
+    const unsigned bytes = (unsigned)(min(TR, r1 - t0) * ld) * 4u;
+    const unsigned bar = bar0 + 8 * s;
+    // the stage's previous contents were read through the generic proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, bytes * (unsigned)(kblocks + 1));
+    for (int b = 0; b <= kblocks; ++b) {
+      const float* src = (b < kblocks ? V + (size_t)b * vstride : Wm) + (size_t)t0 * ld;
+      bulk_g2s(smem_u32(st + (size_t)b * tstride), src, bytes, bar);
     }
-    cp_async_commit();                                  // one group per tile, possibly empty
   };
   float acc[4][W];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
 #pragma unroll
     for (int q = 0; q < W; ++q) acc[e][q] = 0.f;
-#pragma unroll
-  for (int s = 0; s < GS_NST - 1; ++s) issue(s);
+  if (threadIdx.x == 0)
+    for (int s = 0; s < GS_NST - 1; ++s) issue(s);
+  int ok = 1;
+  int waited = 0;                                      // tiles whose copies this CTA has seen land
   for (int tile = 0; tile < ntiles; ++tile) {
-    cp_async_wait<GS_NST - 2>();                        // this thread's copies of `tile` landed
-    __syncthreads();                                    // everyone's did; stage tile-1 is free
-    issue(tile + GS_NST - 1);
+    const unsigned bar = bar0 + 8 * (tile % GS_NST);
+    const bool landed = mbar_wait_bounded(bar, (unsigned)((tile / GS_NST) & 1));
+    if (!__syncthreads_and(landed ? 1 : 0)) {        // stage tile-1 is free once everyone is here
+      ok = 0;
+      break;
+    }
+    waited = tile + 1;
+    if (threadIdx.x == 0) issue(tile + GS_NST - 1);
     if (active) {
       const float* st = gsm + (size_t)(tile % GS_NST) * stage_floats;
       const int nr = min(TR, r1 - (r0 + tile * TR));
@@ -718,7 +764,17 @@ __global__ void __launch_bounds__(GS_T) k_gram_staged(const float* __restrict__ 
       }
     }
   }
-  cp_async_wait<0>();
+  if (!ok) {
+    // a stage did not land in time: record it, give every copy this CTA
+    // issued a bounded chance to finish, and leave without partials
+    if (threadIdx.x == 0) {
+      atomicExch(&g_async_err, 1);
+      const int issued = min(ntiles, waited + GS_NST - 1);
+      for (int tl = waited; tl < issued; ++tl)
+        mbar_wait_bounded(bar0 + 8 * (tl % GS_NST), (unsigned)((tl / GS_NST) & 1));
+    }
+    return;
+  }
   if (!active) return;
   double* dst = part + ((size_t)(blockIdx.x * S + slice) * kblocks + i) * r * r;
 #pragma unroll
@@ -731,6 +787,16 @@ __global__ void __launch_bounds__(GS_T) k_gram_staged(const float* __restrict__ 
   }
 }
 
+// Reads and clears the bounded-wait failure flag of the staged Gram (set when
+// a TMA stage did not land within its poll limit).
+int take_async_error(cudaStream_t st) {
+  int h = 0, zero = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_async_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  if (h) cudaMemcpyToSymbolAsync(g_async_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  return h;
+}
+
 // Stage geometry of the staged Gram: rows per stage (a multiple of 8, at most
 // 128) so that GS_NST stages fit in GS_SMEM, and the padded block-tile stride.
 static bool gram_staged_plan(int kblocks, int ld, int r, int& TR, int& tstride, size_t& smem) {
@@ -738,7 +804,7 @@ static bool gram_staged_plan(int kblocks, int ld, int r, int& TR, int& tstride, 
   for (TR = 128; TR >= 8; TR -= 8) {
     const int pad = ((4 * P4 - TR * ld) % 32 + 32) % 32;
     tstride = TR * ld + pad;
-    smem = (size_t)GS_NST * ((size_t)kblocks * tstride + (size_t)TR * ld) * sizeof(float);
+    smem = GS_BAR_BYTES + (size_t)GS_NST * ((size_t)kblocks * tstride + (size_t)TR * ld) * sizeof(float);
     if (smem <= GS_SMEM) return true;
   }
   return false;
@@ -819,12 +885,11 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
                  int nchunk, double* part, double* gram, cudaStream_t st, bool reduce) {
   count_launch(reduce ? 2 : 1);
   const GramDevice& gd = gram_setup();               // on failure the unstaged kernels run instead
-  const int items = kblocks * ((r + 3) / 4);
   const int w = (r + 3) / 4 * 4;
   int nparts = nchunk;
   int TR = 0, tstride = 0;
   size_t smem = 0;
-  const bool staged = gd.err == cudaSuccess && sizeof(T) == 4 && items <= GS_T && w <= 24 &&
+  const bool staged = gd.err == cudaSuccess && sizeof(T) == 4 && kblocks * ((r + 3) / 4) <= GS_T && w <= 24 &&
                       gram_staged_plan(kblocks, Jp, r, TR, tstride, smem);
   if (staged) {
     const float* Vf = reinterpret_cast<const float*>(V);
