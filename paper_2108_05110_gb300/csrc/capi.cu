@@ -347,7 +347,10 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
     return MHDE_ESTAB;
   }
   c->nchunk = std::max(1, std::min(304, (c->n_rows + 255) / 256));
-  c->nchunk_in = std::max(1, std::min(1024, (c->fe.n2 + 127) / 128));
+  // rows per partial-sum chunk of the inner dot products (MHDE_INNER_ROWS to experiment)
+  int inner_rows = 128;
+  if (const char* ir = std::getenv("MHDE_INNER_ROWS")) inner_rows = std::max(16, std::atoi(ir));
+  c->nchunk_in = std::max(1, std::min(1024, (c->fe.n2 + inner_rows - 1) / inner_rows));
   const char* se = std::getenv("MHDE_SERIAL");
   c->serial = se && se[0] == '1';
   const char* tr = std::getenv("MHDE_TRACE");

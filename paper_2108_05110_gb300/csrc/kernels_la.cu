@@ -7,6 +7,7 @@
 // a row are broadcast to the threads sharing that row.
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 
 #include "kernels.h"
@@ -687,20 +688,26 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
                : "memory");
 }
 
-template <int W>
-__global__ void __launch_bounds__(GS_T, 1) k_gram_staged(const float* __restrict__ V, size_t vstride, int kblocks,
+template <int W, int PC, int NTH>
+__global__ void __launch_bounds__(NTH, 1) k_gram_staged(const float* __restrict__ V, size_t vstride, int kblocks,
                                                       const float* __restrict__ Wm, int n_rows, int ld, int r,
                                                       int rows_per_chunk, int S, int TR, int tstride,
                                                       double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char gsm_raw[];
+  // every bulk copy needs 16-byte aligned tiles and rows; the host plan
+  // guarantees it, and a launch that breaks it copies nothing
+  if ((tstride & 3) || (ld & 3) || ((TR * ld) & 3)) {
+    if (threadIdx.x == 0) atomicExch(&g_async_err, 1);
+    return;
+  }
   float* gsm = reinterpret_cast<float*>(gsm_raw + GS_BAR_BYTES);
   const unsigned bar0 = smem_u32(gsm_raw);            // GS_NST 8-byte barriers
   const int stage_floats = kblocks * tstride + TR * ld;
-  const int P4 = (r + 3) / 4;
-  const int items = kblocks * P4;
+  const int NP = (r + PC - 1) / PC;                    // column groups of PC per block
+  const int items = kblocks * NP;
   const int slice = threadIdx.x / items, item = threadIdx.x % items;
   const bool active = slice < S;
-  const int i = item / P4, p4 = item % P4;
+  const int i = item / NP, pg = item % NP;
   const int r0 = blockIdx.x * rows_per_chunk, r1 = min(n_rows, r0 + rows_per_chunk);
   const int ntiles = r1 > r0 ? (r1 - r0 + TR - 1) / TR : 0;
   if (threadIdx.x == 0) {
@@ -709,7 +716,9 @@ __global__ void __launch_bounds__(GS_T, 1) k_gram_staged(const float* __restrict
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
   __syncthreads();
-  // one thread fills a stage: (kblocks + 1) contiguous spans of nr * ld floats
+  // warp 0 fills a stage: (kblocks + 1) contiguous spans of nr * ld floats,
+  // lane 0 registering the stage's bytes, then one bulk copy per lane
+  const int lane = threadIdx.x & 31;
   auto issue = [&](int tile) {
     if (tile >= ntiles) return;
     const int s = tile % GS_NST;
@@ -719,18 +728,19 @@ __global__ void __launch_bounds__(GS_T, 1) k_gram_staged(const float* __restrict
     const unsigned bar = bar0 + 8 * s;
     // the stage's previous contents were read through the generic proxy
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    mbar_expect_tx(bar, bytes * (unsigned)(kblocks + 1));
-    for (int b = 0; b <= kblocks; ++b) {
+    if (lane == 0) mbar_expect_tx(bar, bytes * (unsigned)(kblocks + 1));
+    __syncwarp();
+    for (int b = lane; b <= kblocks; b += 32) {
       const float* src = (b < kblocks ? V + (size_t)b * vstride : Wm) + (size_t)t0 * ld;
       bulk_g2s(smem_u32(st + (size_t)b * tstride), src, bytes, bar);
     }
   };
-  float acc[4][W];
+  float acc[PC][W];
 #pragma unroll
-  for (int e = 0; e < 4; ++e)
+  for (int e = 0; e < PC; ++e)
 #pragma unroll
     for (int q = 0; q < W; ++q) acc[e][q] = 0.f;
-  if (threadIdx.x == 0)
+  if (threadIdx.x < 32)
     for (int s = 0; s < GS_NST - 1; ++s) issue(s);
   int ok = 1;
   int waited = 0;                                      // tiles whose copies this CTA has seen land
@@ -742,22 +752,28 @@ __global__ void __launch_bounds__(GS_T, 1) k_gram_staged(const float* __restrict
       break;
     }
     waited = tile + 1;
-    if (threadIdx.x == 0) issue(tile + GS_NST - 1);
+    if (threadIdx.x < 32) issue(tile + GS_NST - 1);
     if (active) {
       const float* st = gsm + (size_t)(tile % GS_NST) * stage_floats;
       const int nr = min(TR, r1 - (r0 + tile * TR));
-      const float* vt = st + (size_t)i * tstride + 4 * p4;
+      const float* vt = st + (size_t)i * tstride + PC * pg;
       const float* wt = st + (size_t)kblocks * tstride;
 #pragma unroll 2
       for (int rr = slice; rr < nr; rr += S) {
-        float v[4];
-        row_ld4(vt + rr * ld, v);
+        float v[PC];
+        if constexpr (PC == 4) {
+          row_ld4(vt + rr * ld, v);
+        } else {
+          const float2 t2 = *reinterpret_cast<const float2*>(vt + rr * ld);
+          v[0] = t2.x;
+          v[PC - 1] = t2.y;
+        }
 #pragma unroll
         for (int q4 = 0; q4 < W / 4; ++q4) {
           float w[4];
           row_ld4(wt + rr * ld + 4 * q4, w);
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
+          for (int e = 0; e < PC; ++e)
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc[e][4 * q4 + u] = fmaf(v[e], w[u], acc[e][4 * q4 + u]);
         }
@@ -778,8 +794,8 @@ __global__ void __launch_bounds__(GS_T, 1) k_gram_staged(const float* __restrict
   if (!active) return;
   double* dst = part + ((size_t)(blockIdx.x * S + slice) * kblocks + i) * r * r;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int pr = 4 * p4 + e;
+  for (int e = 0; e < PC; ++e) {
+    const int pr = PC * pg + e;
     if (pr >= r) break;
 #pragma unroll
     for (int q = 0; q < W; ++q)
@@ -799,28 +815,32 @@ int take_async_error(cudaStream_t st) {
 
 // Stage geometry of the staged Gram: rows per stage (a multiple of 8, at most
 // 128) so that GS_NST stages fit in GS_SMEM, and the padded block-tile stride.
-static bool gram_staged_plan(int kblocks, int ld, int r, int& TR, int& tstride, size_t& smem) {
-  const int P4 = (r + 3) / 4;
+static bool gram_staged_plan(int kblocks, int ld, int r, int pc, int& TR, int& tstride, size_t& smem) {
+  const int NP = (r + pc - 1) / pc;
   for (TR = 128; TR >= 8; TR -= 8) {
-    const int pad = ((4 * P4 - TR * ld) % 32 + 32) % 32;
+    // consecutive items read consecutive pc-float words across block tiles too,
+    // as far as the 16-byte alignment of every tile (a TMA bulk-copy
+    // destination) allows: the pad is a multiple of 4 floats
+    const int pad = ((((pc * NP - TR * ld) % 32 + 32) % 32) + 3) / 4 * 4 % 32;
     tstride = TR * ld + pad;
+    if (tstride % 4 != 0 || (TR * ld) % 4 != 0) return false;
     smem = GS_BAR_BYTES + (size_t)GS_NST * ((size_t)kblocks * tstride + (size_t)TR * ld) * sizeof(float);
     if (smem <= GS_SMEM) return true;
   }
   return false;
 }
 
-template <int W>
+template <int W, int PC, int NTH>
 static void gram_staged(const float* V, size_t vstride, int kblocks, const float* Wm, int n_rows, int ld, int r,
                         int nchunk, int nsm, int TR, int tstride, size_t smem, double* part, cudaStream_t st,
                         int& nparts) {
-  const int items = kblocks * ((r + 3) / 4);
-  const int S = std::max(1, std::min(GS_T / items, nchunk));
+  const int items = kblocks * ((r + PC - 1) / PC);
+  const int S = std::max(1, std::min(NTH / items, nchunk));
   const int nctas = std::max(1, std::min(nchunk / S, nsm));
   const int rows_per_chunk = (n_rows + nctas - 1) / nctas;
   nparts = nctas * S;
-  k_gram_staged<W><<<nctas, GS_T, smem, st>>>(V, vstride, kblocks, Wm, n_rows, ld, r, rows_per_chunk, S, TR,
-                                             tstride, part);
+  k_gram_staged<W, PC, NTH><<<nctas, NTH, smem, st>>>(V, vstride, kblocks, Wm, n_rows, ld, r, rows_per_chunk, S,
+                                                      TR, tstride, part);
 }
 
 // Per-device one-time setup of the Gram kernels (shared-memory limits and the
@@ -849,12 +869,18 @@ static const GramDevice& gram_setup() {
   auto set = [&](const void* f, int bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   };
-  set((const void*)k_gram_staged<4>, (int)GS_SMEM);
-  set((const void*)k_gram_staged<8>, (int)GS_SMEM);
-  set((const void*)k_gram_staged<12>, (int)GS_SMEM);
-  set((const void*)k_gram_staged<16>, (int)GS_SMEM);
-  set((const void*)k_gram_staged<20>, (int)GS_SMEM);
-  set((const void*)k_gram_staged<24>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<4, 4, 256>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<4, 2, 512>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<8, 4, 256>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<8, 2, 512>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<12, 4, 256>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<12, 2, 512>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<16, 4, 256>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<16, 2, 512>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<20, 4, 256>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<20, 2, 512>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<24, 4, 256>, (int)GS_SMEM);
+  set((const void*)k_gram_staged<24, 2, 512>, (int)GS_SMEM);
   set((const void*)k_gram<float>, 160 * 1024);
   set((const void*)k_gram<double>, 160 * 1024);
   d.err = e;
@@ -889,13 +915,27 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
   int nparts = nchunk;
   int TR = 0, tstride = 0;
   size_t smem = 0;
-  const bool staged = gd.err == cudaSuccess && sizeof(T) == 4 && kblocks * ((r + 3) / 4) <= GS_T && w <= 24 &&
-                      gram_staged_plan(kblocks, Jp, r, TR, tstride, smem);
+  // item width: 2 columns per thread and 512 threads (16 warps per SM) unless
+  // MHDE_GRAM_PC=4 asks for 4 columns and 256 threads
+  static const int pc_env = [] {
+    const char* e = std::getenv("MHDE_GRAM_PC");
+    return (e && std::atoi(e) == 4) ? 4 : 2;
+  }();
+  const int pc = pc_env, nth = pc == 4 ? 256 : 512;
+  const bool staged = gd.err == cudaSuccess && sizeof(T) == 4 && kblocks * ((r + pc - 1) / pc) <= nth && w <= 24 &&
+                      gram_staged_plan(kblocks, Jp, r, pc, TR, tstride, smem);
   if (staged) {
     const float* Vf = reinterpret_cast<const float*>(V);
     const float* Wf = reinterpret_cast<const float*>(W);
-#define MHDE_GS(WV) \
-  gram_staged<WV>(Vf, vstride, kblocks, Wf, n_rows, Jp, r, nchunk, gd.nsm, TR, tstride, smem, part, st, nparts)
+#define MHDE_GS(WV)                                                                                            \
+  do {                                                                                                         \
+    if (pc == 4)                                                                                               \
+      gram_staged<WV, 4, 256>(Vf, vstride, kblocks, Wf, n_rows, Jp, r, nchunk, gd.nsm, TR, tstride, smem, part, \
+                              st, nparts);                                                                     \
+    else                                                                                                       \
+      gram_staged<WV, 2, 512>(Vf, vstride, kblocks, Wf, n_rows, Jp, r, nchunk, gd.nsm, TR, tstride, smem, part, \
+                              st, nparts);                                                                     \
+  } while (0)
     switch (w) {
       case 4: MHDE_GS(4); break;
       case 8: MHDE_GS(8); break;
