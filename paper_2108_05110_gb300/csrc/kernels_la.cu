@@ -843,6 +843,8 @@ static void gram_staged(const float* V, size_t vstride, int kblocks, const float
                                                       TR, tstride, part);
 }
 
+static cudaError_t combine_staged_attr();
+
 // Per-device one-time setup of the Gram kernels (shared-memory limits and the
 // SM count that sizes the staged grid), done under a mutex because the two
 // subproblems call in from their own host threads.
@@ -882,6 +884,7 @@ static const GramDevice& gram_setup() {
   set((const void*)k_gram_staged<24, 4, 256>, (int)GS_SMEM);
   set((const void*)k_gram_staged<24, 2, 512>, (int)GS_SMEM);
   set((const void*)k_gram<float>, 160 * 1024);
+  if (e == cudaSuccess) e = combine_staged_attr();
   set((const void*)k_gram<double>, 160 * 1024);
   d.err = e;
   d.ready = true;
@@ -1133,9 +1136,173 @@ __global__ void __launch_bounds__(COMB_T) k_block_combine(T* out, const T* in, T
   }
 }
 
+// Staged combination (FP32, W <= 24): a CTA owns CB_ROWS consecutive rows and
+// streams that row range of every basis block through a CB_NST-deep ring of
+// shared-memory stages, one TMA bulk copy per block (the rows of a block are
+// one contiguous span), completion on the stage's mbarrier with the same
+// bounded waits as the staged Gram.  A thread owns two rows; the coefficient
+// blocks sit in shared memory (zero-padded to W x W) and are read as
+// broadcasts.  out may alias a basis block or in: a CTA reads all of its
+// rows before writing them.
+constexpr int CB_T = 128;
+constexpr int CB_ROWS = 2 * CB_T;
+constexpr int CB_NST = 3;
+constexpr size_t CB_COEF_MAX = 96 * 1024;
+
+template <int W>
+__global__ void __launch_bounds__(CB_T) k_combine_staged(float* out, const float* in, float alpha, const float* V,
+                                                       size_t vstride, int kblocks, int r_in,
+                                                       const float* __restrict__ C, int r_out, int n_rows, int ldv,
+                                                       int ldo) {
+  extern __shared__ __align__(16) unsigned char cb_raw[];
+  if ((ldv & 3) || (ldo & 3)) {                        // 16-byte rows for the bulk copies
+    if (threadIdx.x == 0) atomicExch(&g_async_err, 1);
+    return;
+  }
+  const unsigned bar0 = smem_u32(cb_raw);
+  float* stages = reinterpret_cast<float*>(cb_raw + GS_BAR_BYTES);
+  const int stage_floats = CB_ROWS * ldv;
+  float* Cs = stages + (size_t)CB_NST * stage_floats;   // [kblocks][W][W]
+  const int r0 = blockIdx.x * CB_ROWS;
+  const int nr = min(CB_ROWS, n_rows - r0);
+  const unsigned bytes = (unsigned)(nr * ldv) * 4u;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < CB_NST; ++s) mbar_init(bar0 + 8 * s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int b) {                            // thread 0: block b's rows into stage b % CB_NST
+    if (b >= kblocks) return;
+    const unsigned bar = bar0 + 8 * (b % CB_NST);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(smem_u32(stages + (size_t)(b % CB_NST) * stage_floats), V + (size_t)b * vstride + (size_t)r0 * ldv,
+             bytes, bar);
+  };
+  if (threadIdx.x == 0)
+    for (int b = 0; b < CB_NST - 1; ++b) issue(b);
+  for (int e = threadIdx.x; e < kblocks * W * W; e += CB_T) {
+    const int q = e % W, pp = (e / W) % W, ib = e / (W * W);
+    Cs[e] = (pp < r_in && q < r_out) ? C[((size_t)ib * r_in + pp) * r_out + q] : 0.f;
+  }
+  float acc[2][W];
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int q = 0; q < W; ++q) acc[s][q] = 0.f;
+  const int np4 = (r_in + 3) / 4;
+  int ok = 1, waited = 0;
+  for (int b = 0; b < kblocks; ++b) {
+    const bool landed = mbar_wait_bounded(bar0 + 8 * (b % CB_NST), (unsigned)((b / CB_NST) & 1));
+    if (!__syncthreads_and(landed ? 1 : 0)) {        // also: coefficients staged, stage b-1 free
+      ok = 0;
+      break;
+    }
+    waited = b + 1;
+    if (threadIdx.x == 0) issue(b + CB_NST - 1);
+    const float* st = stages + (size_t)(b % CB_NST) * stage_floats;
+    const float* cb = Cs + (size_t)b * W * W;
+    float v[2][W];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int rr = threadIdx.x + s * CB_T;
+#pragma unroll
+      for (int p4 = 0; p4 < W / 4; ++p4) {
+        if (p4 < np4 && rr < nr) {
+          row_ld4(st + (size_t)rr * ldv + 4 * p4, &v[s][4 * p4]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[s][4 * p4 + e] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int pp = 0; pp < W; ++pp)
+        if (pp >= r_in) v[s][pp] = 0.f;
+    }
+#pragma unroll
+    for (int pp = 0; pp < W; ++pp) {
+      const float* cp = cb + pp * W;
+#pragma unroll
+      for (int q4 = 0; q4 < W / 4; ++q4) {
+        float c[4];
+        row_ld4(cp + 4 * q4, c);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[s][4 * q4 + u] = fmaf(v[s][pp], c[u], acc[s][4 * q4 + u]);
+      }
+    }
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      atomicExch(&g_async_err, 1);
+      const int issued = min(kblocks, waited + CB_NST - 1);
+      for (int b = waited; b < issued; ++b) mbar_wait_bounded(bar0 + 8 * (b % CB_NST), (unsigned)((b / CB_NST) & 1));
+    }
+    return;
+  }
+  const int ldo4 = ldo / 4;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int row = r0 + threadIdx.x + s * CB_T;
+    if (row >= n_rows) continue;
+    float* orow = out + (size_t)row * ldo;
+    const float* irow = in ? in + (size_t)row * ldo : nullptr;
+#pragma unroll
+    for (int q4 = 0; q4 < W / 4; ++q4) {
+      if (q4 >= ldo4) break;
+      float res[4];
+      if (irow) {
+        row_ld4(irow + 4 * q4, res);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) res[u] = alpha * res[u] + acc[s][4 * q4 + u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) res[u] = acc[s][4 * q4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * q4 + u >= r_out) res[u] = 0.f;
+      row_st4(orow + 4 * q4, res);
+    }
+    const float z[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q4 = W / 4; q4 < ldo4; ++q4) row_st4(orow + 4 * q4, z);
+  }
+}
+
+static cudaError_t combine_staged_attr() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM);
+  };
+  set((const void*)k_combine_staged<4>);
+  set((const void*)k_combine_staged<8>);
+  set((const void*)k_combine_staged<12>);
+  set((const void*)k_combine_staged<16>);
+  set((const void*)k_combine_staged<20>);
+  set((const void*)k_combine_staged<24>);
+  return e;
+}
+
+static size_t combine_staged_smem(int kblocks, int W, int ldv) {
+  return GS_BAR_BYTES + (size_t)CB_NST * CB_ROWS * ldv * sizeof(float) + (size_t)kblocks * W * W * sizeof(float);
+}
+
 template <typename T, int W>
 static void combine_w(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
                       const T* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4 && W <= 24) {
+    const size_t smem = combine_staged_smem(kblocks, W, ldv);
+    if ((size_t)kblocks * W * W * sizeof(float) <= CB_COEF_MAX && smem <= GS_SMEM && ldv % 4 == 0 && ldo % 4 == 0 &&
+        gram_setup().err == cudaSuccess) {
+      k_combine_staged<W><<<nblk(n_rows, CB_ROWS), CB_T, smem, st>>>(
+          reinterpret_cast<float*>(out), reinterpret_cast<const float*>(in), (float)alpha,
+          reinterpret_cast<const float*>(V), vstride, kblocks, r_in, reinterpret_cast<const float*>(C), r_out,
+          n_rows, ldv, ldo);
+      return;
+    }
+  }
   constexpr int RPT = (sizeof(T) == 4 && W <= 24) ? 2 : 1;
   const size_t per_block = (size_t)W * W * sizeof(T);
   const int kgroup = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(kblocks, 1), COMB_SMEM / per_block));
