@@ -136,13 +136,12 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
   }
 }
 
-// Per-column least squares min || beta e_1 - H y || by Givens rotations for
-// column c (one thread; h, g: shared scratch of (KIN_MAX+1) x KIN_MAX and
-// KIN_MAX+1 doubles).  y is written as doubles, then a float copy.
-__device__ void col_lsq(int C, int kin, int c, const double* __restrict__ H, double beta, double (*h)[KIN_MAX],
-                        double* g, double* __restrict__ y) {
-  for (int l = 0; l <= kin; ++l)
-    for (int i = 0; i < kin; ++i) h[l][i] = (l <= i + 1) ? H[((size_t)l * kin + i) * C + c] : 0.0;
+// Per-column least squares min || beta e_1 - H y || by Givens rotations
+// (one thread; h: the column's (kin+1) x kin Hessenberg matrix, already in
+// shared memory; g, yl: shared scratch of KIN_MAX+1 doubles).  y is written
+// as doubles, then a float copy; nothing is read back from global memory.
+__device__ void col_lsq(int C, int kin, int c, double (*h)[KIN_MAX], double beta, double* g, double* yl,
+                        double* __restrict__ y) {
   for (int l = 0; l <= kin; ++l) g[l] = 0.0;
   g[0] = beta;
   for (int i = 0; i < kin; ++i) {
@@ -160,11 +159,14 @@ __device__ void col_lsq(int C, int kin, int c, const double* __restrict__ H, dou
   }
   for (int i = kin - 1; i >= 0; --i) {
     double sum = g[i];
-    for (int j = i + 1; j < kin; ++j) sum -= h[i][j] * y[(size_t)j * C + c];
-    y[(size_t)i * C + c] = h[i][i] != 0.0 ? sum / h[i][i] : 0.0;
+    for (int j = i + 1; j < kin; ++j) sum -= h[i][j] * yl[j];
+    yl[i] = h[i][i] != 0.0 ? sum / h[i][i] : 0.0;
   }
   float* yf = reinterpret_cast<float*>(y + (size_t)kin * C);
-  for (int i = 0; i < kin; ++i) yf[(size_t)i * C + c] = (float)y[(size_t)i * C + c];
+  for (int i = 0; i < kin; ++i) {
+    y[(size_t)i * C + c] = yl[i];
+    yf[(size_t)i * C + c] = (float)yl[i];
+  }
 }
 
 // Reduce the partial dots over chunks and update the Hessenberg column i.
@@ -174,7 +176,10 @@ __device__ void col_lsq(int C, int kin, int c, const double* __restrict__ H, dou
 // from the Pythagorean identity, H[i+1][i] = norm, inv[col] = 1/norm;
 // mode 2: initial norms beta[col], inv[col] = 1/beta; mode 3: single pass,
 // H[l][i] = h and the norm as in mode 1.  With y given, the launch of the last
-// step (i = kin - 1) also solves the column's least-squares problem into y.
+// step (i = kin - 1) also solves the column's least-squares problem into y:
+// the earlier Hessenberg columns are staged into shared memory by all threads
+// while the partial sums are reduced, so the serial part touches no global
+// memory it has to wait for.
 constexpr int RED_T = 32 * (KIN_MAX + 2);
 
 __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl, int kin,
@@ -185,8 +190,18 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
   __shared__ double sh[KIN_MAX + 2];
   __shared__ double lh[KIN_MAX + 1][KIN_MAX];
   __shared__ double lg[KIN_MAX + 1];
+  __shared__ double ly[KIN_MAX + 1];
   const int c = blockIdx.x;
   const int nout = nl + ((mode == 1 || mode == 3) ? 1 : 0);
+  const bool solve = y && i == kin - 1 && (mode == 1 || mode == 3);
+  if (solve) {
+    // H as the earlier launches left it (column i too, for the mode-1 sum);
+    // entries below the subdiagonal are zero
+    for (int e = threadIdx.x; e < (kin + 1) * kin; e += blockDim.x) {
+      const int l = e / kin, j = e - l * kin;
+      lh[l][j] = (l <= j + 1 && j <= i) ? H[((size_t)l * kin + j) * C + c] : 0.0;
+    }
+  }
   const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
   if (l < nout) {
     double s = 0.0;
@@ -208,6 +223,7 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
     ss += sv * sv;
     if (mode == 0 || mode == 3) H[((size_t)t * kin + i) * C + c] = sv;
     if (mode == 1) H[((size_t)t * kin + i) * C + c] += sv;
+    if (solve) lh[t][i] = (mode == 3) ? sv : lh[t][i] + sv;
   }
   if (mode == 1 || mode == 3) {
     const double n2v = sh[nl] - ss;
@@ -216,7 +232,10 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
     inv[c] = nrm > 0.0 ? 1.0 / nrm : 0.0;
     reinterpret_cast<float*>(inv + C)[c] = (float)inv[c];
     // after the last Arnoldi step, this column's least-squares problem
-    if (y && i == kin - 1) col_lsq(C, kin, c, H, beta[c], lh, lg, y);
+    if (solve) {
+      lh[i + 1][i] = nrm;
+      col_lsq(C, kin, c, lh, beta[c], lg, ly, y);
+    }
   } else if (mode == 2) {
     const double b = sh[0] > 0.0 ? sqrt(sh[0]) : 0.0;
     beta[c] = b;
@@ -325,7 +344,7 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* 
   const T* dotsT = f32 ? (const T*)(s.idot + (size_t)(KIN_MAX + 2) * C) : (const T*)s.idot;
   const T* invT = f32 ? (const T*)(s.ibeta + 2 * C) : (const T*)(s.ibeta + C);
   const T* yT = f32 ? (const T*)(s.iy + (size_t)kin * C) : (const T*)s.iy;
-  count_launch(3 + 4 * kin + 1);
+  count_launch(3 + 4 * kin);
   // beta = ||r||, v_0 = r / beta
   col_dots<T>(nchunk, threads, shm, st, n2, C, 1, r, 0, r, rows_per_chunk, 0, s.ipart);
   k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, 1, kin, s.ipart, s.idot, 2, 0, s.ih, s.ibeta, s.ibeta + C,
@@ -340,7 +359,8 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* 
     col_dots<T>(nchunk, threads, shm, st, n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 1, s.ipart);
     k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, i + 1, kin, s.ipart, s.idot, 3, i, s.ih, s.ibeta,
                                       s.ibeta + C, s.iy);
-    k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, dotsT, w, w, invT);
+    // v_{i+1} is needed only by a further step: the final combination uses v_0..v_{kin-1}
+    if (i + 1 < kin) k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, dotsT, w, w, invT);
   }
   k_col_final<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, kin, Vb, vstride, yT, dinv, z);
 }

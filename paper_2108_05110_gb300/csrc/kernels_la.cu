@@ -1136,29 +1136,27 @@ __global__ void __launch_bounds__(COMB_T) k_block_combine(T* out, const T* in, T
   }
 }
 
-// Staged combination (FP32, W <= 24): a CTA owns CB_ROWS consecutive rows and
-// streams that row range of every basis block through a CB_NST-deep ring of
+// Staged combination (FP32, W <= 24): a CTA of CB_T threads owns CB_ROWS =
+// 2 CB_T consecutive rows and streams that row range of every basis block through a CB_NST-deep ring of
 // shared-memory stages, one TMA bulk copy per block (the rows of a block are
 // one contiguous span), completion on the stage's mbarrier with the same
 // bounded waits as the staged Gram.  A thread owns two rows; the coefficient
 // blocks sit in shared memory (zero-padded to W x W) and are read as
 // broadcasts.  out may alias a basis block or in: a CTA reads all of its
 // rows before writing them.
-constexpr int CB_T = 128;
-constexpr int CB_ROWS = 2 * CB_T;
-constexpr int CB_NST = 3;
 constexpr size_t CB_COEF_MAX = 96 * 1024;
 
-template <int W>
+template <int W, int CB_T, int CB_NST>
 __global__ void __launch_bounds__(CB_T) k_combine_staged(float* out, const float* in, float alpha, const float* V,
                                                        size_t vstride, int kblocks, int r_in,
                                                        const float* __restrict__ C, int r_out, int n_rows, int ldv,
                                                        int ldo) {
   extern __shared__ __align__(16) unsigned char cb_raw[];
-  if ((ldv & 3) || (ldo & 3)) {                        // 16-byte rows for the bulk copies
+  if ((ldv & 3) || (ldo & 3) || (vstride & 3) || (reinterpret_cast<uintptr_t>(V) & 15)) {   // 16-byte copies
     if (threadIdx.x == 0) atomicExch(&g_async_err, 1);
     return;
   }
+  constexpr int CB_ROWS = 2 * CB_T;
   const unsigned bar0 = smem_u32(cb_raw);
   float* stages = reinterpret_cast<float*>(cb_raw + GS_BAR_BYTES);
   const int stage_floats = CB_ROWS * ldv;
@@ -1271,37 +1269,75 @@ __global__ void __launch_bounds__(CB_T) k_combine_staged(float* out, const float
   }
 }
 
-static cudaError_t combine_staged_attr() {
+// CTA width x stage depth of the staged combination: 0 = 256 x 2 (default;
+// two CTAs of 8 warps per SM at J = 20, 54.7 us against 62.6 us for 128 x 3 on
+// the 128 x 128 cavity), 1 = 128 x 2, 2 = 128 x 3, 3 = 64 x 2 (MHDE_COMB to
+// experiment).  A variant whose stages do not fit falls back to 128 x 2.
+static int combine_variant() {
+  static const int v = [] {
+    const char* e = std::getenv("MHDE_COMB");
+    const int x = e ? std::atoi(e) : 0;
+    return (x >= 0 && x <= 3) ? x : 0;
+  }();
+  return v;
+}
+
+template <int W>
+static cudaError_t combine_staged_attr_w() {
   cudaError_t e = cudaSuccess;
   auto set = [&](const void* f) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM);
   };
-  set((const void*)k_combine_staged<4>);
-  set((const void*)k_combine_staged<8>);
-  set((const void*)k_combine_staged<12>);
-  set((const void*)k_combine_staged<16>);
-  set((const void*)k_combine_staged<20>);
-  set((const void*)k_combine_staged<24>);
+  set((const void*)k_combine_staged<W, 128, 3>);
+  set((const void*)k_combine_staged<W, 128, 2>);
+  set((const void*)k_combine_staged<W, 256, 2>);
+  set((const void*)k_combine_staged<W, 64, 2>);
   return e;
 }
 
-static size_t combine_staged_smem(int kblocks, int W, int ldv) {
-  return GS_BAR_BYTES + (size_t)CB_NST * CB_ROWS * ldv * sizeof(float) + (size_t)kblocks * W * W * sizeof(float);
+static cudaError_t combine_staged_attr() {
+  cudaError_t e = combine_staged_attr_w<4>();
+  if (e == cudaSuccess) e = combine_staged_attr_w<8>();
+  if (e == cudaSuccess) e = combine_staged_attr_w<12>();
+  if (e == cudaSuccess) e = combine_staged_attr_w<16>();
+  if (e == cudaSuccess) e = combine_staged_attr_w<20>();
+  if (e == cudaSuccess) e = combine_staged_attr_w<24>();
+  return e;
+}
+
+static size_t combine_staged_smem(int kblocks, int W, int ldv, int nt, int nst) {
+  return GS_BAR_BYTES + (size_t)nst * 2 * nt * ldv * sizeof(float) + (size_t)kblocks * W * W * sizeof(float);
+}
+
+template <int W, int NT, int NST>
+static bool combine_staged_try(float* out, const float* in, float alpha, const float* V, size_t vstride, int kblocks,
+                               int r_in, const float* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st) {
+  const size_t smem = combine_staged_smem(kblocks, W, ldv, NT, NST);
+  if ((size_t)kblocks * W * W * sizeof(float) > CB_COEF_MAX || smem > GS_SMEM || ldv % 4 != 0 || ldo % 4 != 0 ||
+      gram_setup().err != cudaSuccess)
+    return false;
+  k_combine_staged<W, NT, NST><<<nblk(n_rows, 2 * NT), NT, smem, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C,
+                                                                       r_out, n_rows, ldv, ldo);
+  return true;
 }
 
 template <typename T, int W>
 static void combine_w(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
                       const T* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st) {
   if constexpr (sizeof(T) == 4 && W <= 24) {
-    const size_t smem = combine_staged_smem(kblocks, W, ldv);
-    if ((size_t)kblocks * W * W * sizeof(float) <= CB_COEF_MAX && smem <= GS_SMEM && ldv % 4 == 0 && ldo % 4 == 0 &&
-        gram_setup().err == cudaSuccess) {
-      k_combine_staged<W><<<nblk(n_rows, CB_ROWS), CB_T, smem, st>>>(
-          reinterpret_cast<float*>(out), reinterpret_cast<const float*>(in), (float)alpha,
-          reinterpret_cast<const float*>(V), vstride, kblocks, r_in, reinterpret_cast<const float*>(C), r_out,
-          n_rows, ldv, ldo);
-      return;
+    float* o = reinterpret_cast<float*>(out);
+    const float* i = reinterpret_cast<const float*>(in);
+    const float* v = reinterpret_cast<const float*>(V);
+    const float* cc = reinterpret_cast<const float*>(C);
+    bool done = false;
+    switch (combine_variant()) {
+      case 1: break;
+      case 2: done = combine_staged_try<W, 128, 3>(o, i, (float)alpha, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st); break;
+      case 3: done = combine_staged_try<W, 64, 2>(o, i, (float)alpha, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st); break;
+      default: done = combine_staged_try<W, 256, 2>(o, i, (float)alpha, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
     }
+    if (!done) done = combine_staged_try<W, 128, 2>(o, i, (float)alpha, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+    if (done) return;
   }
   constexpr int RPT = (sizeof(T) == 4 && W <= 24) ? 2 : 1;
   const size_t per_block = (size_t)W * W * sizeof(T);
