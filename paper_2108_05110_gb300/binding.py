@@ -39,7 +39,7 @@ class Options(C.Structure):
                 ("jacobi_omega", C.c_double), ("amg_sweeps", C.c_int), ("amg_cycles", C.c_int),
                 ("poly_degree", C.c_int),
                 ("inner_iters", C.c_int),
-                ("schur", C.c_int), ("strict", C.c_int)]
+                ("schur", C.c_int), ("strict", C.c_int), ("inner_fp16", C.c_int)]
 
 
 class Sizes(C.Structure):

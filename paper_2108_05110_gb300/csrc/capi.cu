@@ -288,6 +288,7 @@ void mhde_default_options(mhde_options* o) {
   o->inner_iters = 6;
   o->schur = 1;
   o->strict = 0;
+  o->inner_fp16 = 0;
 }
 
 int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu_m, double s, double dt,
@@ -304,7 +305,8 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
       (c->opt.precision != MHDE_PREC_FP64 && c->opt.precision != MHDE_PREC_MIXED) ||
       (c->opt.conv_form != 0 && c->opt.conv_form != 1) || c->opt.inner_iters < 0 || c->opt.poly_degree < 0 ||
       c->opt.poly_degree > mhde::KIN_MAX || c->opt.poly_degree % 2 != 0 || c->opt.amg_cycles < 1 ||
-      c->opt.inner_iters > mhde::KIN_MAX || (c->opt.schur != 0 && c->opt.schur != 1)) {
+      c->opt.inner_iters > mhde::KIN_MAX || (c->opt.schur != 0 && c->opt.schur != 1) ||
+      (c->opt.inner_fp16 != 0 && c->opt.inner_fp16 != 1)) {
     delete c;
     return MHDE_EINVAL;
   }

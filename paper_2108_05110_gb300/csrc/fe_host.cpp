@@ -512,6 +512,50 @@ void eig_sym(int n, const double* A0, double* w, double* U) {
   std::copy(U2.begin(), U2.end(), U);
 }
 
+// Cholesky QR factors of a full-rank r-column Gram matrix G = R^T R:
+// T_ = R^{-1}, S_ = R (the same conventions as svqb: W T_ has orthonormal
+// columns, W = (W T_) S_).  Used only when full rank is certain: lambda_max
+// <= trace(G) and lambda_min >= 1 / ||R^{-1}||_F^2, so trace(G) ||R^{-1}||_F^2
+// < 1e-2 / thresh means every eigenvalue is above 100 thresh lambda_max and
+// svqb would keep all r directions.  About a hundred times cheaper than the
+// eigen-decomposition, which sits on the critical path of every block
+// iteration.  Returns false (and leaves T_, S_ unspecified) otherwise.
+bool cholqr_factors(int r, const std::vector<double>& G, double thresh, std::vector<double>& Tm,
+                           std::vector<double>& Sm) {
+  std::vector<double> R((size_t)r * r, 0.0);          // upper triangular, G = R^T R
+  double tr = 0.0;
+  for (int i = 0; i < r; ++i) tr += G[(size_t)i * r + i];
+  if (!(tr > 0.0)) return false;
+  for (int j = 0; j < r; ++j) {
+    double d = G[(size_t)j * r + j];
+    for (int k = 0; k < j; ++k) d -= R[(size_t)k * r + j] * R[(size_t)k * r + j];
+    if (!(d > 0.0)) return false;
+    const double rjj = std::sqrt(d);
+    R[(size_t)j * r + j] = rjj;
+    for (int i = j + 1; i < r; ++i) {
+      double v = G[(size_t)j * r + i];
+      for (int k = 0; k < j; ++k) v -= R[(size_t)k * r + j] * R[(size_t)k * r + i];
+      R[(size_t)j * r + i] = v / rjj;
+    }
+  }
+  // R^{-1} (upper triangular), column by column by back substitution
+  std::vector<double> Ri((size_t)r * r, 0.0);
+  double fro = 0.0;
+  for (int c = 0; c < r; ++c) {
+    for (int i = c; i >= 0; --i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= c; ++k) v -= R[(size_t)i * r + k] * Ri[(size_t)k * r + c];
+      v /= R[(size_t)i * r + i];
+      Ri[(size_t)i * r + c] = v;
+      fro += v * v;
+    }
+  }
+  if (!(tr * fro < 1e-2 / thresh)) return false;
+  Tm.swap(Ri);
+  Sm.swap(R);
+  return true;
+}
+
 void BlockLS::init(int r_, int J_, int m_, const double* S0) {
   r = r_;
   J = J_;

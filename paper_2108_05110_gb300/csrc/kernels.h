@@ -16,6 +16,34 @@ long long launch_count();
 void count_launch(long long n = 1);
 void set_capturing(bool on);   // launches issued while capturing a graph are not counted
 
+// Programmatic dependent launch.  The solver's kernels form long chains of
+// small dependent launches on one stream; a kernel launched through
+// launch_pdl may be scheduled while its predecessor drains, and overlaps its
+// launch and CTA start-up with that tail.  Every kernel launched this way
+// executes pdl_wait() before its first global memory access: it blocks until
+// the preceding grid has completed and its writes are visible (without the
+// launch attribute it returns at once), so results do not depend on the
+// overlap.  pdl_trigger() lets the next launch be scheduled once every CTA of
+// this grid has started.  MHDE_PDL=0 turns the attribute off.
+bool pdl_enabled();
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 struct QuadTables {             // degree-5 rule and P2 basis tables (host copy)
   double lam[NQ][3];
   double w[NQ];                 // reference weights, sum 1/2
@@ -113,10 +141,11 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st);
 // standard form (a . grad psi_k, psi_i), a = mean convecting field)
 void launch_Np(const mhde_ctx* c, const double* mean_conv, double* slots, double* Np, float* Npf,
                cudaStream_t st);
-// inner per-column GMRES(k) on F (velocity block), z ~ F^{-1} r
+// inner per-column GMRES(k) on F (velocity block), z ~ F^{-1} r; with
+// allow_half and options.inner_fp16 the FP32 path keeps its basis in FP16
 template <typename T>
 void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* dinv, const T* r, T* z, int ld,
-                        int kin, cudaStream_t st);
+                        int kin, cudaStream_t st, bool allow_half = true);
 // shared-memory limits of the inner and block kernels (set once, before any capture)
 cudaError_t init_inner_attributes();
 cudaError_t init_la_attributes();

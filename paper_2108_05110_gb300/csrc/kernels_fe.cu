@@ -11,6 +11,8 @@
 #include <atomic>
 #include <cmath>
 
+#include <cstdlib>
+
 #include "kernels.h"
 
 namespace mhde {
@@ -18,6 +20,13 @@ namespace mhde {
 static std::atomic<long long> g_launches{0};
 static thread_local bool g_capturing = false;
 long long launch_count() { return g_launches.load(); }
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("MHDE_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 void count_launch(long long n) {
   if (!g_capturing) g_launches += n;
 }

@@ -9,7 +9,15 @@
 // v_{i+1} = w / ||w||.  After k steps
 // the per-column least-squares problems min || beta e_1 - H y || are solved
 // by Givens rotations and z = D^{-1} sum_l v_l y_l.
+//
+// Storage: w (the operator output) is kept in the arithmetic type T; the basis
+// v_0..v_{k-1} is kept in a storage type S, either T or, on the FP32 path,
+// FP16 scaled by sqrt(n2) (a unit column then has entries of order one, well
+// inside FP16's normal range).  Arithmetic is always in T; the FP16 basis
+// halves the traffic of the dot, update and final passes and of the gathers.
 #include <cmath>
+
+#include <cuda_fp16.h>
 
 #include "kernels.h"
 
@@ -51,27 +59,69 @@ __device__ __forceinline__ void st4(double* p, const double v[4]) {
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
+// basis storage: four consecutive entries of S, returned (or given) in T; the
+// FP16 form carries the scale sc (stored = sc * value, isc = 1 / sc)
+__device__ __forceinline__ void lds4(const float* p, float, float v[4]) { ld4(p, v); }
+__device__ __forceinline__ void lds4(const double* p, double, double v[4]) { ld4(p, v); }
+__device__ __forceinline__ void lds4(const __half* p, float isc, float v[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  v[0] = a.x * isc; v[1] = a.y * isc; v[2] = b.x * isc; v[3] = b.y * isc;
+}
+__device__ __forceinline__ void sts4(float* p, float, const float v[4]) { st4(p, v); }
+__device__ __forceinline__ void sts4(double* p, double, const double v[4]) { st4(p, v); }
+__device__ __forceinline__ void sts4(__half* p, float sc, const float v[4]) {
+  const __half2 a = __floats2half2_rn(v[0] * sc, v[1] * sc), b = __floats2half2_rn(v[2] * sc, v[3] * sc);
+  uint2 u;
+  u.x = *reinterpret_cast<const unsigned*>(&a);
+  u.y = *reinterpret_cast<const unsigned*>(&b);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+
+// one IVec-wide chunk (index i in chunks) of a basis row, in T
+template <typename T, typename S> struct Gather;
+template <> struct Gather<float, float> {
+  static __device__ __forceinline__ float4 ld(const float* p, size_t i, float) {
+    return reinterpret_cast<const float4*>(p)[i];
+  }
+};
+template <> struct Gather<double, double> {
+  static __device__ __forceinline__ double2 ld(const double* p, size_t i, double) {
+    return reinterpret_cast<const double2*>(p)[i];
+  }
+};
+template <> struct Gather<float, __half> {
+  static __device__ __forceinline__ float4 ld(const __half* p, size_t i, float isc) {
+    float v[4];
+    lds4(p + 4 * i, isc, v);
+    return make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
 // w[a][:] = sum_k FD_ak v[col_k][:], FD = F D^{-1} (formed at assembly); two
 // nonzeros per iteration keep two gathers in flight
-template <typename T>
+template <typename T, typename S>
 __global__ void k_fd_spmm(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
-                          const T* __restrict__ FD, const T* __restrict__ v, T* __restrict__ w) {
+                          const T* __restrict__ FD, const S* __restrict__ v, T isc, T* __restrict__ w) {
+  pdl_wait();
+  pdl_trigger();
   using V = typename IVec<T>::type;
+  using G = Gather<T, S>;
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (tid >= (long long)n2 * nch) return;
   int a = (int)(tid / nch), ch = (int)(tid % nch);
-  const V* vv = reinterpret_cast<const V*>(v);
   V acc = izero(V());
   int k = rp[a];
   const int e = rp[a + 1];
   for (; k + 1 < e; k += 2) {
     const int c0 = col[k], c1 = col[k + 1];
     const T f0 = FD[k], f1 = FD[k + 1];
-    const V x0 = vv[(size_t)c0 * nch + ch], x1 = vv[(size_t)c1 * nch + ch];
+    const V x0 = G::ld(v, (size_t)c0 * nch + ch, isc), x1 = G::ld(v, (size_t)c1 * nch + ch, isc);
     ifma(acc, f0, x0);
     ifma(acc, f1, x1);
   }
-  if (k < e) ifma(acc, FD[k], vv[(size_t)col[k] * nch + ch]);
+  if (k < e) ifma(acc, FD[k], G::ld(v, (size_t)col[k] * nch + ch, isc));
   reinterpret_cast<V*>(w)[(size_t)a * nch + ch] = acc;
 }
 
@@ -79,10 +129,12 @@ __global__ void k_fd_spmm(int n2, int nch, const int* __restrict__ rp, const int
 // (l < nl), and part[nl][col][chunk] = sum_rows w^2 when with_norm.  A thread
 // owns 4 consecutive columns of a row (one 16-byte load per vector for FP32),
 // so many rows are in flight per CTA.
-template <typename T, int NLM>
-__global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, const T* V, size_t vstride,
+template <typename T, typename S, int NLM>
+__global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, const S* V, size_t vstride, T isc,
                                                   const T* w, int rows_per_chunk, int with_norm,
                                                   double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double red[];
   const int C4 = C / 4;
   const int G = blockDim.x / C4;
@@ -103,7 +155,7 @@ __global__ void __launch_bounds__(256) k_col_dots(int n_rows, int C, int nl, con
       for (int l = 0; l < NLM - 1; ++l)
         if (l < nl) {
           T vv[4];
-          ld4(V + (size_t)l * vstride + o, vv);
+          lds4(V + (size_t)l * vstride + o, isc, vv);
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[l][q] += vv[q] * wv[q];
         }
@@ -187,6 +239,8 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
                                                       int mode, int i, double* __restrict__ H,
                                                       double* __restrict__ beta, double* __restrict__ inv,
                                                       double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[KIN_MAX + 2];
   __shared__ double lh[KIN_MAX + 1][KIN_MAX];
   __shared__ double lg[KIN_MAX + 1];
@@ -245,10 +299,14 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
 }
 
 // out[row][col] = (in[row][col] - sum_l V_l[row][col] dots[l][col]) * scale[col]
-// (in and out may alias; nl may be 0); 4 consecutive entries per thread
-template <typename T>
-__global__ void k_col_update(int n_rows, int C, int nl, const T* V, size_t vstride, const T* __restrict__ dots,
-                             const T* in, T* out, const T* __restrict__ scale) {
+// (nl may be 0); in is in T, the basis V and out in the storage type S (out
+// stored with scale osc); 4 consecutive entries per thread
+template <typename T, typename S>
+__global__ void k_col_update(int n_rows, int C, int nl, const S* __restrict__ V, size_t vstride, T isc,
+                             const T* __restrict__ dots, const T* __restrict__ in, S* __restrict__ out, T osc,
+                             const T* __restrict__ scale) {
+  pdl_wait();
+  pdl_trigger();
   long long t4 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long n = (long long)n_rows * C;
   if (4 * t4 >= n) return;
@@ -258,20 +316,22 @@ __global__ void k_col_update(int n_rows, int C, int nl, const T* V, size_t vstri
   ld4(in + o, acc);
   for (int l = 0; l < nl; ++l) {
     T vv[4];
-    ld4(V + (size_t)l * vstride + o, vv);
+    lds4(V + (size_t)l * vstride + o, isc, vv);
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] -= vv[q] * dots[(size_t)l * C + c0 + q];
   }
   if (scale)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] *= scale[c0 + q];
-  st4(out + o, acc);
+  sts4(out + o, osc, acc);
 }
 
 // z[row][col] = dinv[row] * sum_l V_l[row][col] y[l][col]; 4 entries per thread
-template <typename T>
-__global__ void k_col_final(int n_rows, int C, int kin, const T* __restrict__ V, size_t vstride,
+template <typename T, typename S>
+__global__ void k_col_final(int n_rows, int C, int kin, const S* __restrict__ V, size_t vstride, T isc,
                             const T* __restrict__ y, const T* __restrict__ dinv, T* __restrict__ z) {
+  pdl_wait();
+  pdl_trigger();
   long long t4 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long n = (long long)n_rows * C;
   if (4 * t4 >= n) return;
@@ -281,7 +341,7 @@ __global__ void k_col_final(int n_rows, int C, int kin, const T* __restrict__ V,
   T acc[4] = {T(0), T(0), T(0), T(0)};
   for (int l = 0; l < kin; ++l) {
     T vv[4];
-    ld4(V + (size_t)l * vstride + o, vv);
+    lds4(V + (size_t)l * vstride + o, isc, vv);
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] += vv[q] * y[(size_t)l * C + c0 + q];
   }
@@ -291,44 +351,51 @@ __global__ void k_col_final(int n_rows, int C, int kin, const T* __restrict__ V,
   st4(z + o, acc);
 }
 
-template <typename T>
-static void col_dots(int nchunk, int threads, size_t shm, cudaStream_t st, int n_rows, int C, int nl, const T* V,
-                     size_t vstride, const T* w, int rows_per_chunk, int with_norm, double* part) {
+template <typename T, typename S>
+static void col_dots(int nchunk, int threads, size_t shm, cudaStream_t st, int n_rows, int C, int nl, const S* V,
+                     size_t vstride, T isc, const T* w, int rows_per_chunk, int with_norm, double* part) {
   if (nl + 1 <= 2)
-    k_col_dots<T, 2><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm, part);
+    launch_pdl(k_col_dots<T, S, 2>, dim3(nchunk), dim3(threads), shm, st, n_rows, C, nl, V, vstride, isc, w,
+               rows_per_chunk, with_norm, part);
   else if (nl + 1 <= 4)
-    k_col_dots<T, 4><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm, part);
+    launch_pdl(k_col_dots<T, S, 4>, dim3(nchunk), dim3(threads), shm, st, n_rows, C, nl, V, vstride, isc, w,
+               rows_per_chunk, with_norm, part);
   else if (nl + 1 <= 8)
-    k_col_dots<T, 8><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm, part);
+    launch_pdl(k_col_dots<T, S, 8>, dim3(nchunk), dim3(threads), shm, st, n_rows, C, nl, V, vstride, isc, w,
+               rows_per_chunk, with_norm, part);
   else if (nl + 1 <= 12)
-    k_col_dots<T, 12><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm, part);
+    launch_pdl(k_col_dots<T, S, 12>, dim3(nchunk), dim3(threads), shm, st, n_rows, C, nl, V, vstride, isc, w,
+               rows_per_chunk, with_norm, part);
   else
-    k_col_dots<T, KIN_MAX + 2><<<nchunk, threads, shm, st>>>(n_rows, C, nl, V, vstride, w, rows_per_chunk, with_norm,
-                                                               part);
+    launch_pdl(k_col_dots<T, S, KIN_MAX + 2>, dim3(nchunk), dim3(threads), shm, st, n_rows, C, nl, V, vstride, isc, w,
+               rows_per_chunk, with_norm, part);
 }
 
-template <typename T>
+template <typename T, typename S>
 static cudaError_t dots_attr() {
   cudaError_t e = cudaSuccess;
   auto set = [&](const void* f) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   };
-  set((const void*)k_col_dots<T, 2>);
-  set((const void*)k_col_dots<T, 4>);
-  set((const void*)k_col_dots<T, 8>);
-  set((const void*)k_col_dots<T, 12>);
-  set((const void*)k_col_dots<T, KIN_MAX + 2>);
+  set((const void*)k_col_dots<T, S, 2>);
+  set((const void*)k_col_dots<T, S, 4>);
+  set((const void*)k_col_dots<T, S, 8>);
+  set((const void*)k_col_dots<T, S, 12>);
+  set((const void*)k_col_dots<T, S, KIN_MAX + 2>);
   return e;
 }
 
 cudaError_t init_inner_attributes() {
-  cudaError_t e = dots_attr<float>();
-  if (e != cudaSuccess) return e;
-  return dots_attr<double>();
+  cudaError_t e = dots_attr<float, float>();
+  if (e == cudaSuccess) e = dots_attr<float, __half>();
+  if (e == cudaSuccess) e = dots_attr<double, double>();
+  return e;
 }
 
-template <typename T>
-void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* dinv, const T* r, T* z, int ld,
+// Workspace s.ibasis: w ([n2][C] in T) first, then the basis v_0..v_{kin-1}
+// ([n2][C] each in S); both fit the (kin + 1) T-vectors the workspace holds.
+template <typename T, typename S>
+static void inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* dinv, const T* r, T* z, int ld,
                         int kin, cudaStream_t st) {
   const int n2 = c->fe.n2, C = 2 * ld;
   const int nch = C / IVec<T>::W;
@@ -337,8 +404,12 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* 
   const int rows_per_chunk = (n2 + nchunk - 1) / nchunk;
   const int threads = (256 / (C / 4)) * (C / 4);          // whole row groups of C/4 threads
   const size_t shm = (size_t)(kin + 2) * (threads / (C / 4)) * C * sizeof(float);
+  // FP16 basis: stored = sqrt(n2) * value, so unit columns have entries of order one
+  const bool half = sizeof(S) < sizeof(T);
+  const T sc = half ? (T)std::sqrt((double)n2) : T(1), isc = half ? T(1) / sc : T(1);
 
-  T* Vb = (T*)s.ibasis;
+  T* w = (T*)s.ibasis;
+  S* Vb = reinterpret_cast<S*>((char*)s.ibasis + vstride * sizeof(T));
   const long long nel = (long long)n2 * C;
   const bool f32 = sizeof(T) == 4;
   const T* dotsT = f32 ? (const T*)(s.idot + (size_t)(KIN_MAX + 2) * C) : (const T*)s.idot;
@@ -346,29 +417,44 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* 
   const T* yT = f32 ? (const T*)(s.iy + (size_t)kin * C) : (const T*)s.iy;
   count_launch(3 + 4 * kin);
   // beta = ||r||, v_0 = r / beta
-  col_dots<T>(nchunk, threads, shm, st, n2, C, 1, r, 0, r, rows_per_chunk, 0, s.ipart);
-  k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, 1, kin, s.ipart, s.idot, 2, 0, s.ih, s.ibeta, s.ibeta + C,
-                                    nullptr);
-  k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, 0, Vb, vstride, dotsT, r, Vb, invT);
+  col_dots<T, T>(nchunk, threads, shm, st, n2, C, 1, r, 0, T(1), r, rows_per_chunk, 0, s.ipart);
+  launch_pdl(k_col_reduce, dim3(C), dim3(RED_T), 0, st, nchunk, C, 1, kin, s.ipart, s.idot, 2, 0, s.ih, s.ibeta,
+             s.ibeta + C, nullptr);
+  launch_pdl(k_col_update<T, S>, dim3(nb(nel / 4, 256)), dim3(256), 0, st, n2, C, 0, Vb, vstride, isc, dotsT, r, Vb,
+             sc, invT);
   for (int i = 0; i < kin; ++i) {
-    T* vi = Vb + (size_t)i * vstride;
-    T* w = Vb + (size_t)(i + 1) * vstride;
-    k_fd_spmm<T><<<nb((long long)n2 * nch, 256), 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, FDv, vi, w);
+    const S* vi = Vb + (size_t)i * vstride;
+    launch_pdl(k_fd_spmm<T, S>, dim3(nb((long long)n2 * nch, 256)), dim3(256), 0, st, n2, nch,
+               c->F.rowptr, c->F.col, FDv, vi, isc, w);
     // one classical Gram-Schmidt pass: dots against v_0..v_i and ||w||^2 in a
     // single sweep; the projected norm follows from the Pythagorean identity
-    col_dots<T>(nchunk, threads, shm, st, n2, C, i + 1, Vb, vstride, w, rows_per_chunk, 1, s.ipart);
-    k_col_reduce<<<C, RED_T, 0, st>>>(nchunk, C, i + 1, kin, s.ipart, s.idot, 3, i, s.ih, s.ibeta,
+    col_dots<T, S>(nchunk, threads, shm, st, n2, C, i + 1, Vb, vstride, isc, w, rows_per_chunk, 1, s.ipart);
+    launch_pdl(k_col_reduce, dim3(C), dim3(RED_T), 0, st, nchunk, C, i + 1, kin, s.ipart, s.idot, 3, i, s.ih, s.ibeta,
                                       s.ibeta + C, s.iy);
     // v_{i+1} is needed only by a further step: the final combination uses v_0..v_{kin-1}
-    if (i + 1 < kin) k_col_update<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, i + 1, Vb, vstride, dotsT, w, w, invT);
+    if (i + 1 < kin)
+      launch_pdl(k_col_update<T, S>, dim3(nb(nel / 4, 256)), dim3(256), 0, st, n2, C, i + 1, Vb, vstride, isc, dotsT,
+                 w, Vb + (size_t)(i + 1) * vstride, sc, invT);
   }
-  k_col_final<T><<<nb(nel / 4, 256), 256, 0, st>>>(n2, C, kin, Vb, vstride, yT, dinv, z);
+  launch_pdl(k_col_final<T, S>, dim3(nb(nel / 4, 256)), dim3(256), 0, st, n2, C, kin, Vb, vstride, isc, yT, dinv, z);
+}
+
+template <typename T>
+void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* dinv, const T* r, T* z, int ld,
+                        int kin, cudaStream_t st, bool allow_half) {
+  if constexpr (sizeof(T) == 4) {
+    if (allow_half && c->opt.inner_fp16) {
+      inner_gmres<float, __half>(c, s, FDv, dinv, r, z, ld, kin, st);
+      return;
+    }
+  }
+  inner_gmres<T, T>(c, s, FDv, dinv, r, z, ld, kin, st);
 }
 
 template void launch_inner_gmres<double>(const mhde_ctx*, const Sub&, const double*, const double*,
-                                         const double*, double*, int, int, cudaStream_t);
+                                         const double*, double*, int, int, cudaStream_t, bool);
 template void launch_inner_gmres<float>(const mhde_ctx*, const Sub&, const float*, const float*, const float*,
-                                        float*, int, int, cudaStream_t);
+                                        float*, int, int, cudaStream_t, bool);
 
 // ------------------------------------------------------------ GMRES polynomial
 // z ~ F^{-1} r as q(A) D^{-1} r with A = D^{-1} F and q(z) = (1 - pi(z)) / z,

@@ -72,6 +72,8 @@ __global__ void __launch_bounds__(512) k_saddle(int n2, int np, int nch, const i
                                                 const int* __restrict__ bcol, const T* __restrict__ Bval,
                                                 const unsigned char* __restrict__ isbnd, const T* __restrict__ X,
                                                 const double* __restrict__ Bvec, T* __restrict__ Y) {
+  pdl_wait();
+  pdl_trigger();
   using V = typename Vec<T>::type;
   const V* Xv = reinterpret_cast<const V*>(X);
   V* Yv = reinterpret_cast<V*>(Y);
@@ -278,13 +280,11 @@ void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T
   long long n = ((long long)c->fe.n2 + c->fe.np) * nch;
   const int bs = c->spmm_block;
   if (mode == 0)
-    k_saddle<T, 0><<<nblk(n, bs), bs, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
-                                              c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
-                                              Bval, c->d_isbnd, X, Bvec, Y);
+    launch_pdl(k_saddle<T, 0>, dim3(nblk(n, bs)), dim3(bs), 0, st, c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col,
+               Fval, c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col, Bval, c->d_isbnd, X, Bvec, Y);
   else
-    k_saddle<T, 1><<<nblk(n, bs), bs, 0, st>>>(c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col, Fval,
-                                              c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col,
-                                              Bval, c->d_isbnd, X, Bvec, Y);
+    launch_pdl(k_saddle<T, 1>, dim3(nblk(n, bs)), dim3(bs), 0, st, c->fe.n2, c->fe.np, nch, c->F.rowptr, c->F.col,
+               Fval, c->BT.rowptr, c->BT.col, BTval, c->B.rowptr, c->B.col, Bval, c->d_isbnd, X, Bvec, Y);
 }
 
 // ------------------------------------------------------------ generic CSR
@@ -292,6 +292,8 @@ template <typename T>
 __global__ void k_csr(int nrows, int nch, const int* __restrict__ rp, const int* __restrict__ col,
                       const T* __restrict__ val, const T* __restrict__ dinv, T omega,
                       const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, int mode) {
+  pdl_wait();
+  pdl_trigger();
   using V = typename Vec<T>::type;
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (tid >= (long long)nrows * nch) return;
@@ -324,7 +326,7 @@ void launch_csr(int nrows, const int* rowptr, const int* col, const T* val, cons
   count_launch();
   int nch = Jp / Vec<T>::W;
   long long n = (long long)nrows * nch;
-  k_csr<T><<<nblk(n, 256), 256, 0, st>>>(nrows, nch, rowptr, col, val, dinv, omega, x, b, y, mode);
+  launch_pdl(k_csr<T>, dim3(nblk(n, 256)), dim3(256), 0, st, nrows, nch, rowptr, col, val, dinv, omega, x, b, y, mode);
 }
 
 __device__ __forceinline__ void warp_sum(double2& a) {
@@ -350,6 +352,8 @@ __device__ __forceinline__ void warp_sum(float4& a) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_apply(int n, int nch, const T* __restrict__ A,
                                                      const T* __restrict__ x, T* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   using V = typename Vec<T>::type;
   const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -369,7 +373,7 @@ void launch_dense_apply(int n, const T* Ainv, const T* x, T* y, int Jp, cudaStre
   count_launch();
   int nch = Jp / Vec<T>::W;
   long long threads = (long long)n * nch * 32;
-  k_dense_apply<T><<<nblk(threads, 256), 256, 0, st>>>(n, nch, Ainv, x, y);
+  launch_pdl(k_dense_apply<T>, dim3(nblk(threads, 256)), dim3(256), 0, st, n, nch, Ainv, x, y);
 }
 
 // ------------------------------------------------------------ preconditioner pieces
@@ -416,6 +420,8 @@ template <typename T>
 __global__ void k_precond_p(int np, int nch, const T* __restrict__ x, const T* __restrict__ rp,
                             const T* __restrict__ mp, T inv_dt, T nu_hat, const int* __restrict__ nrp,
                             const int* __restrict__ ncol, const T* __restrict__ Np, T* __restrict__ zp) {
+  pdl_wait();
+  pdl_trigger();
   using V = typename Vec<T>::type;
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (tid >= (long long)np * nch) return;
@@ -442,13 +448,16 @@ void launch_precond_p(int np, int Jp, const T* x, const T* rp, const T* mp, T in
   count_launch();
   int nch = Jp / Vec<T>::W;
   long long n = (long long)np * nch;
-  k_precond_p<T><<<nblk(n, 256), 256, 0, st>>>(np, nch, x, rp, mp, inv_dt, nu_hat, nrp, ncol, Np, zp);
+  launch_pdl(k_precond_p<T>, dim3(nblk(n, 256)), dim3(256), 0, st, np, nch, x, rp, mp, inv_dt, nu_hat, nrp, ncol, Np,
+             zp);
 }
 
 template <typename T>
 __global__ void k_bt_apply(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
                            const T* __restrict__ BT, const unsigned char* __restrict__ isbnd,
                            const T* __restrict__ ru, const T* __restrict__ zp, T* __restrict__ tu) {
+  pdl_wait();
+  pdl_trigger();
   using V = typename Vec<T>::type;
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (tid >= (long long)n2 * 2 * nch) return;
@@ -474,8 +483,8 @@ void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp
   count_launch();
   int nch = ld / Vec<T>::W;
   long long n = (long long)c->fe.n2 * 2 * nch;
-  k_bt_apply<T><<<nblk(n, 256), 256, 0, st>>>(c->fe.n2, nch, c->BT.rowptr, c->BT.col, BTval, c->d_isbnd,
-                                             ru, zp, tu);
+  launch_pdl(k_bt_apply<T>, dim3(nblk(n, 256)), dim3(256), 0, st,
+             c->fe.n2, nch, c->BT.rowptr, c->BT.col, BTval, c->d_isbnd, ru, zp, tu);
 }
 
 // ------------------------------------------------------------ block Gram
@@ -618,6 +627,8 @@ __global__ void __launch_bounds__(256) k_gram_pairs(const T* __restrict__ V, siz
 // the 8 partial sums are added in a fixed order (deterministic).
 __global__ void __launch_bounds__(256) k_gram_reduce(int nparts, int total, const double* __restrict__ part,
                                                      double* __restrict__ gram) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[8][33];
   const int lo = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int o = blockIdx.x * 32 + lo;
@@ -693,6 +704,8 @@ __global__ void __launch_bounds__(NTH, 1) k_gram_staged(const float* __restrict_
                                                       const float* __restrict__ Wm, int n_rows, int ld, int r,
                                                       int rows_per_chunk, int S, int TR, int tstride,
                                                       double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char gsm_raw[];
   // every bulk copy needs 16-byte aligned tiles and rows; the host plan
   // guarantees it, and a launch that breaks it copies nothing
@@ -839,8 +852,8 @@ static void gram_staged(const float* V, size_t vstride, int kblocks, const float
   const int nctas = std::max(1, std::min(nchunk / S, nsm));
   const int rows_per_chunk = (n_rows + nctas - 1) / nctas;
   nparts = nctas * S;
-  k_gram_staged<W, PC, NTH><<<nctas, NTH, smem, st>>>(V, vstride, kblocks, Wm, n_rows, ld, r, rows_per_chunk, S,
-                                                      TR, tstride, part);
+  launch_pdl(k_gram_staged<W, PC, NTH>, dim3(nctas), dim3(NTH), smem, st, V, vstride, kblocks, Wm, n_rows, ld, r,
+             rows_per_chunk, S, TR, tstride, part);
 }
 
 static cudaError_t combine_staged_attr();
@@ -976,7 +989,7 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
   }
   if (!reduce) return;                               // partial sums only (kernel timing)
   const int total = kblocks * r * r;
-  k_gram_reduce<<<(total + 31) / 32, 256, 0, st>>>(nparts, total, part, gram);
+  launch_pdl(k_gram_reduce, dim3((total + 31) / 32), dim3(256), 0, st, nparts, total, part, gram);
 }
 
 // ------------------------------------------------------------ one-reduce Gram-Schmidt helpers
@@ -985,6 +998,8 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
 // lanes striding over the (i, t) terms, then a fixed butterfly of shuffles
 // (deterministic).
 __global__ void __launch_bounds__(256) k_proj_gram(double* G, int k, int r) {
+  pdl_wait();
+  pdl_trigger();
   const int rr = r * r;
   const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -1005,7 +1020,7 @@ __global__ void __launch_bounds__(256) k_proj_gram(double* G, int k, int r) {
 void launch_proj_gram(double* G, int k, int r, cudaStream_t st) {
   count_launch();
   const long long threads = (long long)r * r * 32;
-  k_proj_gram<<<nblk(threads, 256), 256, 0, st>>>(G, k, r);
+  launch_pdl(k_proj_gram, dim3(nblk(threads, 256)), dim3(256), 0, st, G, k, r);
 }
 
 // Coefficients of V_{k+1} = (W - sum_i V_i H_i) T for the block combination:
@@ -1013,6 +1028,8 @@ void launch_proj_gram(double* G, int k, int r, cudaStream_t st) {
 template <typename T>
 __global__ void k_make_coef(const double* __restrict__ G, const double* __restrict__ Tm, int k, int r,
                             T* __restrict__ C) {
+  pdl_wait();
+  pdl_trigger();
   const int rr = r * r;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= (k + 2) * rr) return;
@@ -1033,7 +1050,7 @@ template <typename T>
 void launch_make_coef(const double* G, const double* Tm, int k, int r, T* C, cudaStream_t st) {
   count_launch();
   const int n = (k + 2) * r * r;
-  k_make_coef<T><<<nblk(n, 256), 256, 0, st>>>(G, Tm, k, r, C);
+  launch_pdl(k_make_coef<T>, dim3(nblk(n, 256)), dim3(256), 0, st, G, Tm, k, r, C);
 }
 
 // ------------------------------------------------------------ block combine
@@ -1151,6 +1168,8 @@ __global__ void __launch_bounds__(CB_T) k_combine_staged(float* out, const float
                                                        size_t vstride, int kblocks, int r_in,
                                                        const float* __restrict__ C, int r_out, int n_rows, int ldv,
                                                        int ldo) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char cb_raw[];
   if ((ldv & 3) || (ldo & 3) || (vstride & 3) || (reinterpret_cast<uintptr_t>(V) & 15)) {   // 16-byte copies
     if (threadIdx.x == 0) atomicExch(&g_async_err, 1);
@@ -1316,8 +1335,8 @@ static bool combine_staged_try(float* out, const float* in, float alpha, const f
   if ((size_t)kblocks * W * W * sizeof(float) > CB_COEF_MAX || smem > GS_SMEM || ldv % 4 != 0 || ldo % 4 != 0 ||
       gram_setup().err != cudaSuccess)
     return false;
-  k_combine_staged<W, NT, NST><<<nblk(n_rows, 2 * NT), NT, smem, st>>>(out, in, alpha, V, vstride, kblocks, r_in, C,
-                                                                       r_out, n_rows, ldv, ldo);
+  launch_pdl(k_combine_staged<W, NT, NST>, dim3(nblk(n_rows, 2 * NT)), dim3(NT), smem, st, out, in, alpha, V, vstride,
+             kblocks, r_in, C, r_out, n_rows, ldv, ldo);
   return true;
 }
 
@@ -1330,13 +1349,16 @@ static void combine_w(T* out, const T* in, T alpha, const T* V, size_t vstride, 
     const float* v = reinterpret_cast<const float*>(V);
     const float* cc = reinterpret_cast<const float*>(C);
     bool done = false;
+    const float a = (float)alpha;
     switch (combine_variant()) {
       case 1: break;
-      case 2: done = combine_staged_try<W, 128, 3>(o, i, (float)alpha, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st); break;
-      case 3: done = combine_staged_try<W, 64, 2>(o, i, (float)alpha, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st); break;
-      default: done = combine_staged_try<W, 256, 2>(o, i, (float)alpha, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+      case 2: done = combine_staged_try<W, 128, 3>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+              break;
+      case 3: done = combine_staged_try<W, 64, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+              break;
+      default: done = combine_staged_try<W, 256, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
     }
-    if (!done) done = combine_staged_try<W, 128, 2>(o, i, (float)alpha, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+    if (!done) done = combine_staged_try<W, 128, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
     if (done) return;
   }
   constexpr int RPT = (sizeof(T) == 4 && W <= 24) ? 2 : 1;

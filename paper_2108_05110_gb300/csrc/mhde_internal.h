@@ -95,6 +95,11 @@ bool eig_hessenberg(int n, double* a, double* wr, double* wi);
 // Quadratic factors pi(z) = prod (1 - c1 z + c2 z^2) of the GMRES residual
 // polynomial of degree d (even) from a (d+1) x d Arnoldi Hessenberg matrix.
 bool gmres_poly_factors(int d, const double* H, std::vector<double>& c1, std::vector<double>& c2);
+// Cholesky QR factors T = R^{-1}, S = R of a Gram matrix G = R^T R (r x r,
+// row-major), only when full rank is certain (every eigenvalue above
+// 100 thresh lambda_max); false otherwise (callers then use the eigen form).
+bool cholqr_factors(int r, const std::vector<double>& G, double thresh, std::vector<double>& Tm,
+                    std::vector<double>& Sm);
 
 // Incremental least squares for block GMRES: block upper Hessenberg H with
 // block width r and the right-hand side E1 S0 (S0 is r x J).

@@ -355,7 +355,7 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
     std::vector<double> Tn, Sn;
     int rk;
     if (trP > 1e-3 * trW) {
-      rk = svqb(r, Gp, thresh, Tn, Sn);
+      rk = cholqr_factors(r, Gp, thresh, Tn, Sn) ? r : svqb(r, Gp, thresh, Tn, Sn);
       if (rk == r) {
         // V_{k+1} = (W - sum_i V_i H_i) T  in one pass, in place; the
         // coefficients -H_i T and T are formed on the device
@@ -428,7 +428,7 @@ static int poly_setup(mhde_ctx* c, Sub& s) {
   const int d = c->opt.poly_degree, C = 4;
   cudaStream_t st = s.stream;
   T* zscratch = (T*)s.Pk;                    // output of the setup solve is not used
-  launch_inner_gmres<T>(c, s, Prec<T>::FD(s), Prec<T>::Fd(s), (const T*)c->d_prand, zscratch, 2, d, st);
+  launch_inner_gmres<T>(c, s, Prec<T>::FD(s), Prec<T>::Fd(s), (const T*)c->d_prand, zscratch, 2, d, st, false);
   std::vector<double> Hall((size_t)(d + 1) * d * C), H((size_t)(d + 1) * d);
   SCU(cudaMemcpyAsync(Hall.data(), s.ih, Hall.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   SCU(cudaStreamSynchronize(st));

@@ -5,6 +5,8 @@
 //   "L r J m S0 h_0 ... h_{m-1}"  -> block least squares (BlockLS): after each
 //                                    block column its ok flag and the J residual
 //                                    norms, then the solution (m r x J)
+//   "Q r thresh g_00 ... g_rr"    -> Cholesky QR factors of a Gram matrix: the
+//                                    accepted flag, then T (r x r) and S (r x r)
 #include <cstdio>
 #include <vector>
 
@@ -33,6 +35,18 @@ int main() {
       std::vector<double> Y;
       ls.solve(Y);
       for (double v : Y) std::printf("%.17g\n", v);
+    } else if (mode[0] == 'Q') {
+      const int r = n;
+      double thresh = 0.0;
+      if (std::scanf("%lf", &thresh) != 1) return 1;
+      std::vector<double> G((size_t)r * r), T, S;
+      for (auto& v : G) std::scanf("%lf", &v);
+      const bool ok = mhde::cholqr_factors(r, G, thresh, T, S);
+      std::printf("%d\n", ok ? 1 : 0);
+      if (ok) {
+        for (double v : T) std::printf("%.17g\n", v);
+        for (double v : S) std::printf("%.17g\n", v);
+      }
     } else if (mode[0] == 'E') {
       std::vector<double> a((size_t)n * n), wr(n), wi(n);
       for (auto& v : a) std::scanf("%lf", &v);

@@ -149,6 +149,20 @@ def test_channel_small_mixed():
     sol.close()
 
 
+@pytest.mark.parametrize("inner_fp16", [0, 1])
+def test_inner_basis_storage(inner_fp16):
+    """The mixed path with the inner GMRES basis in FP32 and in FP16: the
+    basis only shapes the preconditioner, so both reach the oracle's fields to
+    the mixed tolerance (the FP64 refinement sets the accuracy)."""
+    ens = lid_cavity(N=16, J=5, s=1.0, nsteps=4, Re=2000.0)
+    ref = oracle_run(ens, 4)
+    sol = gpu_run(ens, 4, precision=PREC_MIXED, inner_fp16=inner_fp16)
+    v, w, _, _ = sol.read_state()
+    assert rel_l2(v, ref.V) <= MIXED_TOL and rel_l2(w, ref.W) <= MIXED_TOL
+    assert max(sol.stats().last_relres) <= 1e-12
+    sol.close()
+
+
 def test_single_member_and_standard_form():
     ens = lid_cavity(N=8, J=1, s=0.3, nsteps=3, Re=500.0)
     ref = oracle_run(ens, 3, form="standard")

@@ -1,6 +1,7 @@
 """CPU checks of the library's host-side small dense routines against numpy:
-the Hessenberg eigensolver (GMRES-polynomial roots) and the block least-squares
-update of the block GMRES iteration."""
+the Hessenberg eigensolver (GMRES-polynomial roots), the block least-squares
+update of the block GMRES iteration and the Cholesky QR factors of a new
+Krylov block."""
 import os
 import shutil
 import subprocess
@@ -123,3 +124,45 @@ def test_block_least_squares_matches_numpy_lstsq(checker, r, J, m):
     Y = np.array([float(v) for v in out[pos:pos + m * r * J]]).reshape(m * r, J)
     Yref = np.linalg.lstsq(Hbar, B, rcond=None)[0]
     assert np.allclose(Y, Yref, rtol=1e-8, atol=1e-10 * np.abs(Yref).max())
+
+
+def _cholqr(exe, G, thresh):
+    r = G.shape[0]
+    text = f"Q {r} {thresh!r}\n" + " ".join(repr(float(v)) for v in G.ravel()) + "\n"
+    out = subprocess.run([exe], input=text, capture_output=True, text=True, check=True).stdout.split()
+    if int(out[0]) == 0:
+        return None
+    vals = np.array([float(v) for v in out[1:1 + 2 * r * r]])
+    return vals[:r * r].reshape(r, r), vals[r * r:].reshape(r, r)
+
+
+@pytest.mark.parametrize("r", [1, 4, 20])
+def test_cholesky_qr_factors_orthonormalise_the_block(checker, r):
+    """A full-rank block W (n x r): with G = W^T W, W T has orthonormal columns,
+    (W T) S = W, S is numpy's upper-triangular Cholesky factor (unique with a
+    positive diagonal) and T = S^{-1}."""
+    rng = np.random.default_rng(5 + r)
+    W = rng.standard_normal((400, r)) @ (np.eye(r) + 0.5 * np.triu(rng.standard_normal((r, r)), 1))
+    G = W.T @ W
+    res = _cholqr(checker, G, 1e-9)
+    assert res is not None
+    T, S = res
+    Q = W @ T
+    assert np.allclose(Q.T @ Q, np.eye(r), atol=1e-10)
+    assert np.allclose(Q @ S, W, atol=1e-10 * np.abs(W).max())
+    assert np.allclose(S, np.linalg.cholesky(G).T, rtol=1e-12, atol=1e-12 * np.abs(S).max())
+    assert np.allclose(T @ S, np.eye(r), atol=1e-11)
+    assert np.allclose(np.tril(S, -1), 0.0) and np.allclose(np.tril(T, -1), 0.0)
+
+
+def test_cholesky_qr_declines_a_nearly_rank_deficient_block(checker):
+    """Eigenvalues spread over 1e-8 of the largest: with thresh = 1e-9 full
+    rank cannot be certified (the eigen form must decide what to drop), and an
+    indefinite or zero matrix is refused outright."""
+    rng = np.random.default_rng(3)
+    U = np.linalg.qr(rng.standard_normal((6, 6)))[0]
+    G = U @ np.diag([1.0, 0.5, 0.1, 1e-3, 1e-6, 1e-8]) @ U.T
+    assert _cholqr(checker, G, 1e-9) is None
+    assert _cholqr(checker, G, 1e-14) is not None          # a looser threshold accepts it
+    assert _cholqr(checker, np.zeros((3, 3)), 1e-9) is None
+    assert _cholqr(checker, np.diag([1.0, -1.0, 1.0]), 1e-9) is None
