@@ -256,15 +256,27 @@ __global__ void __launch_bounds__(RED_T) k_col_reduce(int nchunk, int C, int nl,
       lh[l][j] = (l <= j + 1 && j <= i) ? H[((size_t)l * kin + j) * C + c] : 0.0;
     }
   }
+  // every warp takes a share of one output's chunks: warp l sums output
+  // l % nout over the chunk slices l / nout, l / nout + wpo, ...; the slices
+  // are then added in slice order (a fixed order for given nout)
+  __shared__ double shw[RED_T / 32];
   const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
-  if (l < nout) {
+  const int wpo = nout > 0 ? (RED_T / 32) / nout : 1;
+  if (l < nout * wpo) {
+    const int ot = l % nout, sl = l / nout;
     double s = 0.0;
-    const double* pl = part + ((size_t)l * C + c) * nchunk;
-#pragma unroll 4
-    for (int ch = lane; ch < nchunk; ch += 32) s += pl[ch];
+    const double* pl = part + ((size_t)ot * C + c) * nchunk;
+#pragma unroll 8
+    for (int ch = lane + 32 * sl; ch < nchunk; ch += 32 * wpo) s += pl[ch];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) sh[l] = s;
+    if (lane == 0) shw[l] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < nout) {
+    double s = 0.0;
+    for (int sl = 0; sl < wpo; ++sl) s += shw[sl * nout + threadIdx.x];
+    sh[threadIdx.x] = s;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;

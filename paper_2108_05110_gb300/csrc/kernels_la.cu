@@ -625,24 +625,26 @@ __global__ void __launch_bounds__(256) k_gram_pairs(const T* __restrict__ V, siz
 // Sum of the per-chunk partials: a CTA owns 32 consecutive outputs; each of
 // its 8 warps sums every 8th chunk for them (coalesced 256-byte reads), then
 // the 8 partial sums are added in a fixed order (deterministic).
-__global__ void __launch_bounds__(256) k_gram_reduce(int nparts, int total, const double* __restrict__ part,
-                                                     double* __restrict__ gram) {
+constexpr int GR_WARPS = 16;
+
+__global__ void __launch_bounds__(32 * GR_WARPS) k_gram_reduce(int nparts, int total, const double* __restrict__ part,
+                                                              double* __restrict__ gram) {
   pdl_wait();
   pdl_trigger();
-  __shared__ double sh[8][33];
+  __shared__ double sh[GR_WARPS][33];
   const int lo = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int o = blockIdx.x * 32 + lo;
   double s = 0.0;
   if (o < total) {
-#pragma unroll 4
-    for (int c = g; c < nparts; c += 8) s += part[(size_t)c * total + o];
+#pragma unroll 8
+    for (int c = g; c < nparts; c += GR_WARPS) s += part[(size_t)c * total + o];
   }
   sh[g][lo] = s;
   __syncthreads();
   if (g == 0 && o < total) {
     double v = 0.0;
 #pragma unroll
-    for (int h = 0; h < 8; ++h) v += sh[h][lo];
+    for (int h = 0; h < GR_WARPS; ++h) v += sh[h][lo];
     gram[o] = v;
   }
 }
@@ -989,7 +991,7 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
   }
   if (!reduce) return;                               // partial sums only (kernel timing)
   const int total = kblocks * r * r;
-  launch_pdl(k_gram_reduce, dim3((total + 31) / 32), dim3(256), 0, st, nparts, total, part, gram);
+  launch_pdl(k_gram_reduce, dim3((total + 31) / 32), dim3(32 * GR_WARPS), 0, st, nparts, total, part, gram);
 }
 
 // ------------------------------------------------------------ one-reduce Gram-Schmidt helpers
