@@ -81,7 +81,7 @@ template <typename T>
 void launch_saddle_spmm(const mhde_ctx* c, const T* Fval, const T* Bval, const T* BTval, const T* X,
                         const double* Bvec, T* Y, int mode, int ld, cudaStream_t st);
 // generic CSR: mode 0 y = A x; 1 y = b - A x; 2 y = x + omega dinv (b - A x);
-// 3 y = omega dinv b; 4 y += A x
+// 3 y = omega dinv b; 4 y += A x; 5 y = b + A x
 template <typename T>
 void launch_csr(int nrows, const int* rowptr, const int* col, const T* val, const T* dinv, T omega,
                 const T* x, const T* b, T* y, int mode, int Jp, cudaStream_t st);

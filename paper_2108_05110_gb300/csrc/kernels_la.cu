@@ -315,8 +315,10 @@ __global__ void k_csr(int nrows, int nch, const int* __restrict__ rp, const int*
   } else if (mode == 2) {
     V res = vaxpby(T(1), bv[o], T(-1), acc);
     yv[o] = vaxpby(T(1), xv[o], omega * dinv[r], res);
-  } else {
+  } else if (mode == 4) {
     yv[o] = vaxpby(T(1), yv[o], T(1), acc);
+  } else {
+    yv[o] = vaxpby(T(1), bv[o], T(1), acc);
   }
 }
 

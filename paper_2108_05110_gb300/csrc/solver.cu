@@ -113,15 +113,26 @@ static void vcycle(const mhde_ctx* c, Sub& s, int l, const T* b, T* x, int Jp) {
   launch_csr<T>(R.nrows, R.rowptr, R.col, Prec<T>::Aval(R), nullptr, T(0), other, nullptr,
                 Prec<T>::b(wn), 0, Jp, st);
   vcycle<T>(c, s, l + 1, Prec<T>::b(wn), Prec<T>::x(wn), Jp);
+  // prolongation into the buffer from which the nsw post-smoothing sweeps
+  // (each writing the other buffer) end in x: no copy closes the level (the
+  // residual in `other` has been restricted already, so it may be overwritten)
   const DevCsr& P = op.P;
-  launch_csr<T>(P.nrows, P.rowptr, P.col, Prec<T>::Aval(P), nullptr, T(0), Prec<T>::x(wn), nullptr, cur, 4,
-                Jp, st);
+  T* post = (nsw % 2 == 1) ? (x == cur ? other : cur) : x;
+  if (post == cur) {
+    launch_csr<T>(P.nrows, P.rowptr, P.col, Prec<T>::Aval(P), nullptr, T(0), Prec<T>::x(wn), nullptr, cur, 4,
+                  Jp, st);
+  } else {
+    launch_csr<T>(P.nrows, P.rowptr, P.col, Prec<T>::Aval(P), nullptr, T(0), Prec<T>::x(wn), cur, post, 5,
+                  Jp, st);
+    other = cur;
+    cur = post;
+  }
   for (int k = 0; k < nsw; ++k) {
     launch_csr<T>(A.nrows, A.rowptr, A.col, Prec<T>::Aval(A), Prec<T>::Adinv(A), om, cur, b, other, 2,
                   Jp, st);
     std::swap(cur, other);
   }
-  if (cur != x)
+  if (cur != x)    // not reached: the parity above ends the sweeps in x
     cudaMemcpyAsync(x, cur, (size_t)A.nrows * Jp * sizeof(T), cudaMemcpyDeviceToDevice, st);
 }
 
