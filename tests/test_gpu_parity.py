@@ -149,6 +149,21 @@ def test_channel_small_mixed():
     sol.close()
 
 
+@pytest.mark.parametrize("amg_sweeps,amg_cycles", [(2, 1), (3, 2)])
+def test_vcycle_sweep_counts(amg_sweeps, amg_cycles):
+    """Even and odd smoothing-sweep counts and repeated V-cycles: each level's
+    prolongation targets the buffer from which the post-smoothing sweeps end
+    in the level's output, for either parity; the fields still reach the
+    oracle's to the mixed tolerance."""
+    ens = lid_cavity(N=16, J=5, s=1.0, nsteps=3, Re=2000.0)
+    ref = oracle_run(ens, 3)
+    sol = gpu_run(ens, 3, precision=PREC_MIXED, amg_sweeps=amg_sweeps, amg_cycles=amg_cycles)
+    v, w, _, _ = sol.read_state()
+    assert rel_l2(v, ref.V) <= MIXED_TOL and rel_l2(w, ref.W) <= MIXED_TOL
+    assert max(sol.stats().last_relres) <= 1e-12
+    sol.close()
+
+
 @pytest.mark.parametrize("inner_fp16", [0, 1])
 def test_inner_basis_storage(inner_fp16):
     """The mixed path with the inner GMRES basis in FP32 and in FP16: the
