@@ -10,7 +10,8 @@ Plain, slow and obviously correct: numpy for element-wise arithmetic, scipy
 sparse COO->CSR for assembly, SuperLU (``scipy.sparse.linalg.splu``) for the
 linear systems, all in float64.
 
-Discrete setting (the readings of the paper listed in the design doc):
+Discrete setting (where the paper leaves a choice open, this is the reading
+taken):
 * Taylor-Hood P2 velocity / P1 pressure on a conforming triangulation
   (Section 2, eq. infsup: any inf-sup stable pair);
 * a 7-point degree-5 triangle quadrature derived in :mod:`oracle.quadrature`;
@@ -20,11 +21,15 @@ Discrete setting (the readings of the paper listed in the design doc):
 * forcing as M times the P2 nodal interpolant.
 
 Pins: every function here is checked in ``tests/test_oracle_*.py`` against
-closed forms, exact integrals, brute force, the paper's convergence rates
-(Tables 1-6), the stability inequality of Section 3.1 and the special cases of
-Section 4.4 ("usual MHD").  Parity unpinned: the absolute error values of
-Tables 1-6 (the paper uses Scott-Vogelius elements on barycenter-refined
-meshes); only their rates are pinned.
+closed forms, exact integrals, brute force, the stability inequality of
+Section 3.1, the special cases of Section 4.4 ("usual MHD") and the paper's
+printed numbers: the spatial errors of Table 1 (for a pressure-free velocity,
+where the element pair does not enter the velocity error) and the temporal
+errors of Table 4, values and rates (``tests/golden/``).  The other tables'
+absolute errors are not pinned (the paper uses Scott-Vogelius elements on
+barycenter-refined meshes); with a pressure their second-order rates are.
+Its adjoint (:mod:`oracle.adjoint`) is pinned by central differences of this
+forward run.
 """
 from .quadrature import triangle_rule_deg5  # noqa: F401
 from .fe import P2Space  # noqa: F401
