@@ -324,8 +324,9 @@ def gram_bytes(sz, restart, prec_bytes):
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_gram_staged<20, 2, 512>
-# launch on the 128x128, J=20 workload with 16 blocks (191.97 MB + 4.58 MB)
-GRAM_TRAFFIC = 196.55e6
+# launch on the 128x128, J=20 workload with 16 blocks (191.97 MB + 4.57 MB, taken
+# with --set full on the current kernel, the one that opens with griddepcontrol.wait)
+GRAM_TRAFFIC = 196.54e6
 
 
 def our_arm(args, rank, world, local_rank):
@@ -403,8 +404,8 @@ def our_arm(args, rank, world, local_rank):
     gram_ms = sol.time_kernel(0, 8, reps=50)
     alg = gram_bytes(sol.sizes, sol.options.restart, pbytes)
     achieved = alg / (gram_ms / 1000.0) / 1e9
-    # DRAM bytes of one launch of this kernel at this size (ncu capture summarised
-    # in profiles/k_gram_staged_f32_cavity128_J20.md); only for the default workload
+    # DRAM bytes of one launch of this kernel at this size, from an ncu capture of
+    # the same launch configuration; known only for the default workload
     traffic = GRAM_TRAFFIC if (prec == PREC_MIXED and args.N == WORKLOAD["N"] and args.J == WORKLOAD["J"]
                                and sol.options.restart == 30) else None
     kname = "k_gram_staged, FP32" if pbytes == 4 else "k_gram, FP64"
