@@ -66,6 +66,11 @@ def test_create_rejects_bad_input():
     assert e.value.code == -2
     with pytest.raises(P.MhdeError):
         P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, strict=1, mu=0.4)
+    # option fields outside their ranges
+    for bad_opt in (dict(inner_fp16=2), dict(inner_iters=17), dict(poly_degree=3), dict(schur=2)):
+        with pytest.raises(P.MhdeError):
+            P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, **bad_opt)
+    P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, inner_fp16=1).close()
 
 
 def test_calls_before_bind_fail_cleanly():
