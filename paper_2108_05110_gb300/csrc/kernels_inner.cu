@@ -11,10 +11,13 @@
 // by Givens rotations and z = D^{-1} sum_l v_l y_l.
 //
 // Storage: w (the operator output) is kept in the arithmetic type T; the basis
-// v_0..v_{k-1} is kept in a storage type S, either T or, on the FP32 path,
-// FP16 scaled by sqrt(n2) (a unit column then has entries of order one, well
-// inside FP16's normal range).  Arithmetic is always in T; the FP16 basis
-// halves the traffic of the dot, update and final passes and of the gathers.
+// v_0..v_{k-1} is kept in a storage type S, either T or, on the FP32 path with
+// options.inner_fp16, FP16 scaled by sqrt(n2) (a unit column then has entries
+// of order one, well inside FP16's normal range).  Arithmetic is always in T.
+// The FP16 basis halves the traffic of the dot, update and final passes and
+// of the gathers; on the 128 x 128 cavity ensemble that left the time of an
+// application unchanged (the chain of dependent launches sets it), so it is
+// an option, not the default.
 #include <cmath>
 
 #include <cuda_fp16.h>
