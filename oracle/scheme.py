@@ -19,7 +19,7 @@ Algorithm 1:
     and its mirror for eq. weaknew2 (v <-> w, f1 -> f2), Dirichlet values
     g_{v,j}(t^{n+1}) on boundary rows, zeros on pressure rows;
  5. a direct sparse LU solve (SuperLU) per member, or one factorisation per
-    step shared by all members (same matrix, P:128 of the paper's Section 1);
+    step shared by all members (Section 1: every member has the same matrix);
  6. pressures shifted to mean zero on output (Q = L^2_0, Section 2).
 
 The time loop runs n = 0, ..., M-1 with forcing and boundary data at t^{n+1}.
