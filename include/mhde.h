@@ -78,13 +78,8 @@ typedef struct {
   double jacobi_omega;  /* damping of those sweeps; default 0.3 */
   int amg_sweeps;       /* Jacobi sweeps per level in the pressure-Laplacian V-cycle; default 1 */
   int amg_cycles;       /* V-cycles per application of the pressure-Laplacian inverse; default 1 */
-  int poly_degree;      /* degree d (even, <= 16) of the GMRES polynomial in D^{-1} F that
-                           approximates F^{-1}, rebuilt every step from d Arnoldi steps;
-                           0 = use inner_iters instead; default 0 (the fixed polynomial is
-                           cheaper per application but lost robustness as the cavity flow
-                           developed, so the inner GMRES is the default) */
-  int inner_iters;      /* k of the inner per-column GMRES(k) on F (flexible outer GMRES), used
-                           when poly_degree = 0; 0 = damped Jacobi sweeps instead; default 6
+  int inner_iters;      /* k of the inner per-column GMRES(k) on F (flexible outer GMRES);
+                           0 = damped Jacobi sweeps instead; default 6
                            (on the 128x128 cavity ensemble 6 inner steps and one smoothing
                            sweep per AMG level cost more outer iterations than 8 and 2 but
                            less time per step) */
@@ -294,7 +289,7 @@ int mhde_block_gram_scratch_bytes(int n_rows, int r, int kblocks, size_t* bytes)
 /* G[i][p][q] = sum_rows V_i[row][p] W[row][q] for i < kblocks, p, q < r.
  * V_i = V + i * v_stride (elements); V_i and W are row-major [n_rows][ld]
  * with ld a multiple of 4, r <= ld <= 64 (columns r..ld-1 are read but do
- * not enter G).  G: device [kblocks][r][r].  scratch: device, at least
+ * not enter G), 1 <= kblocks <= 65535.  G: device [kblocks][r][r].  scratch: device, at least
  * mhde_block_gram_scratch_bytes() bytes, owned by the caller; fully
  * rewritten by every call.  The summation order is fixed (deterministic).
  * Errors: MHDE_EINVAL (bad sizes / NULL), MHDE_EWORKSPACE (scratch too
@@ -311,8 +306,11 @@ int mhde_block_gram(const double* V, size_t v_stride, int kblocks, const double*
  * loading the library holds until the process exits.  Sizes whose partials
  * for one row chunk exceed it (kblocks * r * r > 262144) are rejected with
  * MHDE_EWORKSPACE; larger n_rows are handled with fewer, longer chunks.
+ * kblocks > 65535 is MHDE_EINVAL, as for mhde_block_gram.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not call again on a device after a
+ * cudaDeviceReset of it in the same process (the kept address is then stale).  All
  * calls share the array, so calls that overlap on the GPU (different streams
  * without ordering) race; order them on one stream.  Every call rewrites the
  * partials it uses, so no clearing is needed.  Allocates nothing: no

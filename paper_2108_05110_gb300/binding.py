@@ -37,7 +37,6 @@ class Options(C.Structure):
                 ("rtol", C.c_double), ("inner_rtol", C.c_double), ("restart", C.c_int),
                 ("max_iter", C.c_int), ("max_refine", C.c_int), ("jacobi_sweeps", C.c_int),
                 ("jacobi_omega", C.c_double), ("amg_sweeps", C.c_int), ("amg_cycles", C.c_int),
-                ("poly_degree", C.c_int),
                 ("inner_iters", C.c_int),
                 ("schur", C.c_int), ("strict", C.c_int), ("inner_fp16", C.c_int)]
 

@@ -116,7 +116,6 @@ size_t layout(mhde_ctx* c, char* base) {
   }
   c->d_coarse_inv = w.take<double>((size_t)amg.nc * amg.nc);
   c->d_coarse_invf = w.take<float>((size_t)amg.nc * amg.nc);
-  c->d_prand = w.take<char>(n2 * 4 * ksize(c));
   c->d_ccross = w.take<double>(Jp);
   c->d_csame = w.take<double>(Jp);
   // inputs and ensemble quantities
@@ -158,10 +157,11 @@ size_t layout(mhde_ctx* c, char* base) {
     s.coef = w.take<char>(4 * (size_t)(m + 1) * c->J * c->J * 8);
     s.colsq = w.take<double>((size_t)c->nchunk * Jp);
     s.dscale = w.take<double>(2 * Jp);
+    s.d_err = w.take<int>(1);                 // zeroed with the workspace at bind
     s.Np = w.take<double>(fe.Kp.nnz());
     s.Npf = w.take<float>(fe.Kp.nnz());
     {
-      const int kin = std::max({1, c->opt.inner_iters, c->opt.poly_degree});
+      const int kin = std::max(1, c->opt.inner_iters);
       const size_t C2 = 2 * Jp;
       s.ibasis = w.take<char>((size_t)(kin + 1) * n2 * C2 * ks);
       s.ipart = w.take<double>((size_t)c->nchunk_in * (KIN_MAX + 2) * C2);
@@ -170,7 +170,6 @@ size_t layout(mhde_ctx* c, char* base) {
       s.ibeta = w.take<double>(4 * C2);                              // beta, 1/norm, float copy of 1/norm
       s.iy = w.take<double>((size_t)kin * C2 * 2);                   // doubles, then a float copy
       s.zbasis = w.take<char>((size_t)m * vs * ks);
-      s.poly = w.take<double>(KIN_MAX + 2);
     }
     s.amg.assign(amg.levels.size(), DevAmgLevel());
     for (size_t l = 0; l < amg.levels.size(); ++l) {
@@ -284,7 +283,6 @@ void mhde_default_options(mhde_options* o) {
   o->jacobi_omega = 0.3;
   o->amg_sweeps = 1;
   o->amg_cycles = 1;
-  o->poly_degree = 0;
   o->inner_iters = 6;
   o->schur = 1;
   o->strict = 0;
@@ -303,8 +301,8 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
     mhde_default_options(&c->opt);
   if (c->opt.restart < 1 || c->opt.restart > 200 || c->opt.max_iter < 1 || !(c->opt.rtol > 0) ||
       (c->opt.precision != MHDE_PREC_FP64 && c->opt.precision != MHDE_PREC_MIXED) ||
-      (c->opt.conv_form != 0 && c->opt.conv_form != 1) || c->opt.inner_iters < 0 || c->opt.poly_degree < 0 ||
-      c->opt.poly_degree > mhde::KIN_MAX || c->opt.poly_degree % 2 != 0 || c->opt.amg_cycles < 1 ||
+      (c->opt.conv_form != 0 && c->opt.conv_form != 1) || c->opt.inner_iters < 0 ||
+      c->opt.amg_cycles < 1 ||
       c->opt.inner_iters > mhde::KIN_MAX || (c->opt.schur != 0 && c->opt.schur != 1) ||
       (c->opt.inner_fp16 != 0 && c->opt.inner_fp16 != 1)) {
     delete c;
@@ -452,25 +450,6 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
     cs[j] = c->c_same[j];
   }
   CU(up(c->d_ccross, cc, st));
-  {
-    // fixed pseudo-random start block of the per-step polynomial setup
-    std::vector<double> pr((size_t)fe.n2 * 4);
-    unsigned long long x = 0x9E3779B97F4A7C15ull;
-    for (auto& v : pr) {
-      x ^= x << 13;
-      x ^= x >> 7;
-      x ^= x << 17;
-      v = (double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5;
-    }
-    if (ksize(c) == 8) {
-      CU(cudaMemcpyAsync(c->d_prand, pr.data(), pr.size() * 8, cudaMemcpyHostToDevice, st));
-      CU(cudaStreamSynchronize(st));
-    } else {
-      std::vector<float> pf(pr.begin(), pr.end());
-      CU(cudaMemcpyAsync(c->d_prand, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice, st));
-      CU(cudaStreamSynchronize(st));
-    }
-  }
   CU(up(c->d_csame, cs, st));
   // AMG operators
   std::vector<std::vector<float>> keep_f;   // host float copies alive until the sync below
@@ -647,7 +626,7 @@ static int run_sub(mhde_ctx* c, int which) {
     if (e != cudaSuccess) {
       s.err = std::string("stream: ") + cudaGetErrorString(e);
       rc = MHDE_ECUDA;
-    } else if (take_async_error(s.stream) != 0) {
+    } else if (take_async_error(s.d_err, s.stream) != 0) {
       // a Gram launch gave up waiting for a TMA stage (bounded wait): the
       // solve used incomplete projections, so the step is not accepted
       s.err = "a block Gram launch timed out waiting for its shared-memory stage";

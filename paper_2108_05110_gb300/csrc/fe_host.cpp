@@ -689,239 +689,3 @@ void BlockLS::solve(std::vector<double>& Y) const {
 }
 
 }  // namespace mhde
-
-// ------------------------------------------------------------- polynomial roots
-namespace mhde {
-
-namespace {
-inline double sgn(double a, double b) { return b >= 0.0 ? std::fabs(a) : -std::fabs(a); }
-}  // namespace
-
-// Eigenvalues of a real upper Hessenberg matrix (row-major n x n, destroyed)
-// by the Francis double-shift QR algorithm with deflation on negligible
-// subdiagonal entries.  Returns false if an eigenvalue fails to converge.
-bool eig_hessenberg(int n, double* a, double* wr, double* wi) {
-  auto A = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
-  double anorm = 0.0;
-  for (int i = 0; i < n; ++i)
-    for (int j = std::max(i - 1, 0); j < n; ++j) anorm += std::fabs(A(i, j));
-  int nn = n - 1;
-  double t = 0.0;
-  while (nn >= 0) {
-    int its = 0, l;
-    do {
-      for (l = nn; l >= 1; --l) {
-        double s = std::fabs(A(l - 1, l - 1)) + std::fabs(A(l, l));
-        if (s == 0.0) s = anorm;
-        if (std::fabs(A(l, l - 1)) + s == s) {
-          A(l, l - 1) = 0.0;
-          break;
-        }
-      }
-      double x = A(nn, nn);
-      if (l == nn) {                       // one eigenvalue found
-        wr[nn] = x + t;
-        wi[nn] = 0.0;
-        --nn;
-      } else {
-        double y = A(nn - 1, nn - 1);
-        double w = A(nn, nn - 1) * A(nn - 1, nn);
-        if (l == nn - 1) {                 // a 2x2 block: two eigenvalues
-          double p = 0.5 * (y - x);
-          double q = p * p + w;
-          double z = std::sqrt(std::fabs(q));
-          x += t;
-          if (q >= 0.0) {
-            z = p + sgn(z, p);
-            wr[nn - 1] = wr[nn] = x + z;
-            if (z != 0.0) wr[nn] = x - w / z;
-            wi[nn - 1] = wi[nn] = 0.0;
-          } else {
-            wr[nn - 1] = wr[nn] = x + p;
-            wi[nn - 1] = -z;
-            wi[nn] = z;
-          }
-          nn -= 2;
-        } else {                           // a double-shift QR sweep on rows l..nn
-          if (its == 60) return false;
-          if (its == 10 || its == 20) {    // exceptional shift
-            t += x;
-            for (int i = 0; i <= nn; ++i) A(i, i) -= x;
-            double s = std::fabs(A(nn, nn - 1)) + std::fabs(A(nn - 1, nn - 2));
-            y = x = 0.75 * s;
-            w = -0.4375 * s * s;
-          }
-          ++its;
-          int m;
-          double p = 0.0, q = 0.0, r = 0.0, z;
-          for (m = nn - 2; m >= l; --m) {
-            z = A(m, m);
-            r = x - z;
-            double s = y - z;
-            p = (r * s - w) / A(m + 1, m) + A(m, m + 1);
-            q = A(m + 1, m + 1) - z - r - s;
-            r = A(m + 2, m + 1);
-            s = std::fabs(p) + std::fabs(q) + std::fabs(r);
-            p /= s;
-            q /= s;
-            r /= s;
-            if (m == l) break;
-            double u = std::fabs(A(m, m - 1)) * (std::fabs(q) + std::fabs(r));
-            double v = std::fabs(p) * (std::fabs(A(m - 1, m - 1)) + std::fabs(z) + std::fabs(A(m + 1, m + 1)));
-            if (u + v == v) break;
-          }
-          for (int i = m + 2; i <= nn; ++i) {
-            A(i, i - 2) = 0.0;
-            if (i != m + 2) A(i, i - 3) = 0.0;
-          }
-          for (int k = m; k <= nn - 1; ++k) {
-            if (k != m) {
-              p = A(k, k - 1);
-              q = A(k + 1, k - 1);
-              r = (k != nn - 1) ? A(k + 2, k - 1) : 0.0;
-              x = std::fabs(p) + std::fabs(q) + std::fabs(r);
-              if (x != 0.0) {
-                p /= x;
-                q /= x;
-                r /= x;
-              }
-            }
-            double s = sgn(std::sqrt(p * p + q * q + r * r), p);
-            if (s != 0.0) {
-              if (k == m) {
-                if (l != m) A(k, k - 1) = -A(k, k - 1);
-              } else {
-                A(k, k - 1) = -s * x;
-              }
-              p += s;
-              x = p / s;
-              y = q / s;
-              z = r / s;
-              q /= p;
-              r /= p;
-              for (int j = k; j <= nn; ++j) {
-                p = A(k, j) + q * A(k + 1, j);
-                if (k != nn - 1) {
-                  p += r * A(k + 2, j);
-                  A(k + 2, j) -= p * z;
-                }
-                A(k + 1, j) -= p * y;
-                A(k, j) -= p * x;
-              }
-              int mmin = nn < k + 3 ? nn : k + 3;
-              for (int i = l; i <= mmin; ++i) {
-                p = x * A(i, k) + y * A(i, k + 1);
-                if (k != nn - 1) {
-                  p += z * A(i, k + 2);
-                  A(i, k + 2) -= p * r;
-                }
-                A(i, k + 1) -= p * q;
-                A(i, k) -= p;
-              }
-            }
-          }
-        }
-      }
-    } while (nn >= 0 && l < nn - 1);
-  }
-  return true;
-}
-
-// Quadratic factors (c1, c2) of the GMRES residual polynomial
-// pi(z) = prod (1 - c1 z + c2 z^2) from a (d+1) x d Arnoldi Hessenberg
-// matrix H (row-major): roots are the harmonic Ritz values (eigenvalues of
-// H_d + h_{d+1,d}^2 H_d^{-T} e_d e_d^T), grouped into conjugate or real
-// pairs and ordered by a Leja-type rule on the pairs for a stable product.
-bool gmres_poly_factors(int d, const double* H, std::vector<double>& c1, std::vector<double>& c2) {
-  if (d < 2 || d % 2) return false;
-  std::vector<double> Hd((size_t)d * d);
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j < d; ++j) Hd[(size_t)i * d + j] = H[(size_t)i * d + j];
-  // f = H_d^{-T} e_d: solve H_d^T f = e_d (dense Gaussian elimination with pivoting)
-  std::vector<double> M((size_t)d * d), f(d, 0.0);
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j < d; ++j) M[(size_t)i * d + j] = Hd[(size_t)j * d + i];
-  f[d - 1] = 1.0;
-  for (int col = 0; col < d; ++col) {
-    int piv = col;
-    for (int r = col + 1; r < d; ++r)
-      if (std::fabs(M[(size_t)r * d + col]) > std::fabs(M[(size_t)piv * d + col])) piv = r;
-    if (M[(size_t)piv * d + col] == 0.0) return false;
-    if (piv != col) {
-      for (int k = 0; k < d; ++k) std::swap(M[(size_t)piv * d + k], M[(size_t)col * d + k]);
-      std::swap(f[piv], f[col]);
-    }
-    for (int r = col + 1; r < d; ++r) {
-      double m = M[(size_t)r * d + col] / M[(size_t)col * d + col];
-      for (int k = col; k < d; ++k) M[(size_t)r * d + k] -= m * M[(size_t)col * d + k];
-      f[r] -= m * f[col];
-    }
-  }
-  for (int r = d - 1; r >= 0; --r) {
-    double s = f[r];
-    for (int k = r + 1; k < d; ++k) s -= M[(size_t)r * d + k] * f[k];
-    f[r] = s / M[(size_t)r * d + r];
-  }
-  const double h2 = H[(size_t)d * d + (d - 1)] * H[(size_t)d * d + (d - 1)];
-  for (int i = 0; i < d; ++i) Hd[(size_t)i * d + (d - 1)] += h2 * f[i];
-  for (double v : Hd)
-    if (!std::isfinite(v)) return false;
-  std::vector<double> wr(d), wi(d);
-  if (!eig_hessenberg(d, Hd.data(), wr.data(), wi.data())) return false;
-  for (int i = 0; i < d; ++i)
-    if (!std::isfinite(wr[i]) || !std::isfinite(wi[i])) return false;
-  // pairs: conjugate pairs first as they come, then real roots paired in
-  // order of decreasing modulus
-  struct Pair { double c1, c2, re, im; };
-  std::vector<Pair> pairs;
-  std::vector<double> reals;
-  for (int i = 0; i < d; ++i) {
-    if (wi[i] > 0.0) {
-      double m2 = wr[i] * wr[i] + wi[i] * wi[i];
-      pairs.push_back({2.0 * wr[i] / m2, 1.0 / m2, wr[i], wi[i]});
-    } else if (wi[i] == 0.0) {
-      if (wr[i] == 0.0) return false;
-      reals.push_back(wr[i]);
-    }
-  }
-  std::sort(reals.begin(), reals.end(), [](double a, double b) { return std::fabs(a) > std::fabs(b); });
-  if (reals.size() % 2) return false;
-  for (size_t i = 0; i + 1 < reals.size(); i += 2)
-    pairs.push_back({1.0 / reals[i] + 1.0 / reals[i + 1], 1.0 / (reals[i] * reals[i + 1]),
-                     0.5 * (reals[i] + reals[i + 1]), 0.0});
-  if ((int)pairs.size() * 2 != d) return false;
-  // Leja-type order on pair centres: start at the largest modulus, then
-  // repeatedly take the pair maximising the product of distances
-  std::vector<int> order;
-  std::vector<bool> used(pairs.size(), false);
-  int first = 0;
-  for (size_t i = 1; i < pairs.size(); ++i)
-    if (std::hypot(pairs[i].re, pairs[i].im) > std::hypot(pairs[first].re, pairs[first].im)) first = (int)i;
-  order.push_back(first);
-  used[first] = true;
-  while (order.size() < pairs.size()) {
-    int best = -1;
-    double bestv = -std::numeric_limits<double>::infinity();
-    for (size_t i = 0; i < pairs.size(); ++i) {
-      if (used[i]) continue;
-      double v = 0.0;
-      for (int o : order) v += std::log(std::hypot(pairs[i].re - pairs[o].re, pairs[i].im - pairs[o].im) + 1e-300);
-      if (best < 0 || v > bestv) {
-        bestv = v;
-        best = (int)i;
-      }
-    }
-    if (best < 0) return false;
-    order.push_back(best);
-    used[best] = true;
-  }
-  c1.clear();
-  c2.clear();
-  for (int o : order) {
-    c1.push_back(pairs[o].c1);
-    c2.push_back(pairs[o].c2);
-  }
-  return true;
-}
-
-}  // namespace mhde

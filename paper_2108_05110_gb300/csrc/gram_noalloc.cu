@@ -24,7 +24,9 @@ double* g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
 
 // Device address of the scratch array for the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device with that device current.
+// once per device with that device current and cached for the life of the
+// process; a cudaDeviceReset of that device in the same process would leave
+// the cached address stale (this library never resets a device).
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -47,8 +49,9 @@ extern "C" {
 
 int mhde_block_gram_noalloc(const double* V, size_t v_stride, int kblocks, const double* W, int n_rows, int ld,
                             int r, double* G, void* stream) {
-  if (!V || !W || !G || n_rows < 1 || kblocks < 1 || r < 1 || r > mhde::MAX_J || ld < r || ld % 4 != 0 ||
-      ld > mhde::MAX_J)
+  // one grid row per basis block: at most 65535 blocks (the grid's y limit)
+  if (!V || !W || !G || n_rows < 1 || kblocks < 1 || kblocks > 65535 || r < 1 || r > mhde::MAX_J || ld < r ||
+      ld % 4 != 0 || ld > mhde::MAX_J)
     return MHDE_EINVAL;
   const size_t per_chunk = (size_t)kblocks * r * r;
   if (per_chunk > NOALLOC_GRAM_SCRATCH_DOUBLES) return MHDE_EWORKSPACE;   // beyond the fixed maximum

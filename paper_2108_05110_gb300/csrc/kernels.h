@@ -101,23 +101,29 @@ void launch_precond_p(int np, int Jp, const T* x, const T* rp, const T* mp, T in
 template <typename T>
 void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu, int ld,
                      cudaStream_t st);
-// Gram partial sums: part[chunk][i][p][q] = sum_rows V_i[row][p] W[row][q]
+// Gram partial sums: part[chunk][i][p][q] = sum_rows V_i[row][p] W[row][q].
+// err: the calling subproblem's device error word; with it the FP32 Gram may
+// take the TMA-staged kernel, which sets *err = 1 when a stage never lands
+// (nullptr: the unstaged kernels only)
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
-                 int nchunk, double* part, double* gram, cudaStream_t st, bool reduce = true);
+                 int nchunk, double* part, double* gram, cudaStream_t st, bool reduce = true,
+                 int* err = nullptr);
 // G = [H_0 .. H_k, W^T W] (r x r blocks) -> block k+2 := W^T W - sum_i H_i^T H_i
 void launch_proj_gram(double* G, int k, int r, cudaStream_t st);
-// 1 if a staged-Gram launch gave up waiting for a TMA stage since the last
-// call (the flag is then cleared), 0 if not, -1 on a CUDA error
-int take_async_error(cudaStream_t st);
+// 1 if a staged Gram or combine launch of the subproblem owning d_err gave
+// up waiting for a TMA stage since the last call (the word is then cleared
+// on st), 0 if not, -1 on a CUDA error
+int take_async_error(int* d_err, cudaStream_t st);
 // C_i = -H_i T (i <= k), C_{k+1} = T, converted to the Krylov precision
 template <typename T>
 void launch_make_coef(const double* G, const double* Tm, int k, int r, T* C, cudaStream_t st);
 // out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q], q < r_out; 0 beyond
-// (V rows have stride ldv, in/out rows stride Jp)
+// (V rows have stride ldv, in/out rows stride Jp); err as for launch_gram
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
-                          int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st);
+                          int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st,
+                          int* err = nullptr);
 // out[row][q] = (T) sum_p X[row][p] C[p][q], q < r (0 beyond); X, C (J x r) in FP64;
 // X rows have stride Jp, out rows stride ldo
 template <typename T>
@@ -149,11 +155,6 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* 
 // shared-memory limits of the inner and block kernels (set once, before any capture)
 cudaError_t init_inner_attributes();
 cudaError_t init_la_attributes();
-// GMRES-polynomial approximation z ~ F^{-1} r with the factors in s.poly
-template <typename T>
-void launch_poly_apply(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
-                       cudaStream_t st);
-
 // solver entry points (solver.cu)
 int assemble_sub(mhde_ctx* c, int which);
 // zero_guess: start from X = 0 (transposed adjoint solves) instead of the

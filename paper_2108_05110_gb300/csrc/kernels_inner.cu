@@ -471,105 +471,4 @@ template void launch_inner_gmres<double>(const mhde_ctx*, const Sub&, const doub
 template void launch_inner_gmres<float>(const mhde_ctx*, const Sub&, const float*, const float*, const float*,
                                         float*, int, int, cudaStream_t, bool);
 
-// ------------------------------------------------------------ GMRES polynomial
-// z ~ F^{-1} r as q(A) D^{-1} r with A = D^{-1} F and q(z) = (1 - pi(z)) / z,
-// pi(z) = prod_i (1 - c1_i z + c2_i z^2).  Per quadratic factor:
-//   y   += c1 prod - c2 A prod
-//   prod = prod - c1 A prod + c2 A^2 prod
-// Rows are [n2][C] (C = 2 ld: component, member); Dirichlet rows of F are
-// identity rows and get z = r exactly.
-
-// w = D^{-1} F prod
-template <typename T>
-__global__ void k_poly_a(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
-                         const T* __restrict__ F, const T* __restrict__ dinv, const T* __restrict__ prod,
-                         T* __restrict__ w) {
-  using V = typename IVec<T>::type;
-  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= (long long)n2 * nch) return;
-  int a = (int)(tid / nch), ch = (int)(tid % nch);
-  const V* pv = reinterpret_cast<const V*>(prod);
-  V acc = izero(V());
-  for (int k = rp[a]; k < rp[a + 1]; ++k) ifma(acc, F[k], pv[(size_t)col[k] * nch + ch]);
-  const T d = dinv[a];
-  V out;
-  out.x = d * acc.x;
-  out.y = d * acc.y;
-  if constexpr (IVec<T>::W == 4) {
-    out.z = d * acc.z;
-    out.w = d * acc.w;
-  }
-  reinterpret_cast<V*>(w)[(size_t)a * nch + ch] = out;
-}
-
-// t = A w (gathered), then the factor update of y and prod at the own row.
-// last: no prod update, Dirichlet rows set y = r.
-template <typename T, bool LAST>
-__global__ void k_poly_b(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
-                         const T* __restrict__ F, const T* __restrict__ dinv, const unsigned char* __restrict__ isbnd,
-                         const double* __restrict__ coef, int item, int first, T* prod, const T* __restrict__ w,
-                         T* y, const T* __restrict__ r) {
-  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= (long long)n2 * nch) return;
-  constexpr int W = IVec<T>::W;
-  const int a = (int)(tid / nch), ch = (int)(tid % nch);
-  const T c1 = (T)coef[2 * item], c2 = (T)coef[2 * item + 1];
-  const size_t o = ((size_t)a * nch + ch) * W;
-  T tv[W];
-  if (!LAST) {
-    for (int q = 0; q < W; ++q) tv[q] = T(0);
-    for (int k = rp[a]; k < rp[a + 1]; ++k) {
-      const T f = F[k];
-      const size_t oc = ((size_t)col[k] * nch + ch) * W;
-#pragma unroll
-      for (int q = 0; q < W; ++q) tv[q] += f * w[oc + q];
-    }
-  }
-  const T d = dinv[a];
-  const bool bnd = isbnd[a] != 0;
-#pragma unroll
-  for (int q = 0; q < W; ++q) {
-    const T pq = prod[o + q], wq = w[o + q];
-    T yq = (first ? T(0) : y[o + q]) + c1 * pq - c2 * wq;
-    if (LAST && bnd) yq = r[o + q];
-    y[o + q] = yq;
-    if (!LAST) prod[o + q] = pq - c1 * wq + c2 * d * tv[q];
-  }
-}
-
-template <typename T>
-__global__ void k_poly_scale(long long n, int C, const T* __restrict__ dinv, const T* __restrict__ r,
-                             T* __restrict__ prod) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  prod[i] = dinv[i / C] * r[i];
-}
-
-template <typename T>
-void launch_poly_apply(const mhde_ctx* c, const Sub& s, const T* Fv, const T* dinv, const T* r, T* z, int ld,
-                       cudaStream_t st) {
-  const int n2 = c->fe.n2, C = 2 * ld, d = c->opt.poly_degree, items = d / 2;
-  const int nch = C / IVec<T>::W;
-  const long long nel = (long long)n2 * C;
-  T* prod = (T*)s.ibasis;
-  T* w = prod + (size_t)n2 * C;
-  count_launch(1 + 2 * items);
-  k_poly_scale<T><<<nb(nel, 256), 256, 0, st>>>(nel, C, dinv, r, prod);
-  const unsigned g = nb((long long)n2 * nch, 256);
-  for (int i = 0; i < items; ++i) {
-    k_poly_a<T><<<g, 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, prod, w);
-    if (i + 1 < items)
-      k_poly_b<T, false><<<g, 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, c->d_isbnd, s.poly, i, i == 0,
-                                            prod, w, z, r);
-    else
-      k_poly_b<T, true><<<g, 256, 0, st>>>(n2, nch, c->F.rowptr, c->F.col, Fv, dinv, c->d_isbnd, s.poly, i, i == 0,
-                                           prod, w, z, r);
-  }
-}
-
-template void launch_poly_apply<double>(const mhde_ctx*, const Sub&, const double*, const double*, const double*,
-                                        double*, int, cudaStream_t);
-template void launch_poly_apply<float>(const mhde_ctx*, const Sub&, const float*, const float*, const float*,
-                                       float*, int, cudaStream_t);
-
 }  // namespace mhde

@@ -663,7 +663,8 @@ __global__ void __launch_bounds__(32 * GR_WARPS) k_gram_reduce(int nparts, int t
 // own partial, so every sum has a fixed order.
 //
 // Every wait on a stage's mbarrier is bounded: past GS_SPIN_LIMIT polls the
-// thread records the failure in g_async_err, waits (again bounded) for the
+// thread records the failure in the caller's error word (one per subproblem,
+// so concurrent subproblems never see each other's flags), waits (again bounded) for the
 // CTA's copies still in flight, and the kernel returns without its partials.
 constexpr int GS_T = 256;
 constexpr int GS_NST = 3;
@@ -671,7 +672,6 @@ constexpr size_t GS_SMEM = 192 * 1024;
 constexpr size_t GS_BAR_BYTES = 64;                   // mbarriers in front of the stages
 constexpr long long GS_SPIN_LIMIT = 1ll << 24;
 
-__device__ int g_async_err = 0;
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
@@ -707,14 +707,14 @@ template <int W, int PC, int NTH>
 __global__ void __launch_bounds__(NTH, 1) k_gram_staged(const float* __restrict__ V, size_t vstride, int kblocks,
                                                       const float* __restrict__ Wm, int n_rows, int ld, int r,
                                                       int rows_per_chunk, int S, int TR, int tstride,
-                                                      double* __restrict__ part) {
+                                                      double* __restrict__ part, int* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char gsm_raw[];
   // every bulk copy needs 16-byte aligned tiles and rows; the host plan
   // guarantees it, and a launch that breaks it copies nothing
   if ((tstride & 3) || (ld & 3) || ((TR * ld) & 3)) {
-    if (threadIdx.x == 0) atomicExch(&g_async_err, 1);
+    if (threadIdx.x == 0) atomicExch(err, 1);
     return;
   }
   float* gsm = reinterpret_cast<float*>(gsm_raw + GS_BAR_BYTES);
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gram_staged(const float* __restrict_
     // a stage did not land in time: record it, give every copy this CTA
     // issued a bounded chance to finish, and leave without partials
     if (threadIdx.x == 0) {
-      atomicExch(&g_async_err, 1);
+      atomicExch(err, 1);
       const int issued = min(ntiles, waited + GS_NST - 1);
       for (int tl = waited; tl < issued; ++tl)
         mbar_wait_bounded(bar0 + 8 * (tl % GS_NST), (unsigned)((tl / GS_NST) & 1));
@@ -820,13 +820,14 @@ __global__ void __launch_bounds__(NTH, 1) k_gram_staged(const float* __restrict_
   }
 }
 
-// Reads and clears the bounded-wait failure flag of the staged Gram (set when
-// a TMA stage did not land within its poll limit).
-int take_async_error(cudaStream_t st) {
-  int h = 0, zero = 0;
-  if (cudaMemcpyFromSymbolAsync(&h, g_async_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+// Reads and clears a subproblem's bounded-wait failure word (set by a staged
+// Gram or combine launch whose TMA stage did not land within its poll limit),
+// on that subproblem's stream only.
+int take_async_error(int* d_err, cudaStream_t st) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
   if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
-  if (h) cudaMemcpyToSymbolAsync(g_async_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  if (h && cudaMemsetAsync(d_err, 0, sizeof(int), st) != cudaSuccess) return -1;
   return h;
 }
 
@@ -850,14 +851,14 @@ static bool gram_staged_plan(int kblocks, int ld, int r, int pc, int& TR, int& t
 template <int W, int PC, int NTH>
 static void gram_staged(const float* V, size_t vstride, int kblocks, const float* Wm, int n_rows, int ld, int r,
                         int nchunk, int nsm, int TR, int tstride, size_t smem, double* part, cudaStream_t st,
-                        int& nparts) {
+                        int& nparts, int* err) {
   const int items = kblocks * ((r + PC - 1) / PC);
   const int S = std::max(1, std::min(NTH / items, nchunk));
   const int nctas = std::max(1, std::min(nchunk / S, nsm));
   const int rows_per_chunk = (n_rows + nctas - 1) / nctas;
   nparts = nctas * S;
   launch_pdl(k_gram_staged<W, PC, NTH>, dim3(nctas), dim3(NTH), smem, st, V, vstride, kblocks, Wm, n_rows, ld, r,
-             rows_per_chunk, S, TR, tstride, part);
+             rows_per_chunk, S, TR, tstride, part, err);
 }
 
 static cudaError_t combine_staged_attr();
@@ -874,12 +875,9 @@ static std::mutex g_gram_mutex;
 static GramDevice g_gram_dev[64];
 
 static const GramDevice& gram_setup() {
-  static GramDevice none;
+  static const GramDevice none{false, 1, cudaErrorInvalidDevice};   // never written
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    none.err = cudaErrorInvalidDevice;
-    return none;
-  }
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return none;
   std::lock_guard<std::mutex> lock(g_gram_mutex);
   GramDevice& d = g_gram_dev[dev];
   if (d.ready) return d;
@@ -928,7 +926,7 @@ static size_t gram_smem(int Jp, int r) {
 // scratch the caller provides), then one reduction.
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
-                 int nchunk, double* part, double* gram, cudaStream_t st, bool reduce) {
+                 int nchunk, double* part, double* gram, cudaStream_t st, bool reduce, int* err) {
   count_launch(reduce ? 2 : 1);
   const GramDevice& gd = gram_setup();               // on failure the unstaged kernels run instead
   const int w = (r + 3) / 4 * 4;
@@ -942,7 +940,9 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
     return (e && std::atoi(e) == 4) ? 4 : 2;
   }();
   const int pc = pc_env, nth = pc == 4 ? 256 : 512;
-  const bool staged = gd.err == cudaSuccess && sizeof(T) == 4 && kblocks * ((r + pc - 1) / pc) <= nth && w <= 24 &&
+  // the staged kernels report a stage that never landed through `err`, so
+  // they run only for callers that read it
+  const bool staged = err != nullptr && gd.err == cudaSuccess && sizeof(T) == 4 && kblocks * ((r + pc - 1) / pc) <= nth && w <= 24 &&
                       gram_staged_plan(kblocks, Jp, r, pc, TR, tstride, smem);
   if (staged) {
     const float* Vf = reinterpret_cast<const float*>(V);
@@ -951,10 +951,10 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
   do {                                                                                                         \
     if (pc == 4)                                                                                               \
       gram_staged<WV, 4, 256>(Vf, vstride, kblocks, Wf, n_rows, Jp, r, nchunk, gd.nsm, TR, tstride, smem, part, \
-                              st, nparts);                                                                     \
+                              st, nparts, err);                                                                \
     else                                                                                                       \
       gram_staged<WV, 2, 512>(Vf, vstride, kblocks, Wf, n_rows, Jp, r, nchunk, gd.nsm, TR, tstride, smem, part, \
-                              st, nparts);                                                                     \
+                              st, nparts, err);                                                                \
   } while (0)
     switch (w) {
       case 4: MHDE_GS(4); break;
@@ -1171,12 +1171,12 @@ template <int W, int CB_T, int CB_NST>
 __global__ void __launch_bounds__(CB_T) k_combine_staged(float* out, const float* in, float alpha, const float* V,
                                                        size_t vstride, int kblocks, int r_in,
                                                        const float* __restrict__ C, int r_out, int n_rows, int ldv,
-                                                       int ldo) {
+                                                       int ldo, int* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char cb_raw[];
   if ((ldv & 3) || (ldo & 3) || (vstride & 3) || (reinterpret_cast<uintptr_t>(V) & 15)) {   // 16-byte copies
-    if (threadIdx.x == 0) atomicExch(&g_async_err, 1);
+    if (threadIdx.x == 0) atomicExch(err, 1);
     return;
   }
   constexpr int CB_ROWS = 2 * CB_T;
@@ -1257,7 +1257,7 @@ __global__ void __launch_bounds__(CB_T) k_combine_staged(float* out, const float
   }
   if (!ok) {
     if (threadIdx.x == 0) {
-      atomicExch(&g_async_err, 1);
+      atomicExch(err, 1);
       const int issued = min(kblocks, waited + CB_NST - 1);
       for (int b = waited; b < issued; ++b) mbar_wait_bounded(bar0 + 8 * (b % CB_NST), (unsigned)((b / CB_NST) & 1));
     }
@@ -1334,19 +1334,20 @@ static size_t combine_staged_smem(int kblocks, int W, int ldv, int nt, int nst) 
 
 template <int W, int NT, int NST>
 static bool combine_staged_try(float* out, const float* in, float alpha, const float* V, size_t vstride, int kblocks,
-                               int r_in, const float* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st) {
+                               int r_in, const float* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st,
+                               int* err) {
   const size_t smem = combine_staged_smem(kblocks, W, ldv, NT, NST);
-  if ((size_t)kblocks * W * W * sizeof(float) > CB_COEF_MAX || smem > GS_SMEM || ldv % 4 != 0 || ldo % 4 != 0 ||
+  if (err == nullptr || (size_t)kblocks * W * W * sizeof(float) > CB_COEF_MAX || smem > GS_SMEM || ldv % 4 != 0 || ldo % 4 != 0 ||
       gram_setup().err != cudaSuccess)
     return false;
   launch_pdl(k_combine_staged<W, NT, NST>, dim3(nblk(n_rows, 2 * NT)), dim3(NT), smem, st, out, in, alpha, V, vstride,
-             kblocks, r_in, C, r_out, n_rows, ldv, ldo);
+             kblocks, r_in, C, r_out, n_rows, ldv, ldo, err);
   return true;
 }
 
 template <typename T, int W>
 static void combine_w(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
-                      const T* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st) {
+                      const T* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st, int* err) {
   if constexpr (sizeof(T) == 4 && W <= 24) {
     float* o = reinterpret_cast<float*>(out);
     const float* i = reinterpret_cast<const float*>(in);
@@ -1356,13 +1357,13 @@ static void combine_w(T* out, const T* in, T alpha, const T* V, size_t vstride, 
     const float a = (float)alpha;
     switch (combine_variant()) {
       case 1: break;
-      case 2: done = combine_staged_try<W, 128, 3>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+      case 2: done = combine_staged_try<W, 128, 3>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st, err);
               break;
-      case 3: done = combine_staged_try<W, 64, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+      case 3: done = combine_staged_try<W, 64, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st, err);
               break;
-      default: done = combine_staged_try<W, 256, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+      default: done = combine_staged_try<W, 256, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st, err);
     }
-    if (!done) done = combine_staged_try<W, 128, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st);
+    if (!done) done = combine_staged_try<W, 128, 2>(o, i, a, v, vstride, kblocks, r_in, cc, r_out, n_rows, ldv, ldo, st, err);
     if (done) return;
   }
   constexpr int RPT = (sizeof(T) == 4 && W <= 24) ? 2 : 1;
@@ -1377,10 +1378,11 @@ cudaError_t init_la_attributes() { return gram_setup().err; }
 
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
-                          int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st) {
+                          int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st,
+                          int* err) {
   count_launch();
   const int w = std::max((r_in + 3) / 4, (r_out + 3) / 4) * 4;
-#define MHDE_CW(WV) combine_w<T, WV>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st)
+#define MHDE_CW(WV) combine_w<T, WV>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st, err)
   if (w <= 4) MHDE_CW(4);
   else if (w <= 8) MHDE_CW(8);
   else if (w <= 12) MHDE_CW(12);
@@ -1539,10 +1541,10 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
                                     const T*, T*, cudaStream_t);                                        \
   template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, int, cudaStream_t); \
   template void launch_gram<T>(const T*, size_t, int, const T*, int, int, int, int, double*, double*, \
-                               cudaStream_t, bool);                                                  \
+                               cudaStream_t, bool, int*);                                            \
   template void launch_make_coef<T>(const double*, const double*, int, int, T*, cudaStream_t);       \
   template void launch_block_combine<T>(T*, const T*, T, const T*, size_t, int, int, const T*, int,  \
-                                        int, int, int, cudaStream_t);                                \
+                                        int, int, int, cudaStream_t, int*);                          \
   template void launch_colsq<T>(const T*, int, int, int, double*, cudaStream_t);                     \
   template void launch_scale_to<T>(const double*, const double*, T*, size_t, int, cudaStream_t);     \
   template void launch_axpy_from<T>(const T*, const double*, double*, size_t, int, cudaStream_t);     \

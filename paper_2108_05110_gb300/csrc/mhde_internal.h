@@ -90,11 +90,6 @@ std::string build_amg(FeHost& fe, int coarse_max);
 // eigenvalues descending in w, eigenvectors in the columns of U (row-major).
 void eig_sym(int n, const double* A, double* w, double* U);
 
-// Eigenvalues of a real upper Hessenberg matrix (row-major n x n, destroyed).
-bool eig_hessenberg(int n, double* a, double* wr, double* wi);
-// Quadratic factors pi(z) = prod (1 - c1 z + c2 z^2) of the GMRES residual
-// polynomial of degree d (even) from a (d+1) x d Arnoldi Hessenberg matrix.
-bool gmres_poly_factors(int d, const double* H, std::vector<double>& c1, std::vector<double>& c2);
 // Cholesky QR factors T = R^{-1}, S = R of a Gram matrix G = R^T R (r x r,
 // row-major), only when full rank is certain (every eigenvalue above
 // 100 thresh lambda_max); false otherwise (callers then use the eigen form).
@@ -167,6 +162,7 @@ struct Sub {                       // one subproblem (v: which = 0, w: which = 1
   void* Rk = nullptr;              // scaled residual of the correction equation
   void* Dk = nullptr;              // correction
   double* dscale = nullptr;        // [2 Jp]: 1/||res_j||, ||res_j||
+  int* d_err = nullptr;            // bounded-wait failure word of this subproblem's staged kernels
   void* hcoef = nullptr;           // pinned host staging of coefficients [(m+1) J J] doubles
   double* part = nullptr;          // gram partial sums [nchunk][m+1][MAX_J*MAX_J]
   double* gram = nullptr;          // reduced gram [m+1][J][J]
@@ -184,8 +180,6 @@ struct Sub {                       // one subproblem (v: which = 0, w: which = 1
   double* ibeta = nullptr;         // [2 Jp] initial norms, then [2 Jp] inverse norms
   double* iy = nullptr;            // inner least-squares solutions [kin][2 Jp]
   void* zbasis = nullptr;          // flexible GMRES: preconditioned basis m x [n_rows][Jp]
-  double* poly = nullptr;          // GMRES-polynomial quadratic factors (c1, c2) [KIN_MAX/2][2]
-  int poly_fallbacks = 0;          // steps whose polynomial setup fell back to damped Jacobi
   // captured preconditioner graphs keyed by (input, output) device pointers
   std::map<std::tuple<const void*, const void*, int>, std::pair<cudaGraphExec_t, long long>> prec_graphs;
   // stats
@@ -262,7 +256,6 @@ struct mhde_ctx {
   double* d_mean_w = nullptr;
   double* d_l2_v = nullptr;            // [nt][7]
   double* d_l2_w = nullptr;
-  void* d_prand = nullptr;             // fixed pseudo-random start block [n2][4] (Krylov precision)
   double* d_ccross = nullptr;          // [Jp] nu_j - nu_m,j
   double* d_csame = nullptr;           // [Jp] nu'_j + nu'_m,j
   int device = 0;

@@ -160,10 +160,6 @@ static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out, int J
   launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), (T)(1.0 / c->dt), (T)nu_hat, Kp.rowptr, Kp.col,
                       c->opt.schur == 1 ? Prec<T>::Np(s) : (const T*)nullptr, out + poff, st);
   launch_bt_apply<T>(c, Prec<T>::BT(c), in, out + poff, tk, Jp, st);
-  if (c->opt.poly_degree > 0) {
-    launch_poly_apply<T>(c, s, Prec<T>::F(s), Prec<T>::Fd(s), tk, out, Jp, st);
-    return;
-  }
   if (c->opt.inner_iters > 0) {
     launch_inner_gmres<T>(c, s, Prec<T>::FD(s), Prec<T>::Fd(s), tk, out, Jp, c->opt.inner_iters, st);
     return;
@@ -250,7 +246,7 @@ static int gram_chunks(const mhde_ctx* c, int k, int r) {
 template <typename T>
 static int gram_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int k, const T* W, int r,
                      std::vector<double>& out, int ld) {
-  launch_gram<T>(V, vstride, k, W, c->n_rows, ld, r, gram_chunks(c, k, r), s.part, s.gram, s.stream);
+  launch_gram<T>(V, vstride, k, W, c->n_rows, ld, r, gram_chunks(c, k, r), s.part, s.gram, s.stream, true, s.d_err);
   SCU(cudaMemcpyAsync(s.hbuf, s.gram, sizeof(double) * k * r * r, cudaMemcpyDeviceToHost, s.stream));
   SCU(cudaStreamSynchronize(s.stream));
   out.assign(s.hbuf, s.hbuf + (size_t)k * r * r);
@@ -262,7 +258,8 @@ static int gram_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int 
 template <typename T>
 static int gram_proj_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int k, const T* W, int r, int ld,
                           std::vector<double>& out) {
-  launch_gram<T>(V, vstride, k + 2, W, c->n_rows, ld, r, gram_chunks(c, k + 2, r), s.part, s.gram, s.stream);
+  launch_gram<T>(V, vstride, k + 2, W, c->n_rows, ld, r, gram_chunks(c, k + 2, r), s.part, s.gram, s.stream, true,
+                 s.d_err);
   launch_proj_gram(s.gram, k, r, s.stream);
   const size_t n = (size_t)(k + 3) * r * r;
   SCU(cudaMemcpyAsync(s.hbuf, s.gram, sizeof(double) * n, cudaMemcpyDeviceToHost, s.stream));
@@ -372,24 +369,24 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
         // coefficients -H_i T and T are formed on the device
         const double* dT = upload_coef<double>(c, s, Tn, 1);
         launch_make_coef<T>(s.gram, dT, k, r, dcoef, st);
-        launch_block_combine<T>(Wn, nullptr, T(0), Vb, vs, k + 2, r, dcoef, r, c->n_rows, Rp, Rp, st);
+        launch_block_combine<T>(Wn, nullptr, T(0), Vb, vs, k + 2, r, dcoef, r, c->n_rows, Rp, Rp, st, s.d_err);
       }
     } else {
       // strong cancellation: explicit two-pass Gram-Schmidt for this block
       H.assign(Hsum.begin(), Hsum.end());
       for (auto& v : H) v = -v;
       T* dc = upload_coef<T>(c, s, H, 0);
-      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st);
+      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err);
       if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wn, r, H, Rp))) return rc;
       for (size_t t2 = 0; t2 < H.size(); ++t2) Hsum[t2] += H[t2];
       for (auto& v : H) v = -v;
       dc = upload_coef<T>(c, s, H, 1);
-      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st);
+      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err);
       if ((rc = gram_host<T>(c, s, Wn, 0, 1, Wn, r, G, Rp))) return rc;
       rk = svqb(r, G, thresh, Tn, Sn);
       if (rk == r) {
         dc = upload_coef<T>(c, s, Tn, 2);
-        launch_block_combine<T>(Wn, nullptr, T(0), Wn, 0, 1, r, dc, r, c->n_rows, Rp, Rp, st);
+        launch_block_combine<T>(Wn, nullptr, T(0), Wn, 0, 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err);
       }
     }
     pc3.stop(4);
@@ -426,40 +423,7 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   }
   ls.solve(Y);
   T* dc = upload_coef<T>(c, s, Y, 3);
-  launch_block_combine<T>(D, nullptr, T(0), Zb, vs, k, r, dc, J, c->n_rows, Rp, Jp, st);
-  return MHDE_OK;
-}
-
-// ------------------------------------------------------------------ polynomial setup
-// d Arnoldi steps of the inner GMRES on a fixed pseudo-random block give a
-// (d+1) x d Hessenberg matrix; its harmonic Ritz values are the roots of the
-// GMRES residual polynomial used as the F-block preconditioner this step.
-template <typename T>
-static int poly_setup(mhde_ctx* c, Sub& s) {
-  const int d = c->opt.poly_degree, C = 4;
-  cudaStream_t st = s.stream;
-  T* zscratch = (T*)s.Pk;                    // output of the setup solve is not used
-  launch_inner_gmres<T>(c, s, Prec<T>::FD(s), Prec<T>::Fd(s), (const T*)c->d_prand, zscratch, 2, d, st, false);
-  std::vector<double> Hall((size_t)(d + 1) * d * C), H((size_t)(d + 1) * d);
-  SCU(cudaMemcpyAsync(Hall.data(), s.ih, Hall.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  SCU(cudaStreamSynchronize(st));
-  for (int l = 0; l <= d; ++l)
-    for (int i = 0; i < d; ++i) H[(size_t)l * d + i] = Hall[((size_t)l * d + i) * C + 0];
-  std::vector<double> c1, c2;
-  if (!gmres_poly_factors(d, H.data(), c1, c2)) {
-    // fall back to squared damped Jacobi factors (1 - w z)^2
-    const double om = c->opt.jacobi_omega;
-    c1.assign(d / 2, 2.0 * om);
-    c2.assign(d / 2, om * om);
-    s.poly_fallbacks++;
-  }
-  std::vector<double> coef(2 * (d / 2));
-  for (int i = 0; i < d / 2; ++i) {
-    coef[2 * i] = c1[i];
-    coef[2 * i + 1] = c2[i];
-  }
-  SCU(cudaMemcpyAsync(s.poly, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  SCU(cudaStreamSynchronize(st));
+  launch_block_combine<T>(D, nullptr, T(0), Zb, vs, k, r, dc, J, c->n_rows, Rp, Jp, st, s.d_err);
   return MHDE_OK;
 }
 
@@ -482,10 +446,6 @@ int assemble_sub(mhde_ctx* c, int which) {
   launch_rhs_assemble(c, s.S, o.S, c->have_forcing ? (which == 0 ? c->d_F1 : c->d_F2) : nullptr,
                       which == 0 ? c->d_Gv : c->d_Gw, s.Cloc, c->d_ccross, c->d_csame, s.Bv, st);
   SCU(cudaGetLastError());
-  if (c->opt.poly_degree > 0) {
-    int rc = c->opt.precision == MHDE_PREC_FP64 ? poly_setup<double>(c, s) : poly_setup<float>(c, s);
-    if (rc) return rc;
-  }
   pa.stop(0);
   return MHDE_OK;
 }
@@ -574,10 +534,10 @@ void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, cons
   const int nchunk = gram_chunks(c, k, c->J);
   if (c->opt.precision == MHDE_PREC_FP64)
     launch_gram<double>((const double*)V, vstride, k, (const double*)W, c->n_rows, c->Jp, c->J, nchunk, s.part,
-                        s.gram, s.stream, reduce);
+                        s.gram, s.stream, reduce, s.d_err);
   else
     launch_gram<float>((const float*)V, vstride, k, (const float*)W, c->n_rows, c->Jp, c->J, nchunk, s.part,
-                       s.gram, s.stream, reduce);
+                       s.gram, s.stream, reduce, s.d_err);
 }
 
 // out = sum_i V_i C_i over k blocks of J columns with the coefficients in
@@ -586,10 +546,10 @@ void combine_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, v
   Sub& s = c->sub[which];
   if (c->opt.precision == MHDE_PREC_FP64)
     launch_block_combine<double>((double*)out, nullptr, 0.0, (const double*)V, vstride, k, c->J,
-                                 (const double*)s.coef, c->J, c->n_rows, c->Jp, c->Jp, s.stream);
+                                 (const double*)s.coef, c->J, c->n_rows, c->Jp, c->Jp, s.stream, s.d_err);
   else
     launch_block_combine<float>((float*)out, nullptr, 0.f, (const float*)V, vstride, k, c->J, (const float*)s.coef,
-                                c->J, c->n_rows, c->Jp, c->Jp, s.stream);
+                                c->J, c->n_rows, c->Jp, c->Jp, s.stream, s.d_err);
 }
 
 int solve_sub(mhde_ctx* c, int which, bool zero_guess) {

@@ -67,7 +67,7 @@ def test_create_rejects_bad_input():
     with pytest.raises(P.MhdeError):
         P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, strict=1, mu=0.4)
     # option fields outside their ranges
-    for bad_opt in (dict(inner_fp16=2), dict(inner_iters=17), dict(poly_degree=3), dict(schur=2)):
+    for bad_opt in (dict(inner_fp16=2), dict(inner_iters=17), dict(schur=2)):
         with pytest.raises(P.MhdeError):
             P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, **bad_opt)
     P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, inner_fp16=1).close()
@@ -102,3 +102,16 @@ def test_channel_mesh_builds_hierarchy():
     s = ensemble_io.solver_for(ens, bind=False)
     assert s.sizes.amg_levels >= 2
     s.close()
+
+
+def test_block_gram_entry_points_reject_more_blocks_than_grid_rows():
+    """Both Gram entry points launch one grid row per basis block, so more
+    than 65535 blocks is an argument error, caught before any device work
+    (the pointers below are never dereferenced)."""
+    import ctypes as C
+    lib = P.load_library()
+    fake = C.c_void_p(256)
+    nbytes = C.c_size_t()
+    assert lib.mhde_block_gram_scratch_bytes(100, 1, 65536, C.byref(nbytes)) == -1
+    assert lib.mhde_block_gram(fake, 400, 65536, fake, 100, 4, 1, fake, fake, 1 << 30, None) == -1
+    assert lib.mhde_block_gram_noalloc(fake, 400, 65536, fake, 100, 4, 1, fake, None) == -1
