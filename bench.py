@@ -51,7 +51,10 @@ def parse():
                    help="with --profile-only: launch only this hot-path kernel group K times "
                         "(mhde_time_kernel ids: 0 SpMM FP64, 1 SpMM FP32, 2 F assembly, 3 RHS, "
                         "4 means+l2, 5 preconditioner, 6 Gram)")
+    p.add_argument("--no-oracle-check", action="store_true",
+                   help="skip the one-step oracle check of the benchmarked state")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--oracle-check", default=None, help=argparse.SUPPRESS)
     p.add_argument("--N", type=int, default=WORKLOAD["N"])
     p.add_argument("--J", type=int, default=WORKLOAD["J"])
     return p.parse_args()
@@ -107,6 +110,86 @@ def cpu_baseline_block(seconds):
             "sample": "one member's v-subproblem of one step on the full mesh (half a member-step): "
                       "FP64 numpy/scipy assembly + SuperLU factorisation and solve, 1 thread; "
                       f"{seconds:.2f} s"}
+
+
+# --------------------------------------------------------------------------- accuracy at the benchmarked state
+def oracle_step_check(path, N, J):
+    """The next step of the FP64 oracle from the state stored in `path`
+    (both Elsaesser fields of all members, library numbering), with one
+    SuperLU factorisation per subproblem shared by all members: rel L2 of the
+    library's step against it, per subproblem, over all members and nodes."""
+    import numpy as np
+    from workloads.ensembles import lid_cavity
+    from oracle.scheme import OracleRun
+    d = np.load(path)
+    ens = lid_cavity(N=N, J=J, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"])
+    run = OracleRun(ens)
+    run.V, run.W, run.n = d["v0"].copy(), d["w0"].copy(), int(d["n"])
+    t0 = time.perf_counter()
+    run.step()
+    secs = time.perf_counter() - t0
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"rel_l2_v": rel(d["v1"], run.V), "rel_l2_w": rel(d["w1"], run.W), "step": int(d["n"]) + 1,
+            "members": J, "oracle_seconds": secs}
+
+
+def oracle_check(args, sol):
+    """One more library step from the benchmarked state, compared with the
+    same step of the FP64 oracle run in a fresh single-threaded process."""
+    import tempfile
+    import numpy as np
+    v0, w0, _, _ = sol.read_state()
+    n = int(sol.stats().steps)
+    sol.step()
+    v1, w1, _, _ = sol.read_state()
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    try:
+        np.savez(path, v0=v0, w0=w0, v1=v1, w1=w1, n=n)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-check", path, "--N",
+                              str(args.N), "--J", str(args.J)], capture_output=True, text=True, env=env,
+                             timeout=1800)
+    finally:
+        os.remove(path)
+    line = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    if out.returncode != 0 or not line:
+        return {"error": out.stderr[-500:]}
+    res = json.loads(line[-1])
+    res["gate"] = 1e-8 if sol.options.precision == 1 else 1e-10
+    res["what"] = ("rel L2 of the step after the timed ones (all members, all nodes) against the FP64 "
+                   "oracle stepped from the same state")
+    return res
+
+
+def fp64_same_steps(args, ens, state0, device):
+    """The plain FP64 GPU path (FP64 Krylov, SpMM and preconditioner) over the
+    first steps of the timed region, from the same post-warm-up state."""
+    import torch
+    from paper_2108_05110_gb300 import ensemble_io, PREC_FP64
+    sol = ensemble_io.solver_for(ens, precision=PREC_FP64, device=device)
+    ensemble_io.feed_initial(sol, ens)
+    ensemble_io.feed_step_data(sol, ens, ens.dt)
+    sol.load_state(state0)
+    k = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(sol.stream_v)
+    st0 = sol.stats()
+    sol.advance(k)
+    ev1.record(sol.stream_v)
+    torch.cuda.synchronize()
+    st1 = sol.stats()
+    ms = ev0.elapsed_time(ev1)
+    out = {"value": ens.J * k / (ms / 1000.0), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+           "rtol": sol.options.rtol, "final_relres": max(float(st1.last_relres[0]), float(st1.last_relres[1])),
+           "krylov_iters_per_step": (st1.total_iters - st0.total_iters) / k,
+           "what": "FP64 Krylov, SpMM and preconditioner (the plain FP64 GPU form), same post-warm-up state "
+                   "and first steps of the timed region"}
+    sol.close()
+    return out
 
 
 # --------------------------------------------------------------------------- clocks
@@ -369,6 +452,9 @@ def our_arm(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
+    # post-warm-up state: the end-to-end leg below re-runs exactly the steps
+    # that the device-timed region runs
+    state0 = sol.save_state()
     clocks = ClockSampler(local_rank)
     st0 = sol.stats()
     clocks.start()
@@ -390,6 +476,8 @@ def our_arm(args, rank, world, local_rank):
     value = whole_job_rate(ens.J * args.steps, world, ms_max / 1000.0)
     launches = int(st1.launches - st0.launches)
     iters = int(st1.total_iters - st0.total_iters)
+    relres = max(float(st1.last_relres[0]), float(st1.last_relres[1]))
+    v_dev, w_dev, _, _ = sol.read_state()
 
     # dominant kernel (largest share of the step's device time in the ncu
     # launch list): the partial sums of the block Gram, timed alone on
@@ -425,26 +513,42 @@ def our_arm(args, rank, world, local_rank):
                  (("means_l2", 4), ("assemble_F", 2), ("rhs", 3), ("precond", 5), ("gram", 6),
                   ("combine", 7))}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers, over the same
+    # steps: restore the post-warm-up state, then per step copy that step's
+    # Dirichlet data in, step, and read the ensemble means out
     xy = sol._nodes
-    u0, B0 = ens.u0(xy), ens.B0(xy)
     ub, Bb = ens.u_bc(xy, ens.dt), ens.B_bc(xy, ens.dt)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    sol.set_initial(u0, B0)
-    sol.set_dirichlet(ub, Bb)
+    sol.load_state(state0)
     for _ in range(args.steps):
+        sol.set_dirichlet(ub, Bb)
         sol.step()
         um, Bm = sol.read_mean()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = whole_job_rate(ens.J * args.steps, world,
                                max_over_ranks(e2e_s, world, device=f"cuda:{local_rank}"))
-    h2d = (u0.nbytes + B0.nbytes + ub.nbytes + Bb.nbytes) / args.steps
+    v_e2e, w_e2e, _, _ = sol.read_state()
+    same_steps = bool(np.array_equal(v_e2e, v_dev) and np.array_equal(w_e2e, w_dev))
+    sz = sol.sizes
+    # bytes that cross per step: the restored state once, then per step the
+    # packed Dirichlet values of both subproblems in, both means out
+    dirichlet_bytes = 2 * sz.n_boundary * 2 * sz.J_pad * 8
+    h2d = (state0.nbytes + args.steps * dirichlet_bytes) / args.steps
     d2h = um.nbytes + Bm.nbytes
-    sol.close()
+
+    accuracy = None
+    fp64_line = None
     separate = None
+    if rank == 0 and world == 1 and not args.no_separate:
+        # one more step from the benchmarked state, checked against the oracle
+        if not args.no_oracle_check:
+            accuracy = oracle_check(args, sol)
+        if prec == PREC_MIXED:
+            fp64_line = fp64_same_steps(args, ens, state0, f"cuda:{local_rank}")
+    sol.close()
     if rank == 0 and world == 1 and not args.no_separate:
         separate = separate_solve_baseline(args, prec, f"cuda:{local_rank}")
 
@@ -456,9 +560,14 @@ def our_arm(args, rank, world, local_rank):
                 "config": config(args, {"precision": args.precision}),
                 "roofline": roofline, "clocks": clock_info, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                        "d2h_bytes_per_step": int(d2h)},
-                "krylov_iters_per_step": iters / args.steps, "kernel_ms": kernel_ms, "spmm": spmm_line,
+                        "d2h_bytes_per_step": int(d2h), "same_steps_as_value": same_steps},
+                "final_relres": relres, "krylov_iters_per_step": iters / args.steps,
+                "kernel_ms": kernel_ms, "spmm": spmm_line,
                 "wall_ms_per_step": 1000.0 * wall / args.steps}
+        if accuracy is not None:
+            line["accuracy"] = accuracy
+        if fp64_line is not None:
+            line["fp64_path"] = fp64_line
         if cpu_secs is not None:
             line["cpu_baseline"] = cpu_baseline_block(cpu_secs)
         if separate is not None:
@@ -471,6 +580,9 @@ def main():
     args = parse()
     if args.cpu_sample:
         print(json.dumps({"seconds": cpu_sample(args.N, args.J)}), flush=True)
+        return
+    if args.oracle_check:
+        print(json.dumps(oracle_step_check(args.oracle_check, args.N, args.J)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
