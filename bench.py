@@ -28,6 +28,18 @@ sys.path.insert(0, ROOT)
 METRIC = "ensemble member-steps/s at rel L2 <=1e-8 vs FP64 oracle"
 UNIT = "member-steps/s"
 WORKLOAD = dict(N=128, J=20, s=1.0, dt=0.01, Re=15000.0)
+CHANNEL = dict(J=50, s=0.01, dt=0.05, nu=1.0 / 600)
+
+
+def make_ensemble(workload, N, J, seed=None):
+    """The benchmark's synthetic ensembles: the lid-driven-cavity-shaped one
+    (the metric's workload) or the channel-past-a-step-shaped one."""
+    from workloads.ensembles import lid_cavity, channel
+    if workload == "channel":
+        return channel(J=J, dt=CHANNEL["dt"], s=CHANNEL["s"], nu=CHANNEL["nu"], nu_m=CHANNEL["nu"],
+                       seed=3 if seed is None else seed)
+    return lid_cavity(N=N, J=J, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"],
+                      seed=2 if seed is None else seed)
 
 
 def parse():
@@ -39,8 +51,9 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-separate", action="store_true", help="skip the separate-solve comparator")
-    p.add_argument("--workload", default="cavity", choices=["cavity", "batched"],
-                   help="cavity: the metric's workload; batched: uneven independent ensembles")
+    p.add_argument("--workload", default="cavity", choices=["cavity", "channel", "batched"],
+                   help="cavity: the metric's workload; channel: the channel-past-a-step ensemble; "
+                        "batched: uneven independent ensembles")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--batch-threads", type=int, default=4, help="host threads of mhde_advance_many")
     p.add_argument("--batch-mem-gb", type=float, default=240.0,
@@ -56,31 +69,39 @@ def parse():
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--oracle-check", default=None, help=argparse.SUPPRESS)
     p.add_argument("--N", type=int, default=WORKLOAD["N"])
-    p.add_argument("--J", type=int, default=WORKLOAD["J"])
-    return p.parse_args()
+    p.add_argument("--J", type=int, default=None, help="members (default 20 cavity, 50 channel)")
+    a = p.parse_args()
+    if a.J is None:
+        a.J = CHANNEL["J"] if a.workload == "channel" else WORKLOAD["J"]
+    return a
 
 
 def config(args, extra=None):
-    c = {"workload": f"lid-driven-cavity-shaped ensemble, unit square {args.N}x{args.N} "
-                     f"right-diagonal, Taylor-Hood P2-P1, J={args.J}, Re=15000, s=1, dt=0.01",
-         "mesh": f"{args.N}x{args.N}", "J": args.J, "s": WORKLOAD["s"], "dt": WORKLOAD["dt"],
-         "element": "P2-P1", "l2": "per-step working set (Krylov basis 31 blocks + states) > 129 MB L2",
-         "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+    if args.workload == "channel":
+        c = {"workload": f"channel-past-a-step-shaped ensemble, [0,40]x[0,10] minus [5,6]x[0,1], 280x70 "
+                         f"graded jittered cells, Taylor-Hood P2-P1 (157,838 velocity DOFs), J={args.J}, "
+                         f"nu=nu_m=1/600, s=0.01, dt=0.05, inflow scaled by 1+eps_j",
+             "mesh": "channel 280x70 cells minus step", "J": args.J, "s": CHANNEL["s"], "dt": CHANNEL["dt"]}
+    else:
+        c = {"workload": f"lid-driven-cavity-shaped ensemble, unit square {args.N}x{args.N} "
+                         f"right-diagonal, Taylor-Hood P2-P1, J={args.J}, Re=15000, s=1, dt=0.01",
+             "mesh": f"{args.N}x{args.N}", "J": args.J, "s": WORKLOAD["s"], "dt": WORKLOAD["dt"]}
+    c.update({"element": "P2-P1", "l2": "per-step working set (Krylov basis 31 blocks + states) > 129 MB L2",
+              "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"})
     if extra:
         c.update(extra)
     return c
 
 
 # --------------------------------------------------------------------------- CPU oracle sample
-def cpu_sample(N, J_total):
+def cpu_sample(workload, N, J_total):
     """One v-subproblem of one member of the workload's first step on the full
     mesh through the FP64 oracle (assembly + SuperLU factorisation + solve),
     run in a fresh single-threaded process.  Returns seconds."""
     import numpy as np
-    from workloads.ensembles import lid_cavity
     from oracle.scheme import OracleRun, ensemble_mean, mixing_length_sq
     from scipy.sparse.linalg import splu
-    ens = lid_cavity(N=N, J=J_total, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"])
+    ens = make_ensemble(workload, N, J_total)
     run = OracleRun(ens, lu_per_member=True)
     t0 = time.perf_counter()
     mv, mw = ensemble_mean(run.V), ensemble_mean(run.W)
@@ -97,8 +118,9 @@ def cpu_sample(N, J_total):
 def run_cpu_sample_subprocess(args):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--N", str(args.N),
-                          "--J", str(args.J)], capture_output=True, text=True, env=env, timeout=900)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", args.workload,
+                          "--N", str(args.N), "--J", str(args.J)], capture_output=True, text=True, env=env,
+                         timeout=900)
     line = [l for l in out.stdout.splitlines() if l.startswith("{")]
     if out.returncode != 0 or not line:
         raise RuntimeError("cpu sample failed: " + out.stderr[-2000:])
@@ -113,16 +135,15 @@ def cpu_baseline_block(seconds):
 
 
 # --------------------------------------------------------------------------- accuracy at the benchmarked state
-def oracle_step_check(path, N, J):
+def oracle_step_check(path, workload, N, J):
     """The next step of the FP64 oracle from the state stored in `path`
     (both Elsaesser fields of all members, library numbering), with one
     SuperLU factorisation per subproblem shared by all members: rel L2 of the
     library's step against it, per subproblem, over all members and nodes."""
     import numpy as np
-    from workloads.ensembles import lid_cavity
     from oracle.scheme import OracleRun
     d = np.load(path)
-    ens = lid_cavity(N=N, J=J, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"])
+    ens = make_ensemble(workload, N, J)
     run = OracleRun(ens)
     run.V, run.W, run.n = d["v0"].copy(), d["w0"].copy(), int(d["n"])
     t0 = time.perf_counter()
@@ -148,9 +169,9 @@ def oracle_check(args, sol):
         np.savez(path, v0=v0, w0=w0, v1=v1, w1=w1, n=n)
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                    CUDA_VISIBLE_DEVICES="")
-        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-check", path, "--N",
-                              str(args.N), "--J", str(args.J)], capture_output=True, text=True, env=env,
-                             timeout=1800)
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-check", path, "--workload",
+                              args.workload, "--N", str(args.N), "--J", str(args.J)], capture_output=True,
+                             text=True, env=env, timeout=1800)
     finally:
         os.remove(path)
     line = [l for l in out.stdout.splitlines() if l.startswith("{")]
@@ -417,16 +438,13 @@ def our_arm(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     from paper_2108_05110_gb300 import ensemble_io, PREC_FP64, PREC_MIXED
-    from workloads.ensembles import lid_cavity
-
     cpu_secs = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_only:
         cpu_secs = run_cpu_sample_subprocess(args)      # before any GPU work in this process
 
     torch.cuda.set_device(local_rank)
     prec = PREC_MIXED if args.precision == "mixed" else PREC_FP64
-    ens = lid_cavity(N=args.N, J=args.J, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"],
-                     seed=2 + rank)
+    ens = make_ensemble(args.workload, args.N, args.J, seed=(3 if args.workload == "channel" else 2) + rank)
     sol = ensemble_io.solver_for(ens, precision=prec, device=f"cuda:{local_rank}")
     ensemble_io.feed_initial(sol, ens)
     ensemble_io.feed_step_data(sol, ens, ens.dt)     # constant lid / field data
@@ -494,7 +512,8 @@ def our_arm(args, rank, world, local_rank):
     achieved = alg / (gram_ms / 1000.0) / 1e9
     # DRAM bytes of one launch of this kernel at this size, from an ncu capture of
     # the same launch configuration; known only for the default workload
-    traffic = GRAM_TRAFFIC if (prec == PREC_MIXED and args.N == WORKLOAD["N"] and args.J == WORKLOAD["J"]
+    traffic = GRAM_TRAFFIC if (prec == PREC_MIXED and args.workload == "cavity" and args.N == WORKLOAD["N"]
+                               and args.J == WORKLOAD["J"]
                                and sol.options.restart == 30) else None
     kname = "k_gram_staged, FP32" if pbytes == 4 else "k_gram, FP64"
     roofline = {"bound": "hbm", "kernel": f"block Gram partial sums ({kname}), "
@@ -549,7 +568,7 @@ def our_arm(args, rank, world, local_rank):
         if prec == PREC_MIXED:
             fp64_line = fp64_same_steps(args, ens, state0, f"cuda:{local_rank}")
     sol.close()
-    if rank == 0 and world == 1 and not args.no_separate:
+    if rank == 0 and world == 1 and not args.no_separate and args.workload == "cavity":
         separate = separate_solve_baseline(args, prec, f"cuda:{local_rank}")
 
     if rank == 0:
@@ -562,6 +581,10 @@ def our_arm(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "same_steps_as_value": same_steps},
                 "final_relres": relres, "krylov_iters_per_step": iters / args.steps,
+                "block_ops_autotune": {"gram": "tensor cores" if st1.gram_tensor_cores else "cuda cores",
+                                       "gram_us_cuda_tensor": list(st1.gram_tuned_us),
+                                       "combine": "tensor cores" if st1.combine_tensor_cores else "cuda cores",
+                                       "combine_us_cuda_tensor": list(st1.combine_tuned_us)},
                 "kernel_ms": kernel_ms, "spmm": spmm_line,
                 "wall_ms_per_step": 1000.0 * wall / args.steps}
         if accuracy is not None:
@@ -579,10 +602,10 @@ def main():
     faulthandler.enable()
     args = parse()
     if args.cpu_sample:
-        print(json.dumps({"seconds": cpu_sample(args.N, args.J)}), flush=True)
+        print(json.dumps({"seconds": cpu_sample(args.workload, args.N, args.J)}), flush=True)
         return
     if args.oracle_check:
-        print(json.dumps(oracle_step_check(args.oracle_check, args.N, args.J)), flush=True)
+        print(json.dumps(oracle_step_check(args.oracle_check, args.workload, args.N, args.J)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

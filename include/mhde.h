@@ -120,6 +120,13 @@ typedef struct {
                                  saddle SpMM (128, 256 or 512; results do not
                                  depend on it) */
   double spmm_tuned_us[3];    /* its timings of one SpMM at 128, 256, 512 */
+  int gram_tensor_cores;      /* 1 if the bind-time autotuner picked the tensor-core (tcgen05)
+                                 kernel for the FP32 block Gram of the mixed path, 0 the
+                                 CUDA-core kernel (results agree to FP32 rounding) */
+  int combine_tensor_cores;   /* the same choice for the FP32 block combination */
+  double gram_tuned_us[2];    /* its timings of one Gram of restart/2 + 1 blocks: CUDA cores,
+                                 tensor cores (0 where not timed) */
+  double combine_tuned_us[2]; /* the same for one combination of restart/2 blocks */
 } mhde_stats;
 
 /* Default options (listed above). */
@@ -301,6 +308,36 @@ int mhde_block_gram_scratch_bytes(int n_rows, int r, int kblocks, size_t* bytes)
 int mhde_block_gram(const double* V, size_t v_stride, int kblocks, const double* W, int n_rows, int ld,
                     int r, double* G, void* scratch, size_t scratch_bytes, void* stream);
 
+/* FP32 block Gram, the Krylov precision of the mixed path: the same G (in
+ * FP64) from FP32 V_i and W, same layout and limits as mhde_block_gram.
+ * use_tensor_cores = 1 runs the tensor-core kernel (tcgen05, TF32 on split
+ * operands: x = hi + lo with hi exact in TF32, products hi*hi + hi*lo + lo*hi
+ * accumulated in FP32, relative error about 2^-21 per product; needs r <= 64,
+ * ld <= 64, 16-byte aligned V and W and v_stride a multiple of 4, else
+ * MHDE_EINVAL); 0 runs the CUDA-core kernels.  scratch: device, at least
+ * mhde_block_gram_f32_scratch_bytes() bytes, owned by the caller.  The call
+ * synchronizes `stream` and returns MHDE_ECUDA if a kernel's bounded wait for
+ * its shared-memory stages gave up (G is then not valid). */
+int mhde_block_gram_f32_scratch_bytes(int n_rows, int r, int kblocks, size_t* bytes);
+int mhde_block_gram_f32(const float* V, size_t v_stride, int kblocks, const float* W, int n_rows, int ld, int r,
+                        double* G, void* scratch, size_t scratch_bytes, int use_tensor_cores, void* stream);
+
+/* Block combination of the block Krylov solve in FP32 (the new basis block
+ * and the solution update, Section 1 block solvers):
+ *   out[row][q] = alpha in[row][q] + sum_{i < kblocks} sum_{p < r_in} V_i[row][p] C_i[p][q]
+ * for q < r_out, and 0 for r_out <= q < ldo.  V_i = V + i * v_stride
+ * (elements), rows of stride ldv; in (may be NULL: alpha ignored) and out
+ * rows of stride ldo; C: device [kblocks][r_in][r_out].  out may alias in or
+ * one of the V_i (every row is read before it is written).  use_tensor_cores
+ * = 1 runs the tensor-core kernel (tcgen05, TF32 on split operands as in
+ * mhde_block_gram_f32; r_out <= 64 and the shared-memory plan must fit,
+ * 16-byte aligned out, in and V, else MHDE_EINVAL); 0 the CUDA-core kernel.
+ * scratch: device, >= 256 bytes (error word).  The call synchronizes
+ * `stream`; MHDE_ECUDA if a bounded wait gave up. */
+int mhde_block_combine_f32(float* out, const float* in, float alpha, const float* V, size_t v_stride, int kblocks,
+                           int r_in, const float* C, int r_out, int n_rows, int ldv, int ldo, void* scratch,
+                           size_t scratch_bytes, int use_tensor_cores, void* stream);
+
 /* Allocation-free variant of mhde_block_gram, for callers that must not
  * allocate device memory (hosts that own the whole device through their own
  * pool, latency-critical loops that cannot afford cudaMalloc).  The paper has
@@ -321,6 +358,13 @@ int mhde_block_gram(const double* V, size_t v_stride, int kblocks, const double*
  * cudaMalloc, cudaFree or allocating library routine. */
 int mhde_block_gram_noalloc(const double* V, size_t v_stride, int kblocks, const double* W, int n_rows,
                             int ld, int r, double* G, void* stream);
+
+/* Measured rate of independent FP64 fused multiply-adds on the current
+ * device in TFLOP/s (dependent chains, 8 per thread, 8 CTAs of 256 threads
+ * per SM, CUDA events on `stream`): the roofline denominator of the
+ * library's FP64 kernels.  The paper has no counterpart; this measures the
+ * hardware the library runs on.  Synchronizes `stream`. */
+int mhde_fp64_fma_rate(void* stream, double* tflops);
 
 #ifdef __cplusplus
 }

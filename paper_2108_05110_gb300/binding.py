@@ -52,7 +52,9 @@ class Stats(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("last_iters", C.c_int * 2), ("last_refine", C.c_int * 2),
                 ("last_relres", C.c_double * 2), ("total_iters", C.c_longlong),
                 ("last_step_ms", C.c_double), ("launches", C.c_longlong),
-                ("spmm_block", C.c_int), ("spmm_tuned_us", C.c_double * 3)]
+                ("spmm_block", C.c_int), ("spmm_tuned_us", C.c_double * 3),
+                ("gram_tensor_cores", C.c_int), ("combine_tensor_cores", C.c_int),
+                ("gram_tuned_us", C.c_double * 2), ("combine_tuned_us", C.c_double * 2)]
 
 
 def library_path():
@@ -99,6 +101,12 @@ SIGNATURES = {
     "mhde_block_gram": (C.c_int, [_P, C.c_size_t, C.c_int, _P, C.c_int, C.c_int, C.c_int, _P, _P,
                                   C.c_size_t, _P]),
     "mhde_block_gram_noalloc": (C.c_int, [_P, C.c_size_t, C.c_int, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "mhde_block_gram_f32_scratch_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "mhde_block_gram_f32": (C.c_int, [_P, C.c_size_t, C.c_int, _P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_size_t,
+                                      C.c_int, _P]),
+    "mhde_fp64_fma_rate": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "mhde_block_combine_f32": (C.c_int, [_P, _P, C.c_float, _P, C.c_size_t, C.c_int, C.c_int, _P, C.c_int, C.c_int,
+                                         C.c_int, C.c_int, _P, C.c_size_t, C.c_int, _P]),
 }
 
 
@@ -193,6 +201,65 @@ def block_gram(V, W, kblocks, r, stream=None):
     if rc != 0:
         raise MhdeError(rc, "mhde_block_gram")
     return G
+
+
+def block_gram_f32(V, W, kblocks, r, tensor_cores=True, stream=None):
+    """G_i = V_i^T W (FP64 result) from FP32 blocks through mhde_block_gram_f32:
+    V torch float32 CUDA tensor [kblocks, n_rows, ld], W [n_rows, ld]; the
+    tensor-core kernel or the CUDA-core kernels.  Scratch comes from torch."""
+    import torch
+    lib = load_library()
+    k, n_rows, ld = V.shape
+    nbytes = C.c_size_t()
+    rc = lib.mhde_block_gram_f32_scratch_bytes(n_rows, r, kblocks, C.byref(nbytes))
+    if rc != 0:
+        raise MhdeError(rc, "mhde_block_gram_f32_scratch_bytes")
+    scratch = torch.empty(int(nbytes.value), dtype=torch.uint8, device=V.device)
+    G = torch.empty((kblocks, r, r), dtype=torch.float64, device=V.device)
+    st = stream if stream is not None else torch.cuda.current_stream(V.device)
+    rc = lib.mhde_block_gram_f32(C.c_void_p(V.data_ptr()), n_rows * ld, kblocks, C.c_void_p(W.data_ptr()), n_rows,
+                                 ld, r, C.c_void_p(G.data_ptr()), C.c_void_p(scratch.data_ptr()), nbytes.value,
+                                 1 if tensor_cores else 0, C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise MhdeError(rc, "mhde_block_gram_f32")
+    return G
+
+
+def block_combine_f32(out, V, coef, r_in, r_out, in_=None, alpha=0.0, v_stride=None, tensor_cores=True,
+                      stream=None):
+    """out = alpha in + sum_i V_i coef_i through mhde_block_combine_f32.  V:
+    torch float32 CUDA tensor whose leading dimension holds the blocks ([k,
+    n_rows, ldv]; or give v_stride in elements); coef: float32 [k, r_in,
+    r_out]; out / in_: float32 [n_rows, ldo] (may alias each other or a
+    block of V)."""
+    import torch
+    lib = load_library()
+    k = coef.shape[0]
+    n_rows, ldo = out.shape
+    ldv = V.shape[-1]
+    if v_stride is None:
+        v_stride = V.shape[1] * ldv
+    scratch = torch.empty(256, dtype=torch.uint8, device=out.device)
+    st = stream if stream is not None else torch.cuda.current_stream(out.device)
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    rc = lib.mhde_block_combine_f32(ptr(out), ptr(in_), float(alpha), ptr(V), int(v_stride), int(k), int(r_in),
+                                    ptr(coef), int(r_out), int(n_rows), int(ldv), int(ldo), ptr(scratch), 256,
+                                    1 if tensor_cores else 0, C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise MhdeError(rc, "mhde_block_combine_f32")
+    return out
+
+
+def fp64_fma_rate(stream=None):
+    """Measured FP64 FMA rate of the current device (TFLOP/s), mhde_fp64_fma_rate."""
+    import torch
+    lib = load_library()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    rc = lib.mhde_fp64_fma_rate(C.c_void_p(st.cuda_stream), C.byref(out))
+    if rc != 0:
+        raise MhdeError(rc, "mhde_fp64_fma_rate")
+    return out.value
 
 
 def block_gram_noalloc(V, W, kblocks, r, G=None, stream=None):

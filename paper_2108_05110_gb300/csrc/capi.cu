@@ -214,6 +214,63 @@ void to_rows(const mhde_ctx* c, const double* a, const double* b, double sgn, do
 // order whatever the CTA size, so the choice never changes a result bit (a
 // resumed run stays bit-identical to an uninterrupted one).  F's values are
 // still zero at bind time; the access pattern and traffic are the real ones.
+// FP32 block Gram and block combination of the mixed path: time the
+// CUDA-core and the tensor-core kernels on this context's sizes (restart/2
+// basis blocks of the zeroed workspace; values do not change the timing) and
+// keep the faster; MHDE_GRAM_TC / MHDE_COMB_TC = 0 or 1 force the choice.
+// Both give the same results up to FP32 rounding.
+static int autotune_blockops(mhde_ctx* c) {
+  c->gram_tc = c->comb_tc = false;
+  if (c->opt.precision != MHDE_PREC_MIXED) return MHDE_OK;
+  Sub& s = c->sub[0];
+  cudaStream_t st = c->sv;
+  const size_t vs = (size_t)c->n_rows * c->Jp;
+  const int kb = std::max(1, c->opt.restart / 2);
+  const float* Vb = (const float*)s.basis;
+  float* Wn = (float*)s.basis + (size_t)kb * vs;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(c, MHDE_ECUDA, "cudaEventCreate failed in the block-operation autotuner");
+  }
+  const long long launches0 = launch_count();
+  auto time = [&](auto&& once) -> double {
+    once();
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 5; ++r) once();
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
+    return 1000.0 * ms / 5;
+  };
+  const int nchunk = std::max(1, std::min(1216, (c->n_rows + 63) / 64));
+  const size_t cap = (size_t)c->nchunk * (c->opt.restart + 1) * c->J * c->J;
+  const int gchunks = (int)std::max<size_t>(1, std::min<size_t>(cap / ((size_t)(kb + 1) * c->J * c->J), nchunk));
+  for (int tc = 0; tc < 2; ++tc) {
+    c->gram_tuned_us[tc] = time([&] {
+      launch_gram<float>(Vb, vs, kb + 1, Wn, c->n_rows, c->Jp, c->J, gchunks, s.part, s.gram, st, false, s.d_err,
+                         tc == 1);
+    });
+    CU(cudaMemsetAsync(s.coef, 0, (size_t)kb * c->J * c->J * sizeof(float), st));
+    c->comb_tuned_us[tc] = time([&] {
+      launch_block_combine<float>((float*)s.Zk, nullptr, 0.f, Vb, vs, kb, c->J, (const float*)s.coef, c->J, c->n_rows,
+                                  c->Jp, c->Jp, st, s.d_err, tc == 1);
+    });
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  count_launch(launch_count() - launches0 > 0 ? -(launch_count() - launches0) : 0);   // not part of any step
+  if (take_async_error(s.d_err, st) != 0 || cudaGetLastError() != cudaSuccess)
+    return fail(c, MHDE_ECUDA, "block-operation autotuner: a kernel failed");
+  auto pick = [](const double us[2], const char* env) {
+    if (const char* e = std::getenv(env)) return e[0] == '1';
+    return us[1] > 0.0 && (us[0] <= 0.0 || us[1] < us[0]);
+  };
+  c->gram_tc = pick(c->gram_tuned_us, "MHDE_GRAM_TC");
+  c->comb_tc = pick(c->comb_tuned_us, "MHDE_COMB_TC");
+  return MHDE_OK;
+}
+
 int autotune_spmm(mhde_ctx* c) {
   Sub& s = c->sub[0];
   cudaStream_t st = c->sv;
@@ -505,6 +562,10 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   c->bound = true;
   if (!c->spmm_forced) {
     int rc = autotune_spmm(c);
+    if (rc) return rc;
+  }
+  {
+    int rc = autotune_blockops(c);
     if (rc) return rc;
   }
   return MHDE_OK;
@@ -854,6 +915,12 @@ int mhde_get_stats(const mhde_ctx* c, mhde_stats* st) {
   *st = c->stats;
   st->spmm_block = c->spmm_block;
   for (int i = 0; i < 3; ++i) st->spmm_tuned_us[i] = c->spmm_tuned_us[i];
+  st->gram_tensor_cores = c->gram_tc ? 1 : 0;
+  st->combine_tensor_cores = c->comb_tc ? 1 : 0;
+  for (int i = 0; i < 2; ++i) {
+    st->gram_tuned_us[i] = c->gram_tuned_us[i];
+    st->combine_tuned_us[i] = c->comb_tuned_us[i];
+  }
   return MHDE_OK;
 }
 

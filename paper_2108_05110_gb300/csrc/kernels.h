@@ -105,10 +105,36 @@ void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp
 // err: the calling subproblem's device error word; with it the FP32 Gram may
 // take the TMA-staged kernel, which sets *err = 1 when a stage never lands
 // (nullptr: the unstaged kernels only)
+// allow_tc: the FP32 Gram may run on the tensor cores (tcgen05, split TF32)
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
                  int nchunk, double* part, double* gram, cudaStream_t st, bool reduce = true,
-                 int* err = nullptr);
+                 int* err = nullptr, bool allow_tc = false);
+// partial sums of the FP32 block Gram on the tensor cores (kernels_tc.cu):
+// one partial per CTA (at most max_parts) in part[nparts][kblocks][r][r].
+// false (nothing launched) when the sizes or the device do not fit the
+// kernel; err as for launch_gram (required)
+struct TcGramPlan {
+  int nch = 0, N = 0, mtiles = 0, TR = 0, kgroup = 0, ngroups = 0, nst = 0, nl = 0;
+  unsigned ncols = 0, stage_bytes = 0, off_lay = 0, lay_bytes = 0;
+  size_t smem = 0;
+};
+bool gram_tc_plan(int kblocks, int ld, int r, TcGramPlan& plan);
+bool tc_gram_available();
+bool launch_gram_tc(const float* V, size_t vstride, int kblocks, const float* W, int n_rows, int ld, int r,
+                    int max_parts, double* part, cudaStream_t st, int* err, int& nparts);
+void launch_gram_reduce(int nparts, int total, const double* part, double* gram, cudaStream_t st);
+// block combination of launch_block_combine on the tensor cores (kernels_tc.cu,
+// FP32 only): false (nothing launched) when the sizes, alignment or device do
+// not fit
+struct TcCombinePlan {
+  int N = 0, KC = 0, MT = 0, rows_per_cta = 0, nctas = 0, nst = 0, nl = 0;
+  unsigned ncols = 0, stage_bytes = 0, a_bytes = 0, b_bytes = 0, off_a = 0, off_b = 0;
+  size_t smem = 0;
+};
+bool combine_tc_plan(int n_rows, int ldv, int r_in, int r_out, int nsm, TcCombinePlan& plan);
+bool launch_combine_tc(float* out, const float* in, float alpha, const float* V, size_t vstride, int kblocks,
+                       int r_in, const float* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st, int* err);
 // G = [H_0 .. H_k, W^T W] (r x r blocks) -> block k+2 := W^T W - sum_i H_i^T H_i
 void launch_proj_gram(double* G, int k, int r, cudaStream_t st);
 // 1 if a staged Gram or combine launch of the subproblem owning d_err gave
@@ -119,11 +145,12 @@ int take_async_error(int* d_err, cudaStream_t st);
 template <typename T>
 void launch_make_coef(const double* G, const double* Tm, int k, int r, T* C, cudaStream_t st);
 // out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q], q < r_out; 0 beyond
-// (V rows have stride ldv, in/out rows stride Jp); err as for launch_gram
+// (V rows have stride ldv, in/out rows stride Jp); err as for launch_gram;
+// allow_tc: the FP32 combination may run on the tensor cores
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
                           int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st,
-                          int* err = nullptr);
+                          int* err = nullptr, bool allow_tc = false);
 // out[row][q] = (T) sum_p X[row][p] C[p][q], q < r (0 beyond); X, C (J x r) in FP64;
 // X rows have stride Jp, out rows stride ldo
 template <typename T>

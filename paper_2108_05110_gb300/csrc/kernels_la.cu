@@ -926,8 +926,16 @@ static size_t gram_smem(int Jp, int r) {
 // scratch the caller provides), then one reduction.
 template <typename T>
 void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows, int Jp, int r,
-                 int nchunk, double* part, double* gram, cudaStream_t st, bool reduce, int* err) {
+                 int nchunk, double* part, double* gram, cudaStream_t st, bool reduce, int* err, bool allow_tc) {
   count_launch(reduce ? 2 : 1);
+  if (sizeof(T) == 4 && allow_tc && err != nullptr) {
+    int np = 0;
+    if (launch_gram_tc(reinterpret_cast<const float*>(V), vstride, kblocks, reinterpret_cast<const float*>(W),
+                       n_rows, Jp, r, nchunk, part, st, err, np)) {
+      if (reduce) launch_gram_reduce(np, kblocks * r * r, part, gram, st);
+      return;
+    }
+  }
   const GramDevice& gd = gram_setup();               // on failure the unstaged kernels run instead
   const int w = (r + 3) / 4 * 4;
   int nparts = nchunk;
@@ -992,7 +1000,10 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
     }
   }
   if (!reduce) return;                               // partial sums only (kernel timing)
-  const int total = kblocks * r * r;
+  launch_gram_reduce(nparts, kblocks * r * r, part, gram, st);
+}
+
+void launch_gram_reduce(int nparts, int total, const double* part, double* gram, cudaStream_t st) {
   launch_pdl(k_gram_reduce, dim3((total + 31) / 32), dim3(32 * GR_WARPS), 0, st, nparts, total, part, gram);
 }
 
@@ -1347,7 +1358,14 @@ static bool combine_staged_try(float* out, const float* in, float alpha, const f
 
 template <typename T, int W>
 static void combine_w(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks, int r_in,
-                      const T* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st, int* err) {
+                      const T* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st, int* err,
+                      bool allow_tc) {
+  if constexpr (sizeof(T) == 4) {
+    if (allow_tc && launch_combine_tc(reinterpret_cast<float*>(out), reinterpret_cast<const float*>(in), (float)alpha,
+                          reinterpret_cast<const float*>(V), vstride, kblocks, r_in,
+                          reinterpret_cast<const float*>(C), r_out, n_rows, ldv, ldo, st, err))
+      return;
+  }
   if constexpr (sizeof(T) == 4 && W <= 24) {
     float* o = reinterpret_cast<float*>(out);
     const float* i = reinterpret_cast<const float*>(in);
@@ -1379,10 +1397,11 @@ cudaError_t init_la_attributes() { return gram_setup().err; }
 template <typename T>
 void launch_block_combine(T* out, const T* in, T alpha, const T* V, size_t vstride, int kblocks,
                           int r_in, const T* C, int r_out, int n_rows, int ldv, int Jp, cudaStream_t st,
-                          int* err) {
+                          int* err, bool allow_tc) {
   count_launch();
   const int w = std::max((r_in + 3) / 4, (r_out + 3) / 4) * 4;
-#define MHDE_CW(WV) combine_w<T, WV>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st, err)
+#define MHDE_CW(WV) \
+  combine_w<T, WV>(out, in, alpha, V, vstride, kblocks, r_in, C, r_out, n_rows, ldv, Jp, st, err, allow_tc)
   if (w <= 4) MHDE_CW(4);
   else if (w <= 8) MHDE_CW(8);
   else if (w <= 12) MHDE_CW(12);
@@ -1541,10 +1560,10 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
                                     const T*, T*, cudaStream_t);                                        \
   template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, int, cudaStream_t); \
   template void launch_gram<T>(const T*, size_t, int, const T*, int, int, int, int, double*, double*, \
-                               cudaStream_t, bool, int*);                                            \
+                               cudaStream_t, bool, int*, bool);                                      \
   template void launch_make_coef<T>(const double*, const double*, int, int, T*, cudaStream_t);       \
   template void launch_block_combine<T>(T*, const T*, T, const T*, size_t, int, int, const T*, int,  \
-                                        int, int, int, cudaStream_t, int*);                          \
+                                        int, int, int, cudaStream_t, int*, bool);                    \
   template void launch_colsq<T>(const T*, int, int, int, double*, cudaStream_t);                     \
   template void launch_scale_to<T>(const double*, const double*, T*, size_t, int, cudaStream_t);     \
   template void launch_axpy_from<T>(const T*, const double*, double*, size_t, int, cudaStream_t);     \

@@ -1,0 +1,676 @@
+// The dense contractions of the block Krylov solve on the fifth-generation
+// tensor cores (Section 1: one shared matrix, all J right-hand sides solved
+// together with block linear solvers; the block Gram V_i^T W and the block
+// combination sum_i V_i C_i are the method's only dense products).
+//
+// Both run tcgen05.mma kind::tf32 (M = 128, K = 8 per instruction) with the
+// accumulators in tensor memory.  To keep FP32-level accuracy every operand
+// x is split into hi = x with the low 13 mantissa bits cleared (exact in
+// TF32) and lo = x - hi (exact in FP32), and hi*hi + hi*lo + lo*hi is
+// accumulated: the dropped lo*lo term and the TF32 rounding of lo leave a
+// relative error of about 2^-21 per product.  Operands reach shared memory
+// by TMA bulk copies (row-major, a ring of stages); all threads then write
+// the split operands in the canonical K-major no-swizzle layout (core
+// matrices of 8 rows x 16 bytes, 128 contiguous bytes), double-buffered so
+// that the split of one tile overlaps the MMAs of the previous one; one
+// thread issues the MMAs and commits them to an mbarrier per buffer.  Every
+// mbarrier wait is bounded: past the poll limit the kernel sets the
+// caller's error word, gives its copies and MMAs in flight a bounded chance
+// to finish, frees its tensor memory and returns.
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <mutex>
+
+#include "kernels.h"
+
+namespace mhde {
+namespace {
+
+constexpr int TC_T = 256;                        // 8 warps
+constexpr size_t TC_SMEM_MAX = 225 * 1024;
+constexpr unsigned TC_BAR_BYTES = 1024;          // mbarriers and the TMEM address slot
+constexpr int TC_IMAX = 8;                       // split items per thread and tile
+constexpr long long TC_SPIN = 1ll << 24;
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool bar_wait(unsigned bar, unsigned parity) {
+  for (long long it = 0; it < TC_SPIN; ++it)
+    if (bar_try(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand, no swizzle: lbo is
+// the byte offset between core matrices adjacent along K, sbo between core
+// matrices adjacent along M (or N), i.e. between groups of 8 rows.
+__device__ __forceinline__ uint64_t kdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  return d;                                      // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
+// K-major, M and N as given.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(unsigned d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// hi*hi + hi*lo + lo*hi into d
+__device__ __forceinline__ void mma_split3(unsigned d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl,
+                                           uint32_t idesc, int accumulate) {
+  mma_tf32(d, ah, bh, idesc, accumulate);
+  mma_tf32(d, ah, bl, idesc, 1);
+  mma_tf32(d, al, bh, idesc, 1);
+}
+__device__ __forceinline__ void mma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(unsigned slot, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(unsigned tmem, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns of tensor memory
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+__device__ __forceinline__ void split4(const float x[4], float4& hi, float4& lo) {
+  hi = make_float4(tf32_hi(x[0]), tf32_hi(x[1]), tf32_hi(x[2]), tf32_hi(x[3]));
+  lo = make_float4(x[0] - hi.x, x[1] - hi.y, x[2] - hi.z, x[3] - hi.w);
+}
+
+// ------------------------------------------------------------ block Gram
+//   G_i[p][q] = sum_rows V_i[row][p] W[row][q],   i < kblocks,  p, q < r
+// is a GEMM contracting over the mesh rows: A = [V_0 | ... | V_{k-1}]
+// (stacked columns m = i ld + p, M = 128 per tile), B = W (N = r padded to
+// 16..64), K = rows.  The grid is (row ranges) x (groups of blocks whose
+// accumulators fit 256 TMEM columns).  A stage holds TR rows of every block
+// and of W (TMA bulk copies); its split transposes 4 rows x 4 columns per
+// item into 4 K chunks of the layout: per buffer, a W part (TR/4 K slices of
+// N columns) and a V part (TR/4 K slices of mtiles * 128 columns), hi then lo.
+template <int N>
+__global__ void __launch_bounds__(TC_T, 1)
+    k_gram_tc(const float* __restrict__ V, size_t vstride, int kb_total, int kgroup, const float* __restrict__ Wm,
+              int n_rows, int ld, int r, int rows_per_cta, int TR, int mtiles, unsigned ncols, unsigned stage_bytes,
+              int nst, int nl, unsigned off_lay, unsigned lay_bytes, double* __restrict__ part,
+              int* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  const int b0 = blockIdx.y * kgroup;                  // this CTA's blocks b0 .. b0 + kblocks - 1
+  const int kblocks = min(kgroup, kb_total - b0);
+  V += (size_t)b0 * vstride;
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const unsigned base = su32(tsm);
+  const unsigned bar_load = base;                      // nst barriers (<= 8)
+  const unsigned bar_mma = base + 64;                  // nl barriers (<= 4), one phase per tile of the buffer
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(tsm + 128);
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n_rows, r0 + rows_per_cta);
+  const int ntiles = r1 > r0 ? (r1 - r0 + TR - 1) / TR : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (ntiles == 0 || kblocks <= 0) {
+    for (int e = threadIdx.x; e < max(kblocks, 0) * r * r; e += TC_T)
+      part[((size_t)blockIdx.x * kb_total + b0) * r * r + e] = 0.0;
+    return;
+  }
+  const unsigned KSTRW = (unsigned)N * 16u;            // bytes per K slice of the W part
+  const unsigned KSTR = (unsigned)mtiles * 2048u;      // bytes per K slice of the V part
+  const unsigned vpart = (unsigned)(TR / 4) * KSTRW;
+  const unsigned half = lay_bytes / 2;                 // lo after hi
+  // this thread's split items, the same for every tile: 4 rows (4 k4 ..) of
+  // one 16-byte column chunk (4 columns of block b, W for b = kblocks)
+  const int nch = ld / 4, kq = TR / 4;
+  const int items = (kblocks + 1) * nch * kq;
+  int src[TC_IMAX], dst[TC_IMAX], row0[TC_IMAX], ncol[TC_IMAX];
+#pragma unroll
+  for (int q = 0; q < TC_IMAX; ++q) {
+    const int it = threadIdx.x + q * TC_T;
+    const int cg = it / kq, k4 = it - cg * kq;
+    const int b = cg / nch, c = cg - b * nch;
+    src[q] = b * TR * ld + 4 * k4 * ld + 4 * c;
+    row0[q] = 4 * k4;
+    if (it >= items) {
+      ncol[q] = 0;
+      dst[q] = 0;
+    } else if (b == kblocks) {                         // W columns past N never enter G
+      ncol[q] = max(0, min(4, N - 4 * c));
+      dst[q] = (int)(k4 * KSTRW) + 64 * c;
+    } else {
+      ncol[q] = 4;
+      dst[q] = (int)(vpart + k4 * KSTR) + 16 * (b * ld + 4 * c);
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) bar_init(bar_load + 8 * s, 1);
+    for (int j = 0; j < nl; ++j) bar_init(bar_mma + 8 * j, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    proxy_fence();
+  }
+  if (warp == 0) tmem_alloc(su32(tmem_slot), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tmem_slot;
+
+  // warp 0 fills a stage: kblocks + 1 contiguous spans of nr * ld floats
+  auto issue = [&](int tile) {
+    if (tile >= ntiles) return;
+    const int s = tile % nst;
+    const unsigned st = base + TC_BAR_BYTES + (unsigned)s * stage_bytes;
+    const int t0 = r0 + tile * TR;
+    const unsigned bytes = (unsigned)(min(TR, r1 - t0) * ld) * 4u;
+    proxy_fence();                                     // the stage was last read through the generic proxy
+    if (lane == 0) bar_expect_tx(bar_load + 8 * s, bytes * (unsigned)(kblocks + 1));
+    __syncwarp();
+    for (int b = lane; b <= kblocks; b += 32) {
+      const float* g = (b < kblocks ? V + (size_t)b * vstride : Wm) + (size_t)t0 * ld;
+      bulk_load(st + (unsigned)(b * TR * ld) * 4u, g, bytes, bar_load + 8 * s);
+    }
+  };
+  if (warp == 0)
+    for (int s = 0; s < nst; ++s) issue(s);
+
+  const uint32_t idesc = idesc_tf32(128, N);
+  int ok = 1, landed = 0;
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int s = tile % nst, j = tile % nl;
+    bool good = bar_wait(bar_load + 8 * s, (unsigned)((tile / nst) & 1));
+    if (good && tile >= nl) good = bar_wait(bar_mma + 8 * j, (unsigned)((tile / nl - 1) & 1));   // buffer free
+    tc_fence_after();
+    const float* stf = reinterpret_cast<const float*>(tsm + TC_BAR_BYTES + (size_t)s * stage_bytes);
+    unsigned char* lay = tsm + off_lay + (size_t)j * lay_bytes;
+    const int nr = min(TR, r1 - (r0 + tile * TR));
+    if (good) {
+#pragma unroll
+      for (int q = 0; q < TC_IMAX; ++q) {
+        if (ncol[q] == 0) continue;
+        float x[4][4];                                 // [row][column]
+#pragma unroll
+        for (int jr = 0; jr < 4; ++jr) {
+          float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row0[q] + jr < nr) t = *reinterpret_cast<const float4*>(stf + src[q] + jr * ld);
+          x[jr][0] = t.x;
+          x[jr][1] = t.y;
+          x[jr][2] = t.z;
+          x[jr][3] = t.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u >= ncol[q]) break;
+          const float col[4] = {x[0][u], x[1][u], x[2][u], x[3][u]};
+          float4 hi, lo;
+          split4(col, hi, lo);
+          *reinterpret_cast<float4*>(lay + dst[q] + 16 * u) = hi;
+          *reinterpret_cast<float4*>(lay + half + dst[q] + 16 * u) = lo;
+        }
+      }
+    }
+    proxy_fence();                                     // generic writes -> visible to the tensor core
+    tc_fence_before();
+    if (!__syncthreads_and(good ? 1 : 0)) {
+      ok = 0;
+      break;
+    }
+    landed = tile + 1;
+    if (warp == 0) issue(tile + nst);                  // the stage has been consumed
+    if (threadIdx.x == 32) {
+      tc_fence_after();
+      const unsigned hi = base + off_lay + (unsigned)j * lay_bytes, lo = hi + half;
+      for (int t = 0; t < mtiles; ++t)
+        for (int k8 = 0; k8 < TR / 8; ++k8) {
+          // leading (K) offset between the two 4-row K chunks of the step,
+          // stride offset between groups of 8 columns
+          const unsigned aoff = vpart + (unsigned)(2 * k8) * KSTR + (unsigned)t * 2048u;
+          const unsigned boff = (unsigned)(2 * k8) * KSTRW;
+          mma_split3(tmem + (unsigned)(t * N), kdesc(hi + aoff, KSTR, 128u), kdesc(lo + aoff, KSTR, 128u),
+                     kdesc(hi + boff, KSTRW, 128u), kdesc(lo + boff, KSTRW, 128u), idesc, (tile > 0 || k8 > 0) ? 1 : 0);
+        }
+      mma_commit(bar_mma + 8 * j);
+    }
+  }
+  if (ok) {
+    // the last tile's MMAs complete after all earlier ones
+    const int lt = ntiles - 1;
+    ok = __syncthreads_and(bar_wait(bar_mma + 8 * (lt % nl), (unsigned)((lt / nl) & 1)) ? 1 : 0);
+    tc_fence_after();
+    if (ok) {
+      const int q4 = warp & 3, grp = warp >> 2;        // TMEM lanes 32 q4 .. 32 q4 + 31
+      for (int t = grp; t < mtiles; t += TC_T / 128) {
+        float v[N];
+        const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(t * N);
+#pragma unroll
+        for (int c16 = 0; c16 < N / 16; ++c16) tmem_ld16(taddr + 16 * c16, v + 16 * c16);
+        const int m = 128 * t + 32 * q4 + lane;        // stacked column of the V blocks
+        const int b = m / ld, p = m - b * ld;
+        if (b < kblocks && p < r) {
+          double* d = part + (((size_t)blockIdx.x * kb_total + b0 + b) * r + p) * r;
+#pragma unroll
+          for (int q = 0; q < N; ++q)
+            if (q < r) d[q] = (double)v[q];
+        }
+      }
+    }
+  }
+  if (!ok && threadIdx.x == 0) {
+    // a wait gave up: record it, let every copy and MMA in flight finish
+    // (bounded), and leave without partial sums
+    atomicExch(err, 1);
+    for (int tl = landed; tl < min(ntiles, landed + nst); ++tl)
+      bar_wait(bar_load + 8 * (tl % nst), (unsigned)((tl / nst) & 1));
+    if (landed > 0) bar_wait(bar_mma + 8 * ((landed - 1) % nl), (unsigned)(((landed - 1) / nl) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tmem, ncols);
+  }
+}
+
+// ------------------------------------------------------------ block combination
+// out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q]  (q < r_out,
+// zero up to ldo): the new Krylov block and the solution update of the block
+// GMRES.  A GEMM with M = rows, K = (block, column) and N = r_out padded to
+// 16..64: A = the V row tiles, B = the coefficient blocks.  A CTA owns up to
+// MT tiles of 128 rows with their accumulators in tensor memory (MT N <= 512
+// columns) and walks stage s = (block i, row tile t) in block order: one TMA
+// bulk copy of 128 rows into a ring of nst stages, their split into one of
+// nl A buffers (element (m, p) at (p/4) 2048 + m 16 + (p%4) 4), and 3 MMAs per
+// K step of 8.  Coefficient block i is split into buffer i % 2 (element (q,
+// p) at (p/4) N 16 + q 16 + (p%4) 4) at the block's first tile.  The CTA has
+// read all of its rows of every block before it writes out, so out may alias
+// in or one of the blocks.
+template <int N>
+__global__ void __launch_bounds__(TC_T, 1)
+    k_combine_tc(float* out, const float* in, float alpha, const float* V, size_t vstride, int kblocks, int r_in,
+                 const float* __restrict__ C, int r_out, int n_rows, int ldv, int ldo, int rows_per_cta, int KC,
+                 unsigned ncols, unsigned stage_bytes, int nst, int nl, unsigned off_a, unsigned a_bytes,
+                 unsigned off_b, unsigned b_bytes, int* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const unsigned base = su32(tsm);
+  const unsigned bar_load = base;                      // nst barriers (<= 8)
+  const unsigned bar_mma = base + 64;                  // nl barriers (<= 4)
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(tsm + 128);
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n_rows, r0 + rows_per_cta);
+  if (r1 <= r0) return;
+  const int MT = (r1 - r0 + 127) / 128;                // row tiles of this CTA
+  const int nstages = kblocks * MT;
+  const int warp = threadIdx.x >> 5;
+  const int nch = ldv / 4;                             // 16-byte chunks of a V row
+  const unsigned ahalf = a_bytes / 2, bhalf = b_bytes / 2;
+  // this thread's split items of a row tile: (chunk k4, row m)
+  int src[TC_IMAX], dst[TC_IMAX], mrow[TC_IMAX], ncol[TC_IMAX];
+#pragma unroll
+  for (int q = 0; q < TC_IMAX; ++q) {
+    const int it = threadIdx.x + q * TC_T;
+    const int k4 = it >> 7, m = it & 127;
+    src[q] = m * ldv + 4 * k4;
+    dst[q] = k4 * 2048 + m * 16;
+    mrow[q] = m;
+    ncol[q] = it < nch * 128 ? max(0, min(4, r_in - 4 * k4)) : -1;   // -1: no item; columns past r_in are 0
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) bar_init(bar_load + 8 * s, 1);
+    for (int j = 0; j < nl; ++j) bar_init(bar_mma + 8 * j, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    proxy_fence();
+  }
+  // K padding chunks (columns ldv .. 4 KC - 1) of every A buffer stay zero
+  for (int e = threadIdx.x; e < nl * (KC - nch) * 128; e += TC_T) {
+    const int j = e / ((KC - nch) * 128), rem = e - j * (KC - nch) * 128;
+    const int k4 = nch + rem / 128, m = rem % 128;
+    unsigned char* a = tsm + off_a + (size_t)j * a_bytes + (size_t)k4 * 2048 + (size_t)m * 16;
+    *reinterpret_cast<float4*>(a) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(a + ahalf) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (warp == 0) tmem_alloc(su32(tmem_slot), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tmem_slot;
+
+  auto issue = [&](int sidx) {                         // stage sidx = (block i, row tile t)
+    if (sidx >= nstages) return;
+    const int i = sidx / MT, t = sidx - i * MT;
+    const int t0 = r0 + 128 * t;
+    const unsigned bytes = (unsigned)(min(128, r1 - t0) * ldv) * 4u;
+    const unsigned bar = bar_load + 8 * (sidx % nst);
+    proxy_fence();
+    bar_expect_tx(bar, bytes);
+    bulk_load(base + TC_BAR_BYTES + (unsigned)(sidx % nst) * stage_bytes, V + (size_t)i * vstride + (size_t)t0 * ldv,
+              bytes, bar);
+  };
+  if (threadIdx.x == 0)
+    for (int s = 0; s < nst; ++s) issue(s);
+
+  const uint32_t idesc = idesc_tf32(128, N);
+  const unsigned bstride = (unsigned)N * 16u;          // between K chunks of a coefficient buffer
+  int ok = 1, landed = 0;
+  for (int sidx = 0; sidx < nstages; ++sidx) {
+    const int i = sidx / MT, t = sidx - i * MT, j = sidx % nl;
+    bool good = bar_wait(bar_load + 8 * (sidx % nst), (unsigned)((sidx / nst) & 1));
+    // A buffer j is free once the MMAs of stage sidx - nl completed; in order,
+    // so are those of block i - 2 (nl <= MT + 1), whose coefficient buffer
+    // block i reuses
+    if (good && sidx >= nl) good = bar_wait(bar_mma + 8 * j, (unsigned)((sidx / nl - 1) & 1));
+    tc_fence_after();
+    const unsigned bsel = off_b + (unsigned)(i & 1) * b_bytes;
+    if (good && t == 0) {
+      for (int e = threadIdx.x; e < KC * N; e += TC_T) {
+        const int k4 = e / N, q = e - k4 * N;
+        float cv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int pp = 4 * k4 + u;
+          cv[u] = (pp < r_in && q < r_out) ? C[((size_t)i * r_in + pp) * r_out + q] : 0.f;
+        }
+        float4 hi, lo;
+        split4(cv, hi, lo);
+        const size_t o = (size_t)k4 * bstride + (size_t)q * 16;
+        *reinterpret_cast<float4*>(tsm + bsel + o) = hi;
+        *reinterpret_cast<float4*>(tsm + bsel + bhalf + o) = lo;
+      }
+    }
+    if (good) {
+      const float* stf = reinterpret_cast<const float*>(tsm + TC_BAR_BYTES + (size_t)(sidx % nst) * stage_bytes);
+      unsigned char* a = tsm + off_a + (size_t)j * a_bytes;
+      const int nr = min(128, r1 - (r0 + 128 * t));
+#pragma unroll
+      for (int q = 0; q < TC_IMAX; ++q) {
+        if (ncol[q] < 0) continue;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (mrow[q] < nr) {
+          const float4 v4 = *reinterpret_cast<const float4*>(stf + src[q]);
+          x[0] = v4.x;
+          x[1] = v4.y;
+          x[2] = v4.z;
+          x[3] = v4.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u >= ncol[q]) x[u] = 0.f;
+        float4 hi, lo;
+        split4(x, hi, lo);
+        *reinterpret_cast<float4*>(a + dst[q]) = hi;
+        *reinterpret_cast<float4*>(a + ahalf + dst[q]) = lo;
+      }
+    }
+    proxy_fence();
+    tc_fence_before();
+    if (!__syncthreads_and(good ? 1 : 0)) {
+      ok = 0;
+      break;
+    }
+    landed = sidx + 1;
+    if (threadIdx.x == 0) issue(sidx + nst);           // the stage has been consumed
+    if (threadIdx.x == 32) {
+      tc_fence_after();
+      const unsigned ahi = base + off_a + (unsigned)j * a_bytes, alo = ahi + ahalf;
+      const unsigned bhi = base + bsel, blo = bhi + bhalf;
+      const unsigned d = tmem + (unsigned)(t * N);
+      for (int k8 = 0; k8 < KC / 2; ++k8)
+        mma_split3(d, kdesc(ahi + (unsigned)k8 * 4096u, 2048u, 128u), kdesc(alo + (unsigned)k8 * 4096u, 2048u, 128u),
+                   kdesc(bhi + (unsigned)k8 * 2u * bstride, bstride, 128u),
+                   kdesc(blo + (unsigned)k8 * 2u * bstride, bstride, 128u), idesc, (i > 0 || k8 > 0) ? 1 : 0);
+      mma_commit(bar_mma + 8 * j);
+    }
+  }
+  if (ok) {
+    const int ls = nstages - 1;
+    ok = __syncthreads_and(bar_wait(bar_mma + 8 * (ls % nl), (unsigned)((ls / nl) & 1)) ? 1 : 0);
+    tc_fence_after();
+    if (ok) {
+      const int q4 = warp & 3, grp = warp >> 2, lane = threadIdx.x & 31;
+      for (int t = grp; t < MT; t += TC_T / 128) {
+        float v[N];
+        const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(t * N);
+#pragma unroll
+        for (int c16 = 0; c16 < N / 16; ++c16) tmem_ld16(taddr + 16 * c16, v + 16 * c16);
+        const int row = r0 + 128 * t + 32 * q4 + lane;
+        if (row < r1) {
+          float* orow = out + (size_t)row * ldo;
+          const float* irow = in ? in + (size_t)row * ldo : nullptr;
+#pragma unroll
+          for (int q = 0; q < N; q += 4) {
+            if (q < ldo) {
+              float4 i4 = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (irow) i4 = *reinterpret_cast<const float4*>(irow + q);
+              float4 o4;
+              o4.x = q + 0 < r_out ? alpha * i4.x + v[q + 0] : 0.f;
+              o4.y = q + 1 < r_out ? alpha * i4.y + v[q + 1] : 0.f;
+              o4.z = q + 2 < r_out ? alpha * i4.z + v[q + 2] : 0.f;
+              o4.w = q + 3 < r_out ? alpha * i4.w + v[q + 3] : 0.f;
+              *reinterpret_cast<float4*>(orow + q) = o4;
+            }
+          }
+          for (int q = N; q < ldo; q += 4) *reinterpret_cast<float4*>(orow + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    }
+  }
+  if (!ok && threadIdx.x == 0) {
+    atomicExch(err, 1);
+    for (int sl = landed; sl < min(nstages, landed + nst); ++sl)
+      bar_wait(bar_load + 8 * (sl % nst), (unsigned)((sl / nst) & 1));
+    if (landed > 0) bar_wait(bar_mma + 8 * ((landed - 1) % nl), (unsigned)(((landed - 1) / nl) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tmem, ncols);
+  }
+}
+
+struct TcDevice {
+  bool ready = false;
+  int nsm = 1;
+  cudaError_t err = cudaSuccess;
+};
+std::mutex g_tc_mutex;
+TcDevice g_tc_dev[64];
+
+const TcDevice& tc_setup() {
+  static const TcDevice none{false, 1, cudaErrorInvalidDevice};   // never written
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return none;
+  std::lock_guard<std::mutex> lock(g_tc_mutex);
+  TcDevice& d = g_tc_dev[dev];
+  if (d.ready) return d;
+  cudaError_t e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (d.nsm <= 0) d.nsm = 1;
+  int major = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (e == cudaSuccess && major < 10) e = cudaErrorInvalidDeviceFunction;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+  };
+  set((const void*)k_gram_tc<16>);
+  set((const void*)k_gram_tc<32>);
+  set((const void*)k_gram_tc<48>);
+  set((const void*)k_gram_tc<64>);
+  set((const void*)k_combine_tc<16>);
+  set((const void*)k_combine_tc<32>);
+  set((const void*)k_combine_tc<48>);
+  set((const void*)k_combine_tc<64>);
+  d.err = e;
+  d.ready = true;
+  return d;
+}
+
+}  // namespace
+
+bool gram_tc_plan(int kblocks, int ld, int r, TcGramPlan& p) {
+  if (kblocks < 1 || r < 1 || r > 64 || ld < r || ld % 4 != 0 || ld > 64) return false;
+  p.nch = ld / 4;
+  p.N = (r + 15) / 16 * 16;
+  // blocks per CTA: their accumulators (M tiles of 128 stacked columns, N
+  // columns each) fit 256 TMEM columns, so two CTAs on one SM never wait
+  // for each other's tensor memory
+  p.kgroup = std::min(kblocks, std::max(1, (256 / p.N) * 128 / ld));
+  while (p.kgroup > 1 && ((p.kgroup * ld + 127) / 128) * p.N > 256) --p.kgroup;
+  for (; p.kgroup >= 1; --p.kgroup) {
+    p.mtiles = (p.kgroup * ld + 127) / 128;
+    p.ncols = 32;
+    while ((int)p.ncols < p.mtiles * p.N) p.ncols *= 2;
+    // deepest ring first, then the largest tile: 3 stages and 2 split
+    // buffers, else 2 and 2
+    for (int nst = 3; nst >= 2; --nst)
+      for (int TR = 64; TR >= 8; TR -= 8) {
+        const size_t stage = (size_t)(p.kgroup + 1) * TR * ld * 4;
+        const size_t lay = 2 * (size_t)TR * 4 * (p.N + (size_t)p.mtiles * 128);   // hi + lo
+        const size_t off_lay = (TC_BAR_BYTES + nst * stage + 1023) / 1024 * 1024;
+        const size_t total = off_lay + 2 * lay;
+        const int items = (p.kgroup + 1) * p.nch * (TR / 4);
+        if (total <= TC_SMEM_MAX && stage < (1u << 20) && items <= TC_IMAX * TC_T) {
+          p.TR = TR;
+          p.nst = nst;
+          p.nl = 2;
+          p.stage_bytes = (unsigned)stage;
+          p.off_lay = (unsigned)off_lay;
+          p.lay_bytes = (unsigned)lay;
+          p.smem = total;
+          p.ngroups = (kblocks + p.kgroup - 1) / p.kgroup;
+          return true;
+        }
+      }
+  }
+  return false;
+}
+
+bool tc_gram_available() { return tc_setup().err == cudaSuccess; }
+
+bool launch_gram_tc(const float* V, size_t vstride, int kblocks, const float* W, int n_rows, int ld, int r,
+                    int max_parts, double* part, cudaStream_t st, int* err, int& nparts) {
+  TcGramPlan p;
+  const TcDevice& d = tc_setup();
+  if (d.err != cudaSuccess || !err || !gram_tc_plan(kblocks, ld, r, p)) return false;
+  if ((reinterpret_cast<uintptr_t>(V) & 15) || (reinterpret_cast<uintptr_t>(W) & 15) || (vstride & 3)) return false;
+  const int nctas = std::max(1, std::min({d.nsm / p.ngroups, max_parts, (n_rows + 7) / 8}));
+  const int rows_per_cta = (n_rows + nctas - 1) / nctas;
+  nparts = nctas;
+  const dim3 grid(nctas, p.ngroups);
+#define MHDE_TC(NN)                                                                                          \
+  launch_pdl(k_gram_tc<NN>, grid, dim3(TC_T), p.smem, st, V, vstride, kblocks, p.kgroup, W, n_rows, ld, r, \
+             rows_per_cta, p.TR, p.mtiles, p.ncols, p.stage_bytes, p.nst, p.nl, p.off_lay, p.lay_bytes, part, err)
+  switch (p.N) {
+    case 16: MHDE_TC(16); break;
+    case 32: MHDE_TC(32); break;
+    case 48: MHDE_TC(48); break;
+    default: MHDE_TC(64); break;
+  }
+#undef MHDE_TC
+  return true;
+}
+
+bool combine_tc_plan(int n_rows, int ldv, int r_in, int r_out, int nsm, TcCombinePlan& p) {
+  if (r_in < 1 || r_out < 1 || r_out > 64 || ldv < r_in || ldv % 4 != 0 || ldv > 64 || n_rows < 1) return false;
+  p.N = (r_out + 15) / 16 * 16;
+  p.KC = (ldv + 7) / 8 * 2;                            // 16-byte K chunks, an even number (K steps of 8)
+  if ((ldv / 4) * 128 > TC_IMAX * TC_T) return false;
+  const int mt_max = 512 / p.N;
+  int rows = (n_rows + std::max(nsm, 1) - 1) / std::max(nsm, 1);
+  rows = (rows + 127) / 128 * 128;
+  p.MT = std::max(1, std::min(mt_max, rows / 128));
+  p.rows_per_cta = 128 * p.MT;
+  p.nctas = (n_rows + p.rows_per_cta - 1) / p.rows_per_cta;
+  p.ncols = 32;
+  while ((int)p.ncols < p.MT * p.N) p.ncols *= 2;
+  p.stage_bytes = 128u * (unsigned)ldv * 4u;
+  p.a_bytes = 2u * (unsigned)p.KC * 2048u;
+  p.b_bytes = 2u * (unsigned)p.KC * (unsigned)p.N * 16u;
+  // as many split buffers as fit (at most 4 and MT + 1), then stages
+  for (int nl = std::min(4, p.MT + 1); nl >= 1; --nl)
+    for (int nst = 3; nst >= 2; --nst) {
+      const size_t off_a = (TC_BAR_BYTES + (size_t)nst * p.stage_bytes + 1023) / 1024 * 1024;
+      const size_t off_b = off_a + (size_t)nl * p.a_bytes;
+      const size_t total = off_b + 2 * (size_t)p.b_bytes;
+      if (total <= TC_SMEM_MAX) {
+        p.nl = nl;
+        p.nst = nst;
+        p.off_a = (unsigned)off_a;
+        p.off_b = (unsigned)off_b;
+        p.smem = total;
+        return true;
+      }
+    }
+  return false;
+}
+
+bool launch_combine_tc(float* out, const float* in, float alpha, const float* V, size_t vstride, int kblocks,
+                       int r_in, const float* C, int r_out, int n_rows, int ldv, int ldo, cudaStream_t st, int* err) {
+  if (!err || kblocks < 1) return false;
+  const TcDevice& d = tc_setup();
+  TcCombinePlan p;
+  if (d.err != cudaSuccess || !combine_tc_plan(n_rows, ldv, r_in, r_out, d.nsm, p)) return false;
+  if ((reinterpret_cast<uintptr_t>(V) & 15) || (reinterpret_cast<uintptr_t>(out) & 15) ||
+      (reinterpret_cast<uintptr_t>(in) & 15) || (vstride & 3) || (ldo & 3) || ldo > 64 || ldo < r_out)
+    return false;
+#define MHDE_TCC(NN)                                                                                              \
+  launch_pdl(k_combine_tc<NN>, dim3(p.nctas), dim3(TC_T), p.smem, st, out, in, alpha, V, vstride, kblocks, r_in, C, \
+             r_out, n_rows, ldv, ldo, p.rows_per_cta, p.KC, p.ncols, p.stage_bytes, p.nst, p.nl, p.off_a,          \
+             p.a_bytes, p.off_b, p.b_bytes, err)
+  switch (p.N) {
+    case 16: MHDE_TCC(16); break;
+    case 32: MHDE_TCC(32); break;
+    case 48: MHDE_TCC(48); break;
+    default: MHDE_TCC(64); break;
+  }
+#undef MHDE_TCC
+  return true;
+}
+
+}  // namespace mhde

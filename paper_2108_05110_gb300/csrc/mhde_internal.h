@@ -266,6 +266,11 @@ struct mhde_ctx {
   int spmm_block = 256;                // CTA size of the chunked saddle SpMM (autotuned at bind)
   bool spmm_forced = false;            // MHDE_SPMM set: skip the autotuner
   double spmm_tuned_us[3] = {0, 0, 0}; // autotuner timings for CTA sizes 128, 256, 512
+  // FP32 block Gram and combination: tensor-core (tcgen05) or CUDA-core
+  // kernels, picked at bind by timing both on this context's sizes
+  bool gram_tc = false, comb_tc = false;
+  double gram_tuned_us[2] = {0, 0};    // CUDA cores, tensor cores
+  double comb_tuned_us[2] = {0, 0};
   mhde::Sub sub[2];
   std::vector<int> h_bidx;             // boundary index of every P2 node (host copy)
   std::vector<double> h_M;             // mass matrix values (host copy, for the energy)

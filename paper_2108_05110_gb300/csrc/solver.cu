@@ -246,7 +246,8 @@ static int gram_chunks(const mhde_ctx* c, int k, int r) {
 template <typename T>
 static int gram_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int k, const T* W, int r,
                      std::vector<double>& out, int ld) {
-  launch_gram<T>(V, vstride, k, W, c->n_rows, ld, r, gram_chunks(c, k, r), s.part, s.gram, s.stream, true, s.d_err);
+  launch_gram<T>(V, vstride, k, W, c->n_rows, ld, r, gram_chunks(c, k, r), s.part, s.gram, s.stream, true, s.d_err,
+                 c->gram_tc);
   SCU(cudaMemcpyAsync(s.hbuf, s.gram, sizeof(double) * k * r * r, cudaMemcpyDeviceToHost, s.stream));
   SCU(cudaStreamSynchronize(s.stream));
   out.assign(s.hbuf, s.hbuf + (size_t)k * r * r);
@@ -259,7 +260,7 @@ template <typename T>
 static int gram_proj_host(const mhde_ctx* c, Sub& s, const T* V, size_t vstride, int k, const T* W, int r, int ld,
                           std::vector<double>& out) {
   launch_gram<T>(V, vstride, k + 2, W, c->n_rows, ld, r, gram_chunks(c, k + 2, r), s.part, s.gram, s.stream, true,
-                 s.d_err);
+                 s.d_err, c->gram_tc);
   launch_proj_gram(s.gram, k, r, s.stream);
   const size_t n = (size_t)(k + 3) * r * r;
   SCU(cudaMemcpyAsync(s.hbuf, s.gram, sizeof(double) * n, cudaMemcpyDeviceToHost, s.stream));
@@ -369,24 +370,24 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
         // coefficients -H_i T and T are formed on the device
         const double* dT = upload_coef<double>(c, s, Tn, 1);
         launch_make_coef<T>(s.gram, dT, k, r, dcoef, st);
-        launch_block_combine<T>(Wn, nullptr, T(0), Vb, vs, k + 2, r, dcoef, r, c->n_rows, Rp, Rp, st, s.d_err);
+        launch_block_combine<T>(Wn, nullptr, T(0), Vb, vs, k + 2, r, dcoef, r, c->n_rows, Rp, Rp, st, s.d_err, c->comb_tc);
       }
     } else {
       // strong cancellation: explicit two-pass Gram-Schmidt for this block
       H.assign(Hsum.begin(), Hsum.end());
       for (auto& v : H) v = -v;
       T* dc = upload_coef<T>(c, s, H, 0);
-      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err);
+      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err, c->comb_tc);
       if ((rc = gram_host<T>(c, s, Vb, vs, k + 1, Wn, r, H, Rp))) return rc;
       for (size_t t2 = 0; t2 < H.size(); ++t2) Hsum[t2] += H[t2];
       for (auto& v : H) v = -v;
       dc = upload_coef<T>(c, s, H, 1);
-      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err);
+      launch_block_combine<T>(Wn, Wn, T(1), Vb, vs, k + 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err, c->comb_tc);
       if ((rc = gram_host<T>(c, s, Wn, 0, 1, Wn, r, G, Rp))) return rc;
       rk = svqb(r, G, thresh, Tn, Sn);
       if (rk == r) {
         dc = upload_coef<T>(c, s, Tn, 2);
-        launch_block_combine<T>(Wn, nullptr, T(0), Wn, 0, 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err);
+        launch_block_combine<T>(Wn, nullptr, T(0), Wn, 0, 1, r, dc, r, c->n_rows, Rp, Rp, st, s.d_err, c->comb_tc);
       }
     }
     pc3.stop(4);
@@ -423,7 +424,7 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
   }
   ls.solve(Y);
   T* dc = upload_coef<T>(c, s, Y, 3);
-  launch_block_combine<T>(D, nullptr, T(0), Zb, vs, k, r, dc, J, c->n_rows, Rp, Jp, st, s.d_err);
+  launch_block_combine<T>(D, nullptr, T(0), Zb, vs, k, r, dc, J, c->n_rows, Rp, Jp, st, s.d_err, c->comb_tc);
   return MHDE_OK;
 }
 
@@ -534,10 +535,10 @@ void gram_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, cons
   const int nchunk = gram_chunks(c, k, c->J);
   if (c->opt.precision == MHDE_PREC_FP64)
     launch_gram<double>((const double*)V, vstride, k, (const double*)W, c->n_rows, c->Jp, c->J, nchunk, s.part,
-                        s.gram, s.stream, reduce, s.d_err);
+                        s.gram, s.stream, reduce, s.d_err, c->gram_tc);
   else
     launch_gram<float>((const float*)V, vstride, k, (const float*)W, c->n_rows, c->Jp, c->J, nchunk, s.part,
-                       s.gram, s.stream, reduce, s.d_err);
+                       s.gram, s.stream, reduce, s.d_err, c->gram_tc);
 }
 
 // out = sum_i V_i C_i over k blocks of J columns with the coefficients in
@@ -546,10 +547,12 @@ void combine_any(mhde_ctx* c, int which, const void* V, size_t vstride, int k, v
   Sub& s = c->sub[which];
   if (c->opt.precision == MHDE_PREC_FP64)
     launch_block_combine<double>((double*)out, nullptr, 0.0, (const double*)V, vstride, k, c->J,
-                                 (const double*)s.coef, c->J, c->n_rows, c->Jp, c->Jp, s.stream, s.d_err);
+                                 (const double*)s.coef, c->J, c->n_rows, c->Jp, c->Jp, s.stream, s.d_err,
+                                c->comb_tc);
   else
     launch_block_combine<float>((float*)out, nullptr, 0.f, (const float*)V, vstride, k, c->J, (const float*)s.coef,
-                                c->J, c->n_rows, c->Jp, c->Jp, s.stream, s.d_err);
+                                c->J, c->n_rows, c->Jp, c->Jp, s.stream, s.d_err,
+                                c->comb_tc);
 }
 
 int solve_sub(mhde_ctx* c, int which, bool zero_guess) {
