@@ -51,9 +51,10 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-separate", action="store_true", help="skip the separate-solve comparator")
-    p.add_argument("--workload", default="cavity", choices=["cavity", "channel", "batched"],
+    p.add_argument("--workload", default="cavity", choices=["cavity", "channel", "batched", "adjoint"],
                    help="cavity: the metric's workload; channel: the channel-past-a-step ensemble; "
-                        "batched: uneven independent ensembles")
+                        "batched: uneven independent ensembles; adjoint: forward and forward + discrete "
+                        "adjoint of the sensitivity workload")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--batch-threads", type=int, default=4, help="host threads of mhde_advance_many")
     p.add_argument("--batch-mem-gb", type=float, default=240.0,
@@ -66,6 +67,9 @@ def parse():
                         "4 means+l2, 5 preconditioner, 6 Gram)")
     p.add_argument("--no-oracle-check", action="store_true",
                    help="skip the one-step oracle check of the benchmarked state")
+    p.add_argument("--cpu-study", action="store_true",
+                   help="time the FP64 oracle on the host cores three ways (factor per member, factor once per "
+                        "step, a process pool over members) on the workload's first step, print one JSON line")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--oracle-check", default=None, help=argparse.SUPPRESS)
     p.add_argument("--N", type=int, default=WORKLOAD["N"])
@@ -211,6 +215,81 @@ def fp64_same_steps(args, ens, state0, device):
                    "and first steps of the timed region"}
     sol.close()
     return out
+
+
+# --------------------------------------------------------------------------- CPU oracle study
+def _v_system(workload, N, J):
+    """The v-subproblem of the workload's first step through the oracle:
+    (saddle matrix, right-hand sides of all members)."""
+    from oracle.scheme import OracleRun, ensemble_mean, mixing_length_sq
+    ens = make_ensemble(workload, N, J)
+    run = OracleRun(ens)
+    mw = ensemble_mean(run.W)
+    Wp = run.W - mw
+    A = run.saddle(run.shared_matrix(mw, mixing_length_sq(run.S, Wp)))
+    f1, _, gv, _ = run.member_data(ens.dt)
+    bs = [run.rhs(run.V, run.W, Wp, f1, gv, j, run.nu_p + run.nu_m_p, run.nu - run.nu_m) for j in range(J)]
+    return A, bs
+
+
+def _pool_member(args):
+    """One member's v-subproblem with its own factorisation (a pool worker)."""
+    workload, N, J, j = args
+    from scipy.sparse.linalg import splu
+    A, bs = _v_system(workload, N, J)
+    t0 = time.perf_counter()
+    splu(A).solve(bs[j])
+    return time.perf_counter() - t0
+
+
+def cpu_study(args):
+    """Host-core baselines of the oracle on the v-subproblem of the first
+    step (half a member-step per member): (1) factor per member, (2) factor
+    once and solve every member (the shared matrix of Section 1), (3) a
+    process pool over members, each factorising its own copy.  Rates are in
+    member-steps/s (two subproblems per member-step)."""
+    import multiprocessing as mp
+    import platform
+    from scipy.sparse.linalg import splu
+    info = {"os_cpu_count": os.cpu_count(), "machine": platform.machine(), "processor": platform.processor()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "CPU(s)", "Thread(s) per core", "Core(s) per socket",
+                                              "Socket(s)", "Vendor ID"):
+                info[line.split(":")[0].strip()] = line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    J = args.J
+    t0 = time.perf_counter()
+    A, bs = _v_system(args.workload, args.N, J)
+    t_assemble = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lu = splu(A)
+    t_factor = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for b in bs:
+        lu.solve(b)
+    t_solves = time.perf_counter() - t0
+    per_member = t_factor + t_solves / J
+    once = t_factor + t_solves
+    workers = max(1, min(J, os.cpu_count() or 1))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        t0 = time.perf_counter()
+        per_worker = pool.map(_pool_member, [(args.workload, args.N, J, j) for j in range(workers)])
+        t_wall = time.perf_counter() - t0
+    t_pool = max(per_worker)                            # the workers factorise and solve concurrently
+    rate = lambda members, secs: 0.5 * members / secs
+    return {"cpu_study": True, "workload": config(args)["workload"], "host": info,
+            "threads_per_process": os.environ.get("OMP_NUM_THREADS", "unset"),
+            "assemble_s": t_assemble, "factor_s": t_factor, "solve_s_per_member": t_solves / J,
+            "factor_per_member": {"member_steps_per_s": rate(1, per_member), "cores": 1},
+            "factor_once_per_step": {"member_steps_per_s": rate(J, once), "cores": 1},
+            "process_pool": {"member_steps_per_s": rate(workers, t_pool), "cores": workers,
+                             "slowest_worker_s": t_pool, "pool_wall_s": t_wall,
+                             "what": f"{workers} spawned processes at once, each assembling, factorising and "
+                                     "solving its own member; rate from the slowest worker's factor + solve"}}
 
 
 # --------------------------------------------------------------------------- clocks
@@ -404,6 +483,46 @@ def batched_arm(args, local_rank):
     for sol in sols:
         sol.close()
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- adjoint timing
+def adjoint_arm(args, local_rank):
+    """The sensitivity workload (64x64, J = 8, s = 0.5, dt = 0.01, 40 steps,
+    checkpoint every 5): wall time of the 40 forward steps alone and of the
+    forward run plus the discrete adjoint (mhde_energy_adjoint), both
+    precisions, after one untimed run of each."""
+    import torch
+    from paper_2108_05110_gb300 import ensemble_io, PREC_FP64, PREC_MIXED
+    from workloads.ensembles import sensitivity
+    torch.cuda.set_device(local_rank)
+    ens = sensitivity()
+    K, C = ens.nsteps, 5
+    out = {"metric": "discrete adjoint of E_h^K: wall time", "unit": "s", "config": {
+        "workload": "sensitivity: unit square 64x64, P2-P1, J=8, nu, nu_m = 0.005(1+delta), s=0.5, dt=0.01, "
+                    "K=40 steps, checkpoint every 5", "mesh": "64x64", "J": ens.J}, "data": "synthetic"}
+    for name, prec in (("fp64", PREC_FP64), ("mixed", PREC_MIXED)):
+        sol = ensemble_io.solver_for(ens, precision=prec, device=f"cuda:{local_rank}")
+        ensemble_io.feed_initial(sol, ens)
+        ensemble_io.feed_step_data(sol, ens, ens.dt)
+        state = sol.save_state()
+        res = {}
+        for rep in range(2):
+            sol.load_state(state)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol.advance(K)
+            torch.cuda.synchronize()
+            res["forward_s"] = time.perf_counter() - t0
+            sol.load_state(state)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = sol.energy_adjoint(K, C)
+            torch.cuda.synchronize()
+            res["forward_and_adjoint_s"] = time.perf_counter() - t0
+        res["loss"] = g["loss"]
+        out[name] = res
+        sol.close()
+    print(json.dumps(out), flush=True)
 
 
 # --------------------------------------------------------------------------- our arm
@@ -607,6 +726,9 @@ def main():
     if args.oracle_check:
         print(json.dumps(oracle_step_check(args.oracle_check, args.workload, args.N, args.J)), flush=True)
         return
+    if args.cpu_study:
+        print(json.dumps(cpu_study(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -616,6 +738,10 @@ def main():
     if args.workload == "batched":
         if rank == 0:
             batched_arm(args, local_rank)
+        return
+    if args.workload == "adjoint":
+        if rank == 0:
+            adjoint_arm(args, local_rank)
         return
     if world > 1:
         import torch

@@ -115,7 +115,7 @@ void launch_gram(const T* V, size_t vstride, int kblocks, const T* W, int n_rows
 // false (nothing launched) when the sizes or the device do not fit the
 // kernel; err as for launch_gram (required)
 struct TcGramPlan {
-  int nch = 0, N = 0, mtiles = 0, TR = 0, kgroup = 0, ngroups = 0, nst = 0, nl = 0;
+  int nch = 0, N = 0, mtiles = 0, TR = 0, kgroup = 0, ngroups = 0, nst = 0, nl = 0, per_sm = 1;
   unsigned ncols = 0, stage_bytes = 0, off_lay = 0, lay_bytes = 0;
   size_t smem = 0;
 };

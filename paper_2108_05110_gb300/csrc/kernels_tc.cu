@@ -29,6 +29,7 @@ namespace {
 
 constexpr int TC_T = 256;                        // 8 warps
 constexpr size_t TC_SMEM_MAX = 225 * 1024;
+constexpr size_t TC_SMEM_TWO = 110 * 1024;       // two CTAs per SM below this
 constexpr unsigned TC_BAR_BYTES = 1024;          // mbarriers and the TMEM address slot
 constexpr int TC_IMAX = 8;                       // split items per thread and tile
 constexpr long long TC_SPIN = 1ll << 24;
@@ -137,11 +138,13 @@ __device__ __forceinline__ void split4(const float x[4], float4& hi, float4& lo)
 // (stacked columns m = i ld + p, M = 128 per tile), B = W (N = r padded to
 // 16..64), K = rows.  The grid is (row ranges) x (groups of blocks whose
 // accumulators fit 256 TMEM columns).  A stage holds TR rows of every block
-// and of W (TMA bulk copies); its split transposes 4 rows x 4 columns per
-// item into 4 K chunks of the layout: per buffer, a W part (TR/4 K slices of
-// N columns) and a V part (TR/4 K slices of mtiles * 128 columns), hi then lo.
+// and of W (TMA bulk copies); its split transposes 4 rows of one column per
+// item into one K chunk of the layout (consecutive threads take consecutive
+// columns, so neither the reads nor the writes conflict in shared-memory
+// banks): per buffer, a W part (TR/4 K slices of N columns) and a V part
+// (TR/4 K slices of mtiles * 128 columns), hi then lo.
 template <int N>
-__global__ void __launch_bounds__(TC_T, 1)
+__global__ void __launch_bounds__(TC_T, 2)
     k_gram_tc(const float* __restrict__ V, size_t vstride, int kb_total, int kgroup, const float* __restrict__ Wm,
               int n_rows, int ld, int r, int rows_per_cta, int TR, int mtiles, unsigned ncols, unsigned stage_bytes,
               int nst, int nl, unsigned off_lay, unsigned lay_bytes, double* __restrict__ part,
@@ -168,27 +171,24 @@ __global__ void __launch_bounds__(TC_T, 1)
   const unsigned KSTR = (unsigned)mtiles * 2048u;      // bytes per K slice of the V part
   const unsigned vpart = (unsigned)(TR / 4) * KSTRW;
   const unsigned half = lay_bytes / 2;                 // lo after hi
-  // this thread's split items, the same for every tile: 4 rows (4 k4 ..) of
-  // one 16-byte column chunk (4 columns of block b, W for b = kblocks)
-  const int nch = ld / 4, kq = TR / 4;
-  const int items = (kblocks + 1) * nch * kq;
-  int src[TC_IMAX], dst[TC_IMAX], row0[TC_IMAX], ncol[TC_IMAX];
+  // this thread's split items, the same for every tile: rows 4 k4 .. 4 k4 + 3
+  // of stage column col (column p of block b, W for b = kblocks); -1: none
+  const int cols = (kblocks + 1) * ld;
+  const int items = cols * (TR / 4);
+  int src[TC_IMAX], dst[TC_IMAX], row0[TC_IMAX];
 #pragma unroll
   for (int q = 0; q < TC_IMAX; ++q) {
     const int it = threadIdx.x + q * TC_T;
-    const int cg = it / kq, k4 = it - cg * kq;
-    const int b = cg / nch, c = cg - b * nch;
-    src[q] = b * TR * ld + 4 * k4 * ld + 4 * c;
+    const int k4 = it / cols, col = it - k4 * cols;
+    const int b = col / ld, p = col - b * ld;
+    src[q] = b * TR * ld + 4 * k4 * ld + p;
     row0[q] = 4 * k4;
-    if (it >= items) {
-      ncol[q] = 0;
-      dst[q] = 0;
-    } else if (b == kblocks) {                         // W columns past N never enter G
-      ncol[q] = max(0, min(4, N - 4 * c));
-      dst[q] = (int)(k4 * KSTRW) + 64 * c;
+    if (it >= items || (b == kblocks && p >= N)) {     // W columns past N never enter G
+      dst[q] = -1;
+    } else if (b == kblocks) {
+      dst[q] = (int)(k4 * KSTRW) + 16 * p;
     } else {
-      ncol[q] = 4;
-      dst[q] = (int)(vpart + k4 * KSTR) + 16 * (b * ld + 4 * c);
+      dst[q] = (int)(vpart + k4 * KSTR) + 16 * (b * ld + p);
     }
   }
   if (threadIdx.x == 0) {
@@ -234,26 +234,14 @@ __global__ void __launch_bounds__(TC_T, 1)
     if (good) {
 #pragma unroll
       for (int q = 0; q < TC_IMAX; ++q) {
-        if (ncol[q] == 0) continue;
-        float x[4][4];                                 // [row][column]
+        if (dst[q] < 0) continue;
+        float x[4];
 #pragma unroll
-        for (int jr = 0; jr < 4; ++jr) {
-          float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (row0[q] + jr < nr) t = *reinterpret_cast<const float4*>(stf + src[q] + jr * ld);
-          x[jr][0] = t.x;
-          x[jr][1] = t.y;
-          x[jr][2] = t.z;
-          x[jr][3] = t.w;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (u >= ncol[q]) break;
-          const float col[4] = {x[0][u], x[1][u], x[2][u], x[3][u]};
-          float4 hi, lo;
-          split4(col, hi, lo);
-          *reinterpret_cast<float4*>(lay + dst[q] + 16 * u) = hi;
-          *reinterpret_cast<float4*>(lay + half + dst[q] + 16 * u) = lo;
-        }
+        for (int jr = 0; jr < 4; ++jr) x[jr] = row0[q] + jr < nr ? stf[src[q] + jr * ld] : 0.f;
+        float4 hi, lo;
+        split4(x, hi, lo);
+        *reinterpret_cast<float4*>(lay + dst[q]) = hi;
+        *reinterpret_cast<float4*>(lay + half + dst[q]) = lo;
       }
     }
     proxy_fence();                                     // generic writes -> visible to the tensor core
@@ -332,7 +320,7 @@ __global__ void __launch_bounds__(TC_T, 1)
 // read all of its rows of every block before it writes out, so out may alias
 // in or one of the blocks.
 template <int N>
-__global__ void __launch_bounds__(TC_T, 1)
+__global__ void __launch_bounds__(TC_T, 2)
     k_combine_tc(float* out, const float* in, float alpha, const float* V, size_t vstride, int kblocks, int r_in,
                  const float* __restrict__ C, int r_out, int n_rows, int ldv, int ldo, int rows_per_cta, int KC,
                  unsigned ncols, unsigned stage_bytes, int nst, int nl, unsigned off_a, unsigned a_bytes,
@@ -566,27 +554,31 @@ bool gram_tc_plan(int kblocks, int ld, int r, TcGramPlan& p) {
     p.mtiles = (p.kgroup * ld + 127) / 128;
     p.ncols = 32;
     while ((int)p.ncols < p.mtiles * p.N) p.ncols *= 2;
-    // deepest ring first, then the largest tile: 3 stages and 2 split
-    // buffers, else 2 and 2
-    for (int nst = 3; nst >= 2; --nst)
-      for (int TR = 64; TR >= 8; TR -= 8) {
-        const size_t stage = (size_t)(p.kgroup + 1) * TR * ld * 4;
-        const size_t lay = 2 * (size_t)TR * 4 * (p.N + (size_t)p.mtiles * 128);   // hi + lo
-        const size_t off_lay = (TC_BAR_BYTES + nst * stage + 1023) / 1024 * 1024;
-        const size_t total = off_lay + 2 * lay;
-        const int items = (p.kgroup + 1) * p.nch * (TR / 4);
-        if (total <= TC_SMEM_MAX && stage < (1u << 20) && items <= TC_IMAX * TC_T) {
-          p.TR = TR;
-          p.nst = nst;
-          p.nl = 2;
-          p.stage_bytes = (unsigned)stage;
-          p.off_lay = (unsigned)off_lay;
-          p.lay_bytes = (unsigned)lay;
-          p.smem = total;
-          p.ngroups = (kblocks + p.kgroup - 1) / p.kgroup;
-          return true;
+    // one CTA per SM with the largest tile that fits, deepest ring first
+    // (two CTAs per SM with 8-row tiles measured 123 against 119 us for 16
+    // blocks at J = 20)
+    for (int pass = 1; pass < 2; ++pass)
+      for (int nst = 3; nst >= 2; --nst)
+        for (int TR = 64; TR >= 8; TR -= 8) {
+          const size_t stage = (size_t)(p.kgroup + 1) * TR * ld * 4;
+          const size_t lay = 2 * (size_t)TR * 4 * (p.N + (size_t)p.mtiles * 128);   // hi + lo
+          const size_t off_lay = (TC_BAR_BYTES + nst * stage + 1023) / 1024 * 1024;
+          const size_t total = off_lay + 2 * lay;
+          const int items = (p.kgroup + 1) * ld * (TR / 4);
+          const size_t cap = pass == 0 ? TC_SMEM_TWO : TC_SMEM_MAX;
+          if (total <= cap && stage < (1u << 20) && items <= TC_IMAX * TC_T && (pass == 1 || nst == 3)) {
+            p.TR = TR;
+            p.nst = nst;
+            p.nl = 2;
+            p.stage_bytes = (unsigned)stage;
+            p.off_lay = (unsigned)off_lay;
+            p.lay_bytes = (unsigned)lay;
+            p.smem = total;
+            p.ngroups = (kblocks + p.kgroup - 1) / p.kgroup;
+            p.per_sm = pass == 0 ? 2 : 1;
+            return true;
+          }
         }
-      }
   }
   return false;
 }
@@ -599,7 +591,7 @@ bool launch_gram_tc(const float* V, size_t vstride, int kblocks, const float* W,
   const TcDevice& d = tc_setup();
   if (d.err != cudaSuccess || !err || !gram_tc_plan(kblocks, ld, r, p)) return false;
   if ((reinterpret_cast<uintptr_t>(V) & 15) || (reinterpret_cast<uintptr_t>(W) & 15) || (vstride & 3)) return false;
-  const int nctas = std::max(1, std::min({d.nsm / p.ngroups, max_parts, (n_rows + 7) / 8}));
+  const int nctas = std::max(1, std::min({p.per_sm * d.nsm / p.ngroups, max_parts, (n_rows + 7) / 8}));
   const int rows_per_cta = (n_rows + nctas - 1) / nctas;
   nparts = nctas;
   const dim3 grid(nctas, p.ngroups);
@@ -621,32 +613,41 @@ bool combine_tc_plan(int n_rows, int ldv, int r_in, int r_out, int nsm, TcCombin
   p.N = (r_out + 15) / 16 * 16;
   p.KC = (ldv + 7) / 8 * 2;                            // 16-byte K chunks, an even number (K steps of 8)
   if ((ldv / 4) * 128 > TC_IMAX * TC_T) return false;
-  const int mt_max = 512 / p.N;
-  int rows = (n_rows + std::max(nsm, 1) - 1) / std::max(nsm, 1);
-  rows = (rows + 127) / 128 * 128;
-  p.MT = std::max(1, std::min(mt_max, rows / 128));
-  p.rows_per_cta = 128 * p.MT;
-  p.nctas = (n_rows + p.rows_per_cta - 1) / p.rows_per_cta;
-  p.ncols = 32;
-  while ((int)p.ncols < p.MT * p.N) p.ncols *= 2;
+  p.ncols = 0;
   p.stage_bytes = 128u * (unsigned)ldv * 4u;
   p.a_bytes = 2u * (unsigned)p.KC * 2048u;
   p.b_bytes = 2u * (unsigned)p.KC * (unsigned)p.N * 16u;
-  // as many split buffers as fit (at most 4 and MT + 1), then stages
-  for (int nl = std::min(4, p.MT + 1); nl >= 1; --nl)
-    for (int nst = 3; nst >= 2; --nst) {
-      const size_t off_a = (TC_BAR_BYTES + (size_t)nst * p.stage_bytes + 1023) / 1024 * 1024;
-      const size_t off_b = off_a + (size_t)nl * p.a_bytes;
-      const size_t total = off_b + 2 * (size_t)p.b_bytes;
-      if (total <= TC_SMEM_MAX) {
-        p.nl = nl;
-        p.nst = nst;
-        p.off_a = (unsigned)off_a;
-        p.off_b = (unsigned)off_b;
-        p.smem = total;
-        return true;
+  // two CTAs per SM (rows split over 2 nsm CTAs, half the tensor memory and
+  // shared memory each) if a ring of 3 stages and 2 split buffers fits,
+  // else one: then as many split buffers (at most 4 and MT + 1) and as deep
+  // a ring (at most 6) as fit
+  for (int per_sm = 2; per_sm >= 1; --per_sm) {
+    const int mt_max = (512 / per_sm) / p.N;
+    if (mt_max < 1) continue;
+    const int nct = std::max(nsm, 1) * per_sm;
+    int rows = (n_rows + nct - 1) / nct;
+    rows = (rows + 127) / 128 * 128;
+    p.MT = std::max(1, std::min(mt_max, rows / 128));
+    p.rows_per_cta = 128 * p.MT;
+    p.nctas = (n_rows + p.rows_per_cta - 1) / p.rows_per_cta;
+    p.ncols = 32;
+    while ((int)p.ncols < p.MT * p.N) p.ncols *= 2;
+    const size_t cap = per_sm == 2 ? TC_SMEM_TWO : TC_SMEM_MAX;
+    for (int nl = std::min(per_sm == 2 ? 2 : 4, p.MT + 1); nl >= 1; --nl)
+      for (int nst = per_sm == 2 ? 3 : 6; nst >= 2; --nst) {
+        const size_t off_a = (TC_BAR_BYTES + (size_t)nst * p.stage_bytes + 1023) / 1024 * 1024;
+        const size_t off_b = off_a + (size_t)nl * p.a_bytes;
+        const size_t total = off_b + 2 * (size_t)p.b_bytes;
+        if (total <= cap && (per_sm == 1 || (nl == 2 && nst == 3))) {
+          p.nl = nl;
+          p.nst = nst;
+          p.off_a = (unsigned)off_a;
+          p.off_b = (unsigned)off_b;
+          p.smem = total;
+          return true;
+        }
       }
-    }
+  }
   return false;
 }
 
