@@ -332,7 +332,7 @@ void mhde_default_options(mhde_options* o) {
   o->conv_form = 0;
   o->precision = MHDE_PREC_MIXED;
   o->rtol = 0.0;                 // resolved by precision at create
-  o->inner_rtol = 1e-5;
+  o->inner_rtol = 1e-3;
   o->restart = 30;
   o->max_iter = 2000;
   o->max_refine = 60;
