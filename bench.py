@@ -631,10 +631,14 @@ def our_arm(args, rank, world, local_rank):
     achieved = alg / (gram_ms / 1000.0) / 1e9
     # DRAM bytes of one launch of this kernel at this size, from an ncu capture of
     # the same launch configuration; known only for the default workload
+    gram_tc = bool(st1.gram_tensor_cores)
     traffic = GRAM_TRAFFIC if (prec == PREC_MIXED and args.workload == "cavity" and args.N == WORKLOAD["N"]
-                               and args.J == WORKLOAD["J"]
+                               and args.J == WORKLOAD["J"] and not gram_tc
                                and sol.options.restart == 30) else None
-    kname = "k_gram_staged, FP32" if pbytes == 4 else "k_gram, FP64"
+    if pbytes == 8:
+        kname = "k_gram, FP64"
+    else:
+        kname = "k_gram_tc, FP32 on tensor cores" if gram_tc else "k_gram_staged, FP32"
     roofline = {"bound": "hbm", "kernel": f"block Gram partial sums ({kname}), "
                 f"{sol.options.restart // 2 + 1} blocks x {args.J} columns",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -703,7 +707,9 @@ def our_arm(args, rank, world, local_rank):
                 "block_ops_autotune": {"gram": "tensor cores" if st1.gram_tensor_cores else "cuda cores",
                                        "gram_us_cuda_tensor": list(st1.gram_tuned_us),
                                        "combine": "tensor cores" if st1.combine_tensor_cores else "cuda cores",
-                                       "combine_us_cuda_tensor": list(st1.combine_tuned_us)},
+                                       "combine_us_cuda_tensor": list(st1.combine_tuned_us),
+                                       "inner": "persistent" if st1.inner_persistent else "launch chain",
+                                       "inner_us_chain_persistent": list(st1.inner_tuned_us)},
                 "kernel_ms": kernel_ms, "spmm": spmm_line,
                 "wall_ms_per_step": 1000.0 * wall / args.steps}
         if accuracy is not None:

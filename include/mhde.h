@@ -130,6 +130,11 @@ typedef struct {
   double gram_tuned_us[2];    /* its timings of one Gram of restart/2 + 1 blocks: CUDA cores,
                                  tensor cores (0 where not timed) */
   double combine_tuned_us[2]; /* the same for one combination of restart/2 blocks */
+  int inner_persistent;       /* 1 if the bind-time autotuner picked the persistent (one cooperative
+                                 launch, grid barriers) form of the mixed path's inner GMRES on F,
+                                 0 the chain of per-phase launches */
+  double inner_tuned_us[2];   /* its timings of one inner solve: launch chain, persistent
+                                 (0 where not timed) */
 } mhde_stats;
 
 /* Default options (listed above). */
@@ -275,6 +280,16 @@ int mhde_probe_rhs(mhde_ctx* ctx, int which, double* rhs);
  * (x-components, y-components, pressures).  precision: 0 FP64 kernel,
  * 1 FP32 kernel (inputs rounded to float). */
 int mhde_probe_spmm(mhde_ctx* ctx, int which, int precision, const double* X, double* Y);
+
+/* Z ~ F^{-1} R by the mixed path's inner solve of the velocity block (the
+ * preconditioner's per-column GMRES(k) on F D^{-1}, k = options.inner_iters,
+ * zero start, FP32; Section 1 block solvers) for subproblem `which` at the
+ * current step.  R and Z: host [J][2][n2] (member, component, node), R
+ * rounded to float.  form: 0 the chain of per-phase launches, 1 the
+ * persistent cooperative kernel.  MHDE_EINVAL on the FP64 path, with
+ * inner_iters = 0, or for form 1 where the persistent kernel is not
+ * available on this device or size. */
+int mhde_probe_inner(mhde_ctx* ctx, int which, int form, const double* R, double* Z);
 
 /* Average device time in milliseconds of one launch of a hot-path kernel
  * group on the current state of subproblem `which`, from CUDA events on that

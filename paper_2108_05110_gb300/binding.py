@@ -54,7 +54,8 @@ class Stats(C.Structure):
                 ("last_step_ms", C.c_double), ("launches", C.c_longlong),
                 ("spmm_block", C.c_int), ("spmm_tuned_us", C.c_double * 3),
                 ("gram_tensor_cores", C.c_int), ("combine_tensor_cores", C.c_int),
-                ("gram_tuned_us", C.c_double * 2), ("combine_tuned_us", C.c_double * 2)]
+                ("gram_tuned_us", C.c_double * 2), ("combine_tuned_us", C.c_double * 2),
+                ("inner_persistent", C.c_int), ("inner_tuned_us", C.c_double * 2)]
 
 
 def library_path():
@@ -96,6 +97,7 @@ SIGNATURES = {
     "mhde_probe_matrix_F": (C.c_int, [_P, C.c_int, _I, _I, _D]),
     "mhde_probe_rhs": (C.c_int, [_P, C.c_int, _D]),
     "mhde_probe_spmm": (C.c_int, [_P, C.c_int, C.c_int, _D, _D]),
+    "mhde_probe_inner": (C.c_int, [_P, C.c_int, C.c_int, _D, _D]),
     "mhde_time_kernel": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D]),
     "mhde_block_gram_scratch_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "mhde_block_gram": (C.c_int, [_P, C.c_size_t, C.c_int, _P, C.c_int, C.c_int, C.c_int, _P, _P,
@@ -505,6 +507,15 @@ class EnsembleSolver:
         self._check(self.lib.mhde_time_kernel(self.ctx, int(which), int(kernel), int(reps), C.byref(ms)),
                     "mhde_time_kernel")
         return ms.value
+
+    def probe_inner(self, which, R, form=0):
+        """Inner solve of the velocity block (mixed path): R, Z [J][2][n2];
+        form 0 the launch chain, 1 the persistent kernel."""
+        R = _f64(R, (self.J, 2, self.sizes.n2))
+        Z = np.empty_like(R)
+        self._check(self.lib.mhde_probe_inner(self.ctx, int(which), int(form), _dptr(R), _dptr(Z)),
+                    "mhde_probe_inner")
+        return Z
 
     def probe_spmm(self, which, X, precision=0):
         X = _f64(X, (self.J, self.sizes.n_rows))

@@ -114,6 +114,7 @@ size_t layout(mhde_ctx* c, char* base) {
       mk(H.R, D.R, false);
     }
   }
+  c->d_ig_rows = w.take<int>(IG_PMAX + 1);
   c->d_coarse_inv = w.take<double>((size_t)amg.nc * amg.nc);
   c->d_coarse_invf = w.take<float>((size_t)amg.nc * amg.nc);
   c->d_ccross = w.take<double>(Jp);
@@ -169,6 +170,7 @@ size_t layout(mhde_ctx* c, char* base) {
       s.ih = w.take<double>((size_t)(kin + 1) * kin * C2);
       s.ibeta = w.take<double>(4 * C2);                              // beta, 1/norm, float copy of 1/norm
       s.iy = w.take<double>((size_t)kin * C2 * 2);                   // doubles, then a float copy
+      s.ibar = w.take<unsigned>(2);                                  // zero between launches
       s.zbasis = w.take<char>((size_t)m * vs * ks);
     }
     s.amg.assign(amg.levels.size(), DevAmgLevel());
@@ -268,6 +270,66 @@ static int autotune_blockops(mhde_ctx* c) {
   };
   c->gram_tc = pick(c->gram_tuned_us, "MHDE_GRAM_TC");
   c->comb_tc = pick(c->comb_tuned_us, "MHDE_COMB_TC");
+  return MHDE_OK;
+}
+
+// Inner GMRES on F of the mixed path: the persistent form (one cooperative
+// launch, grid barriers) against the launch chain, timed on this context's
+// sizes (subproblem v's buffers and current operator values); the faster is
+// kept.  MHDE_INNER_GRID = 0 or 1 forces the choice.  Both forms compute the
+// same method with the same step count (rounding differs).
+int autotune_inner(mhde_ctx* c) {
+  c->inner_grid = false;
+  c->ig_P = 0;
+  c->inner_tuned_us[0] = c->inner_tuned_us[1] = 0.0;
+  const char* env = std::getenv("MHDE_INNER_GRID");
+  if (c->opt.precision != MHDE_PREC_MIXED || c->opt.inner_iters < 1 || c->opt.inner_fp16 || (env && env[0] == '0'))
+    return MHDE_OK;
+  std::vector<int> rows;
+  const int P = inner_grid_plan(c, rows);
+  if (P <= 0) return MHDE_OK;
+  Sub& s = c->sub[0];
+  cudaStream_t st = c->sv;
+  CU(cudaMemcpyAsync(c->d_ig_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  c->ig_P = P;
+  const float* r = (const float*)s.Tk;
+  float* z = (float*)s.Pk;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(c, MHDE_ECUDA, "cudaEventCreate failed in the inner-solve autotuner");
+  }
+  const long long launches0 = launch_count();
+  bool launched = true;
+  for (int form = 0; form < 2; ++form) {
+    c->inner_grid = form == 1;
+    auto once = [&]() {
+      launch_inner_gmres<float>(c, s, s.FDf, s.Fdinvf, r, z, c->Jp, c->opt.inner_iters, st, false);
+    };
+    once();
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 5; ++rep) once();
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) launched = false;
+    c->inner_tuned_us[form] = 1000.0 * ms / 5;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  count_launch(-(launch_count() - launches0));   // not part of any step
+  const int aerr = take_async_error(s.d_err, st);
+  if (!launched || aerr != 0 || cudaGetLastError() != cudaSuccess) {
+    // the persistent form did not run (or gave up at a barrier): keep the chain
+    c->inner_grid = false;
+    c->ig_P = 0;
+    c->inner_tuned_us[1] = 0.0;
+    return MHDE_OK;
+  }
+  if (env && env[0] == '1')
+    c->inner_grid = true;
+  else
+    c->inner_grid = c->inner_tuned_us[1] > 0.0 && c->inner_tuned_us[1] < c->inner_tuned_us[0];
   return MHDE_OK;
 }
 
@@ -476,6 +538,7 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   CU(upload_quad_tables());
   CU(upload_adjoint_tables());
   CU(init_inner_attributes());
+  CU(init_inner_grid_attributes());
   CU(init_la_attributes());
   const FeHost& fe = c->fe;
   cudaStream_t st = c->sv;
@@ -566,6 +629,10 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   }
   {
     int rc = autotune_blockops(c);
+    if (rc) return rc;
+  }
+  {
+    int rc = autotune_inner(c);
     if (rc) return rc;
   }
   return MHDE_OK;
@@ -695,7 +762,8 @@ static int run_sub(mhde_ctx* c, int which) {
     } else if (take_async_error(s.d_err, s.stream) != 0) {
       // a Gram launch gave up waiting for a TMA stage (bounded wait): the
       // solve used incomplete projections, so the step is not accepted
-      s.err = "a block Gram launch timed out waiting for its shared-memory stage";
+      s.err = "a bounded wait gave up (a block Gram or combination waiting for its shared-memory stage, "
+              "or a grid barrier of the inner solve)";
       rc = MHDE_ECUDA;
     }
   }
@@ -920,7 +988,9 @@ int mhde_get_stats(const mhde_ctx* c, mhde_stats* st) {
   for (int i = 0; i < 2; ++i) {
     st->gram_tuned_us[i] = c->gram_tuned_us[i];
     st->combine_tuned_us[i] = c->comb_tuned_us[i];
+    st->inner_tuned_us[i] = c->inner_tuned_us[i];
   }
+  st->inner_persistent = c->inner_grid ? 1 : 0;
   return MHDE_OK;
 }
 
@@ -1039,6 +1109,39 @@ int mhde_probe_rhs(mhde_ctx* c, int which, double* rhs) {
   for (int j = 0; j < J; ++j)
     for (int k = 0; k < n2; ++k)
       for (int d = 0; d < 2; ++d) rhs[((size_t)j * n2 + k) * 2 + d] = buf[((size_t)k * 2 + d) * Jp + j];
+  return MHDE_OK;
+}
+
+int mhde_probe_inner(mhde_ctx* c, int which, int form, const double* R, double* Z) {
+  int rc = probe_assemble(c, which);
+  if (rc) return rc;
+  if (!R || !Z || (form != 0 && form != 1)) return fail(c, MHDE_EINVAL, "R or Z is NULL, or form not 0/1");
+  if (c->opt.precision != MHDE_PREC_MIXED || c->opt.inner_iters < 1)
+    return fail(c, MHDE_EINVAL, "the inner solve probe needs the mixed path with inner_iters >= 1");
+  if (form == 1 && c->ig_P <= 0) return fail(c, MHDE_EINVAL, "the persistent inner solve is not available here");
+  const int n2 = c->fe.n2, J = c->J, Jp = c->Jp;
+  const size_t nv = (size_t)2 * n2 * Jp;
+  std::vector<float> buf(nv, 0.f);
+  for (int j = 0; j < J; ++j)
+    for (int d = 0; d < 2; ++d)
+      for (int k = 0; k < n2; ++k) buf[((size_t)k * 2 + d) * Jp + j] = (float)R[((size_t)j * 2 + d) * n2 + k];
+  Sub& s = c->sub[which];
+  float* dr = (float*)s.Tk;
+  float* dz = (float*)s.Pk;
+  CU(cudaStreamSynchronize(c->sv));
+  CU(cudaStreamSynchronize(s.stream));
+  CU(cudaMemcpy(dr, buf.data(), nv * sizeof(float), cudaMemcpyHostToDevice));
+  const bool keep = c->inner_grid;
+  c->inner_grid = form == 1;
+  launch_inner_gmres<float>(c, s, s.FDf, s.Fdinvf, dr, dz, Jp, c->opt.inner_iters, s.stream, false);
+  c->inner_grid = keep;
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s.stream));
+  if (take_async_error(s.d_err, s.stream) != 0) return fail(c, MHDE_ECUDA, "inner solve probe: a bounded wait gave up");
+  CU(cudaMemcpy(buf.data(), dz, nv * sizeof(float), cudaMemcpyDeviceToHost));
+  for (int j = 0; j < J; ++j)
+    for (int d = 0; d < 2; ++d)
+      for (int k = 0; k < n2; ++k) Z[((size_t)j * 2 + d) * n2 + k] = buf[((size_t)k * 2 + d) * Jp + j];
   return MHDE_OK;
 }
 

@@ -179,8 +179,15 @@ void launch_Np(const mhde_ctx* c, const double* mean_conv, double* slots, double
 template <typename T>
 void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* dinv, const T* r, T* z, int ld,
                         int kin, cudaStream_t st, bool allow_half = true);
+// the persistent form (kernels_inner_grid.cu) on the FP32 path: grid size
+// and row ranges for a context (0: not applicable), and the launch (false:
+// not launched, use the chain)
+int inner_grid_plan(const mhde_ctx* c, std::vector<int>& row_start);
+bool launch_inner_grid(const mhde_ctx* c, const Sub& s, const float* FDv, const float* dinv, const float* r,
+                       float* z, int ld, int kin, cudaStream_t st);
 // shared-memory limits of the inner and block kernels (set once, before any capture)
 cudaError_t init_inner_attributes();
+cudaError_t init_inner_grid_attributes();
 cudaError_t init_la_attributes();
 // solver entry points (solver.cu)
 int assemble_sub(mhde_ctx* c, int which);

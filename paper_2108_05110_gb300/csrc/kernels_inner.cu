@@ -462,6 +462,9 @@ void launch_inner_gmres(const mhde_ctx* c, const Sub& s, const T* FDv, const T* 
       inner_gmres<float, __half>(c, s, FDv, dinv, r, z, ld, kin, st);
       return;
     }
+    // the persistent form (kernels_inner_grid.cu) where the bind-time
+    // autotuner found it faster
+    if (c->inner_grid && launch_inner_grid(c, s, FDv, dinv, r, z, ld, kin, st)) return;
   }
   inner_gmres<T, T>(c, s, FDv, dinv, r, z, ld, kin, st);
 }

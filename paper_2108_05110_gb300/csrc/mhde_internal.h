@@ -19,6 +19,7 @@ constexpr int NQ = 7;        // quadrature points per triangle (degree-5 rule)
 constexpr int NLOC = 6;      // P2 nodes per triangle
 constexpr int MAX_J = 64;    // members per ensemble handled by the small dense kernels
 constexpr int KIN_MAX = 16;  // longest inner GMRES on F
+constexpr int IG_PMAX = 512;  // largest grid of the persistent inner GMRES
 
 // ----------------------------------------------------------------- host FE data
 struct HostCsr {
@@ -179,12 +180,14 @@ struct Sub {                       // one subproblem (v: which = 0, w: which = 1
   double* ih = nullptr;            // inner Hessenberg [kin+1][kin][2 Jp]
   double* ibeta = nullptr;         // [2 Jp] initial norms, then [2 Jp] inverse norms
   double* iy = nullptr;            // inner least-squares solutions [kin][2 Jp]
+  unsigned* ibar = nullptr;        // grid-barrier counters of the persistent inner GMRES [2]
   void* zbasis = nullptr;          // flexible GMRES: preconditioned basis m x [n_rows][Jp]
   // captured preconditioner graphs keyed by (input, output) device pointers
   std::map<std::tuple<const void*, const void*, int>, std::pair<cudaGraphExec_t, long long>> prec_graphs;
   // stats
   int iters = 0, refine = 0;
   int graphs_built = 0;
+  bool graphs_off = false;         // a capture failed: the preconditioner runs uncaptured from then on
   double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // MHDE_TRACE: assemble, residual, precond, spmm, cgs, normalise
   double relres = 0.0;
   int status = 0;
@@ -271,6 +274,13 @@ struct mhde_ctx {
   bool gram_tc = false, comb_tc = false;
   double gram_tuned_us[2] = {0, 0};    // CUDA cores, tensor cores
   double comb_tuned_us[2] = {0, 0};
+  // mixed-path inner GMRES: persistent cooperative kernel (ig_P CTAs, row
+  // ranges d_ig_rows; 0 CTAs where it does not apply) or the launch chain,
+  // picked at bind by timing both
+  bool inner_grid = false;
+  int ig_P = 0;
+  int* d_ig_rows = nullptr;            // [IG_PMAX + 1]
+  double inner_tuned_us[2] = {0, 0};   // launch chain, persistent
   mhde::Sub sub[2];
   std::vector<int> h_bidx;             // boundary index of every P2 node (host copy)
   std::vector<double> h_M;             // mass matrix values (host copy, for the energy)

@@ -184,7 +184,7 @@ static std::mutex g_capture_mutex;
 
 template <typename T>
 static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out, int ld) {
-  if (!c->use_graphs) {
+  if (!c->use_graphs || s.graphs_off) {
     apply_prec_raw<T>(c, s, in, out, ld);
     return;
   }
@@ -208,6 +208,7 @@ static void apply_prec(const mhde_ctx* c, Sub& s, const T* in, T* out, int ld) {
         cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
+      s.graphs_off = true;   // do not retry a capture that failed once
       apply_prec_raw<T>(c, s, in, out, ld);
       return;
     }
