@@ -29,9 +29,7 @@ namespace {
 
 constexpr int TC_T = 256;                        // 8 warps
 constexpr size_t TC_SMEM_MAX = 225 * 1024;
-constexpr size_t TC_SMEM_TWO = 110 * 1024;       // two CTAs per SM below this
 constexpr unsigned TC_BAR_BYTES = 1024;          // mbarriers and the TMEM address slot
-constexpr int TC_IMAX = 8;                       // split items per thread and tile
 constexpr long long TC_SPIN = 1ll << 24;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -137,14 +135,43 @@ __device__ __forceinline__ void split4(const float x[4], float4& hi, float4& lo)
 // is a GEMM contracting over the mesh rows: A = [V_0 | ... | V_{k-1}]
 // (stacked columns m = i ld + p, M = 128 per tile), B = W (N = r padded to
 // 16..64), K = rows.  The grid is (row ranges) x (groups of blocks whose
-// accumulators fit 256 TMEM columns).  A stage holds TR rows of every block
-// and of W (TMA bulk copies); its split transposes 4 rows of one column per
-// item into one K chunk of the layout (consecutive threads take consecutive
-// columns, so neither the reads nor the writes conflict in shared-memory
-// banks): per buffer, a W part (TR/4 K slices of N columns) and a V part
-// (TR/4 K slices of mtiles * 128 columns), hi then lo.
+// accumulators fit 256 TMEM columns).
+//
+// Warp-specialised pipeline, one CTA per SM, no CTA-wide barrier in the
+// main loop:
+//   warp 0      fills a ring of nst stages (TR rows of every block and of W)
+//               with TMA bulk copies, each stage reused once the split warps
+//               have released it (mbarrier `empty`);
+//   warps 2..7  split a landed stage into one of nl operand buffers in the
+//               canonical K-major layout, hi then lo (4 rows of one column per
+//               item: consecutive threads take consecutive columns, so
+//               neither the reads nor the writes conflict in shared-memory
+//               banks), once the MMAs that last read that buffer completed
+//               (mbarrier `lempty`, arrived by tcgen05.commit), then release
+//               the stage and hand the buffer over (mbarrier `lfull`);
+//   warp 1      allocates the tensor memory and, on one lane, issues the
+//               3 mtiles TR/8 MMAs of each buffer and commits them.
+// All 8 warps read the accumulators out at the end.  A wait that gives up
+// raises a shared abort flag that the other roles poll, so every role
+// leaves its loop; the CTA then records the failure, waits (bounded) for
+// the copies and MMAs it has in flight, frees its tensor memory and returns.
+constexpr int GW_SPLIT = 6;                      // split warps
+constexpr int GW_IMAX = 16;                      // split items per split thread and tile
+
+__device__ __forceinline__ void bar_arrive(unsigned bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+// bounded wait that also gives up once another role has raised the abort flag
+__device__ __forceinline__ bool bar_wait_ab(unsigned bar, unsigned parity, const volatile int* abort_flag) {
+  for (long long it = 0; it < TC_SPIN; ++it) {
+    if (bar_try(bar, parity)) return true;
+    if ((it & 255) == 255 && *abort_flag) return false;
+  }
+  return false;
+}
+
 template <int N>
-__global__ void __launch_bounds__(TC_T, 2)
+__global__ void __launch_bounds__(TC_T, 1)
     k_gram_tc(const float* __restrict__ V, size_t vstride, int kb_total, int kgroup, const float* __restrict__ Wm,
               int n_rows, int ld, int r, int rows_per_cta, int TR, int mtiles, unsigned ncols, unsigned stage_bytes,
               int nst, int nl, unsigned off_lay, unsigned lay_bytes, double* __restrict__ part,
@@ -156,9 +183,13 @@ __global__ void __launch_bounds__(TC_T, 2)
   V += (size_t)b0 * vstride;
   extern __shared__ __align__(1024) unsigned char tsm[];
   const unsigned base = su32(tsm);
-  const unsigned bar_load = base;                      // nst barriers (<= 8)
-  const unsigned bar_mma = base + 64;                  // nl barriers (<= 4), one phase per tile of the buffer
-  unsigned* tmem_slot = reinterpret_cast<unsigned*>(tsm + 128);
+  const unsigned bar_full = base;                      // nst (<= 8) stage landed
+  const unsigned bar_empty = base + 64;                // nst stage released by the split warps
+  const unsigned bar_lfull = base + 128;               // nl (<= 4) operand buffer written
+  const unsigned bar_lempty = base + 160;              // nl operand buffer read by its MMAs
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(tsm + 192);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + 196);
+  volatile int* progress = reinterpret_cast<volatile int*>(tsm + 200);   // tiles issued, split, committed
   const int r0 = blockIdx.x * rows_per_cta, r1 = min(n_rows, r0 + rows_per_cta);
   const int ntiles = r1 > r0 ? (r1 - r0 + TR - 1) / TR : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -171,69 +202,110 @@ __global__ void __launch_bounds__(TC_T, 2)
   const unsigned KSTR = (unsigned)mtiles * 2048u;      // bytes per K slice of the V part
   const unsigned vpart = (unsigned)(TR / 4) * KSTRW;
   const unsigned half = lay_bytes / 2;                 // lo after hi
-  // this thread's split items, the same for every tile: rows 4 k4 .. 4 k4 + 3
-  // of stage column col (column p of block b, W for b = kblocks); -1: none
-  const int cols = (kblocks + 1) * ld;
-  const int items = cols * (TR / 4);
-  int src[TC_IMAX], dst[TC_IMAX], row0[TC_IMAX];
-#pragma unroll
-  for (int q = 0; q < TC_IMAX; ++q) {
-    const int it = threadIdx.x + q * TC_T;
-    const int k4 = it / cols, col = it - k4 * cols;
-    const int b = col / ld, p = col - b * ld;
-    src[q] = b * TR * ld + 4 * k4 * ld + p;
-    row0[q] = 4 * k4;
-    if (it >= items || (b == kblocks && p >= N)) {     // W columns past N never enter G
-      dst[q] = -1;
-    } else if (b == kblocks) {
-      dst[q] = (int)(k4 * KSTRW) + 16 * p;
-    } else {
-      dst[q] = (int)(vpart + k4 * KSTR) + 16 * (b * ld + p);
-    }
-  }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < nst; ++s) bar_init(bar_load + 8 * s, 1);
-    for (int j = 0; j < nl; ++j) bar_init(bar_mma + 8 * j, 1);
+    for (int s = 0; s < nst; ++s) {
+      bar_init(bar_full + 8 * s, 1);
+      bar_init(bar_empty + 8 * s, GW_SPLIT);
+    }
+    for (int j = 0; j < nl; ++j) {
+      bar_init(bar_lfull + 8 * j, GW_SPLIT);
+      bar_init(bar_lempty + 8 * j, 1);
+    }
+    *abort_flag = 0;
+    progress[0] = progress[1] = progress[2] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     proxy_fence();
   }
-  if (warp == 0) tmem_alloc(su32(tmem_slot), ncols);
+  if (warp == 1) tmem_alloc(su32(tmem_slot), ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = *tmem_slot;
 
-  // warp 0 fills a stage: kblocks + 1 contiguous spans of nr * ld floats
-  auto issue = [&](int tile) {
-    if (tile >= ntiles) return;
-    const int s = tile % nst;
-    const unsigned st = base + TC_BAR_BYTES + (unsigned)s * stage_bytes;
-    const int t0 = r0 + tile * TR;
-    const unsigned bytes = (unsigned)(min(TR, r1 - t0) * ld) * 4u;
-    proxy_fence();                                     // the stage was last read through the generic proxy
-    if (lane == 0) bar_expect_tx(bar_load + 8 * s, bytes * (unsigned)(kblocks + 1));
-    __syncwarp();
-    for (int b = lane; b <= kblocks; b += 32) {
-      const float* g = (b < kblocks ? V + (size_t)b * vstride : Wm) + (size_t)t0 * ld;
-      bulk_load(st + (unsigned)(b * TR * ld) * 4u, g, bytes, bar_load + 8 * s);
+  if (warp == 0) {
+    // ---- producer: kblocks + 1 contiguous spans of nr * ld floats per stage
+    for (int tile = 0; tile < ntiles; ++tile) {
+      const int s = tile % nst;
+      if (tile >= nst && !bar_wait_ab(bar_empty + 8 * s, (unsigned)((tile / nst - 1) & 1), abort_flag)) {
+        if (lane == 0) *abort_flag = 1;
+        break;
+      }
+      const unsigned st = base + TC_BAR_BYTES + (unsigned)s * stage_bytes;
+      const int t0 = r0 + tile * TR;
+      const unsigned bytes = (unsigned)(min(TR, r1 - t0) * ld) * 4u;
+      proxy_fence();                                   // the stage was last read through the generic proxy
+      if (lane == 0) bar_expect_tx(bar_full + 8 * s, bytes * (unsigned)(kblocks + 1));
+      __syncwarp();
+      for (int b = lane; b <= kblocks; b += 32) {
+        const float* g = (b < kblocks ? V + (size_t)b * vstride : Wm) + (size_t)t0 * ld;
+        bulk_load(st + (unsigned)(b * TR * ld) * 4u, g, bytes, bar_full + 8 * s);
+      }
+      if (lane == 0) progress[0] = tile + 1;
     }
-  };
-  if (warp == 0)
-    for (int s = 0; s < nst; ++s) issue(s);
-
-  const uint32_t idesc = idesc_tf32(128, N);
-  int ok = 1, landed = 0;
-  for (int tile = 0; tile < ntiles; ++tile) {
-    const int s = tile % nst, j = tile % nl;
-    bool good = bar_wait(bar_load + 8 * s, (unsigned)((tile / nst) & 1));
-    if (good && tile >= nl) good = bar_wait(bar_mma + 8 * j, (unsigned)((tile / nl - 1) & 1));   // buffer free
-    tc_fence_after();
-    const float* stf = reinterpret_cast<const float*>(tsm + TC_BAR_BYTES + (size_t)s * stage_bytes);
-    unsigned char* lay = tsm + off_lay + (size_t)j * lay_bytes;
-    const int nr = min(TR, r1 - (r0 + tile * TR));
-    if (good) {
+  } else if (warp == 1) {
+    // ---- MMA issue: per buffer, per M tile, per K step of 8: hi*hi + hi*lo + lo*hi
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(128, N);
+      for (int tile = 0; tile < ntiles; ++tile) {
+        const int j = tile % nl;
+        if (!bar_wait_ab(bar_lfull + 8 * j, (unsigned)((tile / nl) & 1), abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const unsigned hi = base + off_lay + (unsigned)j * lay_bytes, lo = hi + half;
+        for (int t = 0; t < mtiles; ++t)
+          for (int k8 = 0; k8 < TR / 8; ++k8) {
+            // leading (K) offset between the two 4-row K chunks of the step,
+            // stride offset between groups of 8 columns
+            const unsigned aoff = vpart + (unsigned)(2 * k8) * KSTR + (unsigned)t * 2048u;
+            const unsigned boff = (unsigned)(2 * k8) * KSTRW;
+            mma_split3(tmem + (unsigned)(t * N), kdesc(hi + aoff, KSTR, 128u), kdesc(lo + aoff, KSTR, 128u),
+                       kdesc(hi + boff, KSTRW, 128u), kdesc(lo + boff, KSTRW, 128u), idesc,
+                       (tile > 0 || k8 > 0) ? 1 : 0);
+          }
+        mma_commit(bar_lempty + 8 * j);
+        progress[2] = tile + 1;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- split: this thread's items, the same for every tile: rows
+    // 4 k4 .. 4 k4 + 3 of stage column col (column p of block b, W for
+    // b = kblocks); -1: none
+    const int sid = threadIdx.x - 64;
+    const int cols = (kblocks + 1) * ld;
+    const int items = cols * (TR / 4);
+    int src[GW_IMAX], dst[GW_IMAX], row0[GW_IMAX];
 #pragma unroll
-      for (int q = 0; q < TC_IMAX; ++q) {
+    for (int q = 0; q < GW_IMAX; ++q) {
+      const int it = sid + q * 32 * GW_SPLIT;
+      const int k4 = it / cols, col = it - k4 * cols;
+      const int b = col / ld, p = col - b * ld;
+      src[q] = b * TR * ld + 4 * k4 * ld + p;
+      row0[q] = 4 * k4;
+      if (it >= items || (b == kblocks && p >= N)) {   // W columns past N never enter G
+        dst[q] = -1;
+      } else if (b == kblocks) {
+        dst[q] = (int)(k4 * KSTRW) + 16 * p;
+      } else {
+        dst[q] = (int)(vpart + k4 * KSTR) + 16 * (b * ld + p);
+      }
+    }
+    for (int tile = 0; tile < ntiles; ++tile) {
+      const int s = tile % nst, j = tile % nl;
+      bool good = bar_wait_ab(bar_full + 8 * s, (unsigned)((tile / nst) & 1), abort_flag);
+      if (good && tile >= nl) good = bar_wait_ab(bar_lempty + 8 * j, (unsigned)((tile / nl - 1) & 1), abort_flag);
+      if (!good) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const float* stf = reinterpret_cast<const float*>(tsm + TC_BAR_BYTES + (size_t)s * stage_bytes);
+      unsigned char* lay = tsm + off_lay + (size_t)j * lay_bytes;
+      const int nr = min(TR, r1 - (r0 + tile * TR));
+#pragma unroll
+      for (int q = 0; q < GW_IMAX; ++q) {
         if (dst[q] < 0) continue;
         float x[4];
 #pragma unroll
@@ -243,64 +315,51 @@ __global__ void __launch_bounds__(TC_T, 2)
         *reinterpret_cast<float4*>(lay + dst[q]) = hi;
         *reinterpret_cast<float4*>(lay + half + dst[q]) = lo;
       }
-    }
-    proxy_fence();                                     // generic writes -> visible to the tensor core
-    tc_fence_before();
-    if (!__syncthreads_and(good ? 1 : 0)) {
-      ok = 0;
-      break;
-    }
-    landed = tile + 1;
-    if (warp == 0) issue(tile + nst);                  // the stage has been consumed
-    if (threadIdx.x == 32) {
-      tc_fence_after();
-      const unsigned hi = base + off_lay + (unsigned)j * lay_bytes, lo = hi + half;
-      for (int t = 0; t < mtiles; ++t)
-        for (int k8 = 0; k8 < TR / 8; ++k8) {
-          // leading (K) offset between the two 4-row K chunks of the step,
-          // stride offset between groups of 8 columns
-          const unsigned aoff = vpart + (unsigned)(2 * k8) * KSTR + (unsigned)t * 2048u;
-          const unsigned boff = (unsigned)(2 * k8) * KSTRW;
-          mma_split3(tmem + (unsigned)(t * N), kdesc(hi + aoff, KSTR, 128u), kdesc(lo + aoff, KSTR, 128u),
-                     kdesc(hi + boff, KSTRW, 128u), kdesc(lo + boff, KSTRW, 128u), idesc, (tile > 0 || k8 > 0) ? 1 : 0);
-        }
-      mma_commit(bar_mma + 8 * j);
-    }
-  }
-  if (ok) {
-    // the last tile's MMAs complete after all earlier ones
-    const int lt = ntiles - 1;
-    ok = __syncthreads_and(bar_wait(bar_mma + 8 * (lt % nl), (unsigned)((lt / nl) & 1)) ? 1 : 0);
-    tc_fence_after();
-    if (ok) {
-      const int q4 = warp & 3, grp = warp >> 2;        // TMEM lanes 32 q4 .. 32 q4 + 31
-      for (int t = grp; t < mtiles; t += TC_T / 128) {
-        float v[N];
-        const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(t * N);
-#pragma unroll
-        for (int c16 = 0; c16 < N / 16; ++c16) tmem_ld16(taddr + 16 * c16, v + 16 * c16);
-        const int m = 128 * t + 32 * q4 + lane;        // stacked column of the V blocks
-        const int b = m / ld, p = m - b * ld;
-        if (b < kblocks && p < r) {
-          double* d = part + (((size_t)blockIdx.x * kb_total + b0 + b) * r + p) * r;
-#pragma unroll
-          for (int q = 0; q < N; ++q)
-            if (q < r) d[q] = (double)v[q];
-        }
+      proxy_fence();                                   // generic writes -> visible to the tensor core
+      __syncwarp();
+      if (lane == 0) {
+        bar_arrive(bar_lfull + 8 * j);
+        bar_arrive(bar_empty + 8 * s);
+        if (warp == 2) progress[1] = tile + 1;
       }
     }
   }
-  if (!ok && threadIdx.x == 0) {
+  __syncthreads();
+  // the last buffer's commit completes after all earlier MMAs
+  int good = *abort_flag == 0;
+  if (good) {
+    const int lt = ntiles - 1;
+    good = bar_wait(bar_lempty + 8 * (lt % nl), (unsigned)((lt / nl) & 1)) ? 1 : 0;
+  }
+  good = __syncthreads_and(good);
+  if (good) {
+    tc_fence_after();
+    const int q4 = warp & 3, grp = warp >> 2;          // TMEM lanes 32 q4 .. 32 q4 + 31
+    for (int t = grp; t < mtiles; t += TC_T / 128) {
+      float v[N];
+      const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(t * N);
+#pragma unroll
+      for (int c16 = 0; c16 < N / 16; ++c16) tmem_ld16(taddr + 16 * c16, v + 16 * c16);
+      const int m = 128 * t + 32 * q4 + lane;          // stacked column of the V blocks
+      const int b = m / ld, p = m - b * ld;
+      if (b < kblocks && p < r) {
+        double* d = part + (((size_t)blockIdx.x * kb_total + b0 + b) * r + p) * r;
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+          if (q < r) d[q] = (double)v[q];
+      }
+    }
+  } else if (threadIdx.x == 0) {
     // a wait gave up: record it, let every copy and MMA in flight finish
     // (bounded), and leave without partial sums
     atomicExch(err, 1);
-    for (int tl = landed; tl < min(ntiles, landed + nst); ++tl)
-      bar_wait(bar_load + 8 * (tl % nst), (unsigned)((tl / nst) & 1));
-    if (landed > 0) bar_wait(bar_mma + 8 * ((landed - 1) % nl), (unsigned)(((landed - 1) / nl) & 1));
+    const int issued = progress[0], taken = progress[1], committed = progress[2];
+    for (int tl = taken; tl < issued; ++tl) bar_wait(bar_full + 8 * (tl % nst), (unsigned)((tl / nst) & 1));
+    if (committed > 0) bar_wait(bar_lempty + 8 * ((committed - 1) % nl), (unsigned)(((committed - 1) / nl) & 1));
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
     tmem_free(tmem, ncols);
   }
@@ -310,49 +369,73 @@ __global__ void __launch_bounds__(TC_T, 2)
 // out[row][q] = alpha in[row][q] + sum_i sum_p V_i[row][p] C_i[p][q]  (q < r_out,
 // zero up to ldo): the new Krylov block and the solution update of the block
 // GMRES.  A GEMM with M = rows, K = (block, column) and N = r_out padded to
-// 16..64: A = the V row tiles, B = the coefficient blocks.  A CTA owns up to
-// MT tiles of 128 rows with their accumulators in tensor memory (MT N <= 512
-// columns) and walks stage s = (block i, row tile t) in block order: one TMA
-// bulk copy of 128 rows into a ring of nst stages, their split into one of
-// nl A buffers (element (m, p) at (p/4) 2048 + m 16 + (p%4) 4), and 3 MMAs per
-// K step of 8.  Coefficient block i is split into buffer i % 2 (element (q,
-// p) at (p/4) N 16 + q 16 + (p%4) 4) at the block's first tile.  The CTA has
-// read all of its rows of every block before it writes out, so out may alias
-// in or one of the blocks.
+// 16..64: A = the V row tiles, B = the coefficient blocks.  A CTA (one per
+// SM) owns a row range, walked in groups of up to MT tiles of 128 rows whose
+// accumulators sit in tensor memory (MT N <= 512 columns); within a group
+// the stages s = (block i, row tile t) run in block order.  Same warp roles
+// as the Gram:
+//   warp 0      one TMA bulk copy of 128 rows per stage into a ring of nst;
+//   warps 2..7  split a landed stage into one of nl A buffers (element (m, p)
+//               at (p/4) 2048 + m 16 + (p%4) 4), and at a block's first tile
+//               its coefficients into B buffer (block sequence number) % 2
+//               (element (q, p) at (p/4) N 16 + q 16 + (p%4) 4), each buffer
+//               reused once the MMAs that read it completed (mbarriers
+//               aempty / bempty, arrived by tcgen05.commit);
+//   warp 1      3 MMAs per K step of 8 into the tile's accumulator, a commit
+//               per stage and one per block.
+// At the end of a group, warps 2..5 (one per quarter of the 128 TMEM lanes)
+// write out alpha in + the accumulators and release the tensor memory to
+// the next group (mbarrier tfree).  The CTA has read all rows of a group in
+// every block before it writes them, so out may alias in or one of the
+// blocks.  Waits are bounded as in the Gram.
 template <int N>
-__global__ void __launch_bounds__(TC_T, 2)
+__global__ void __launch_bounds__(TC_T, 1)
     k_combine_tc(float* out, const float* in, float alpha, const float* V, size_t vstride, int kblocks, int r_in,
                  const float* __restrict__ C, int r_out, int n_rows, int ldv, int ldo, int rows_per_cta, int KC,
-                 unsigned ncols, unsigned stage_bytes, int nst, int nl, unsigned off_a, unsigned a_bytes,
+                 int MT, unsigned ncols, unsigned stage_bytes, int nst, int nl, unsigned off_a, unsigned a_bytes,
                  unsigned off_b, unsigned b_bytes, int* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(1024) unsigned char tsm[];
   const unsigned base = su32(tsm);
-  const unsigned bar_load = base;                      // nst barriers (<= 8)
-  const unsigned bar_mma = base + 64;                  // nl barriers (<= 4)
-  unsigned* tmem_slot = reinterpret_cast<unsigned*>(tsm + 128);
+  const unsigned bar_full = base;                      // nst (<= 8)
+  const unsigned bar_empty = base + 64;                // nst
+  const unsigned bar_afull = base + 128;               // nl (<= 4)
+  const unsigned bar_aempty = base + 160;              // nl
+  const unsigned bar_bempty = base + 192;              // 2
+  const unsigned bar_tfree = base + 208;               // 1
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(tsm + 216);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + 220);
+  volatile int* progress = reinterpret_cast<volatile int*>(tsm + 224);   // stages issued, split, committed
   const int r0 = blockIdx.x * rows_per_cta, r1 = min(n_rows, r0 + rows_per_cta);
   if (r1 <= r0) return;
-  const int MT = (r1 - r0 + 127) / 128;                // row tiles of this CTA
-  const int nstages = kblocks * MT;
-  const int warp = threadIdx.x >> 5;
+  const int T = (r1 - r0 + 127) / 128;                 // row tiles of this CTA
+  const int nstages = kblocks * T;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = ldv / 4;                             // 16-byte chunks of a V row
   const unsigned ahalf = a_bytes / 2, bhalf = b_bytes / 2;
-  // this thread's split items of a row tile: (chunk k4, row m)
-  int src[TC_IMAX], dst[TC_IMAX], mrow[TC_IMAX], ncol[TC_IMAX];
-#pragma unroll
-  for (int q = 0; q < TC_IMAX; ++q) {
-    const int it = threadIdx.x + q * TC_T;
-    const int k4 = it >> 7, m = it & 127;
-    src[q] = m * ldv + 4 * k4;
-    dst[q] = k4 * 2048 + m * 16;
-    mrow[q] = m;
-    ncol[q] = it < nch * 128 ? max(0, min(4, r_in - 4 * k4)) : -1;   // -1: no item; columns past r_in are 0
-  }
+  // stage sidx -> group g, block i, tile t of the group (mt tiles in it)
+  auto decode = [&](int sidx, int& g, int& i, int& t, int& mt) {
+    g = sidx / (kblocks * MT);
+    const int rem = sidx - g * kblocks * MT;
+    mt = min(MT, T - g * MT);
+    i = rem / mt;
+    t = rem - i * mt;
+  };
   if (threadIdx.x == 0) {
-    for (int s = 0; s < nst; ++s) bar_init(bar_load + 8 * s, 1);
-    for (int j = 0; j < nl; ++j) bar_init(bar_mma + 8 * j, 1);
+    for (int s = 0; s < nst; ++s) {
+      bar_init(bar_full + 8 * s, 1);
+      bar_init(bar_empty + 8 * s, GW_SPLIT);
+    }
+    for (int j = 0; j < nl; ++j) {
+      bar_init(bar_afull + 8 * j, GW_SPLIT);
+      bar_init(bar_aempty + 8 * j, 1);
+    }
+    bar_init(bar_bempty, 1);
+    bar_init(bar_bempty + 8, 1);
+    bar_init(bar_tfree, 4);
+    *abort_flag = 0;
+    progress[0] = progress[1] = progress[2] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     proxy_fence();
   }
@@ -364,60 +447,113 @@ __global__ void __launch_bounds__(TC_T, 2)
     *reinterpret_cast<float4*>(a) = make_float4(0.f, 0.f, 0.f, 0.f);
     *reinterpret_cast<float4*>(a + ahalf) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (warp == 0) tmem_alloc(su32(tmem_slot), ncols);
+  if (warp == 1) tmem_alloc(su32(tmem_slot), ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = *tmem_slot;
-
-  auto issue = [&](int sidx) {                         // stage sidx = (block i, row tile t)
-    if (sidx >= nstages) return;
-    const int i = sidx / MT, t = sidx - i * MT;
-    const int t0 = r0 + 128 * t;
-    const unsigned bytes = (unsigned)(min(128, r1 - t0) * ldv) * 4u;
-    const unsigned bar = bar_load + 8 * (sidx % nst);
-    proxy_fence();
-    bar_expect_tx(bar, bytes);
-    bulk_load(base + TC_BAR_BYTES + (unsigned)(sidx % nst) * stage_bytes, V + (size_t)i * vstride + (size_t)t0 * ldv,
-              bytes, bar);
-  };
-  if (threadIdx.x == 0)
-    for (int s = 0; s < nst; ++s) issue(s);
-
-  const uint32_t idesc = idesc_tf32(128, N);
   const unsigned bstride = (unsigned)N * 16u;          // between K chunks of a coefficient buffer
-  int ok = 1, landed = 0;
-  for (int sidx = 0; sidx < nstages; ++sidx) {
-    const int i = sidx / MT, t = sidx - i * MT, j = sidx % nl;
-    bool good = bar_wait(bar_load + 8 * (sidx % nst), (unsigned)((sidx / nst) & 1));
-    // A buffer j is free once the MMAs of stage sidx - nl completed; in order,
-    // so are those of block i - 2 (nl <= MT + 1), whose coefficient buffer
-    // block i reuses
-    if (good && sidx >= nl) good = bar_wait(bar_mma + 8 * j, (unsigned)((sidx / nl - 1) & 1));
-    tc_fence_after();
-    const unsigned bsel = off_b + (unsigned)(i & 1) * b_bytes;
-    if (good && t == 0) {
-      for (int e = threadIdx.x; e < KC * N; e += TC_T) {
-        const int k4 = e / N, q = e - k4 * N;
-        float cv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int pp = 4 * k4 + u;
-          cv[u] = (pp < r_in && q < r_out) ? C[((size_t)i * r_in + pp) * r_out + q] : 0.f;
+
+  if (warp == 0) {
+    // ---- producer
+    if (lane == 0) {
+      for (int sidx = 0; sidx < nstages; ++sidx) {
+        const int s = sidx % nst;
+        if (sidx >= nst && !bar_wait_ab(bar_empty + 8 * s, (unsigned)((sidx / nst - 1) & 1), abort_flag)) {
+          *abort_flag = 1;
+          break;
         }
-        float4 hi, lo;
-        split4(cv, hi, lo);
-        const size_t o = (size_t)k4 * bstride + (size_t)q * 16;
-        *reinterpret_cast<float4*>(tsm + bsel + o) = hi;
-        *reinterpret_cast<float4*>(tsm + bsel + bhalf + o) = lo;
+        int g, i, t, mt;
+        decode(sidx, g, i, t, mt);
+        const int t0 = r0 + 128 * (g * MT + t);
+        const unsigned bytes = (unsigned)(min(128, r1 - t0) * ldv) * 4u;
+        proxy_fence();
+        bar_expect_tx(bar_full + 8 * s, bytes);
+        bulk_load(base + TC_BAR_BYTES + (unsigned)s * stage_bytes, V + (size_t)i * vstride + (size_t)t0 * ldv, bytes,
+                  bar_full + 8 * s);
+        progress[0] = sidx + 1;
       }
     }
-    if (good) {
-      const float* stf = reinterpret_cast<const float*>(tsm + TC_BAR_BYTES + (size_t)(sidx % nst) * stage_bytes);
-      unsigned char* a = tsm + off_a + (size_t)j * a_bytes;
-      const int nr = min(128, r1 - (r0 + 128 * t));
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(128, N);
+      for (int sidx = 0; sidx < nstages; ++sidx) {
+        int g, i, t, mt;
+        decode(sidx, g, i, t, mt);
+        const int j = sidx % nl, bs = g * kblocks + i;
+        // the tensor memory of group g - 1 has been written out
+        bool good = true;
+        if (g > 0 && i == 0 && t == 0) good = bar_wait_ab(bar_tfree, (unsigned)((g - 1) & 1), abort_flag);
+        if (good) good = bar_wait_ab(bar_afull + 8 * j, (unsigned)((sidx / nl) & 1), abort_flag);
+        if (!good) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const unsigned ahi = base + off_a + (unsigned)j * a_bytes, alo = ahi + ahalf;
+        const unsigned bhi = base + off_b + (unsigned)(bs & 1) * b_bytes, blo = bhi + bhalf;
+        const unsigned d = tmem + (unsigned)(t * N);
+        for (int k8 = 0; k8 < KC / 2; ++k8)
+          mma_split3(d, kdesc(ahi + (unsigned)k8 * 4096u, 2048u, 128u), kdesc(alo + (unsigned)k8 * 4096u, 2048u, 128u),
+                     kdesc(bhi + (unsigned)k8 * 2u * bstride, bstride, 128u),
+                     kdesc(blo + (unsigned)k8 * 2u * bstride, bstride, 128u), idesc, (i > 0 || k8 > 0) ? 1 : 0);
+        mma_commit(bar_aempty + 8 * j);
+        if (t == mt - 1) mma_commit(bar_bempty + 8 * (bs & 1));   // the block's coefficients are free
+        progress[2] = sidx + 1;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- split (warps 2..7); warps 2..5 also write out each group
+    const int sid = threadIdx.x - 64;
+    int src[GW_IMAX], dst[GW_IMAX], mrow[GW_IMAX], ncol[GW_IMAX];
 #pragma unroll
-      for (int q = 0; q < TC_IMAX; ++q) {
+    for (int q = 0; q < GW_IMAX; ++q) {
+      const int it = sid + q * 32 * GW_SPLIT;
+      const int k4 = it >> 7, m = it & 127;
+      src[q] = m * ldv + 4 * k4;
+      dst[q] = k4 * 2048 + m * 16;
+      mrow[q] = m;
+      ncol[q] = it < nch * 128 ? max(0, min(4, r_in - 4 * k4)) : -1;   // -1: no item; columns past r_in are 0
+    }
+    const bool writer = warp >= 2 && warp <= 5;
+    for (int sidx = 0; sidx < nstages; ++sidx) {
+      int g, i, t, mt;
+      decode(sidx, g, i, t, mt);
+      const int s = sidx % nst, j = sidx % nl, bs = g * kblocks + i;
+      bool good = bar_wait_ab(bar_full + 8 * s, (unsigned)((sidx / nst) & 1), abort_flag);
+      if (good && sidx >= nl) good = bar_wait_ab(bar_aempty + 8 * j, (unsigned)((sidx / nl - 1) & 1), abort_flag);
+      if (good && t == 0 && bs >= 2)
+        good = bar_wait_ab(bar_bempty + 8 * (bs & 1), (unsigned)((bs / 2 - 1) & 1), abort_flag);
+      if (!good) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      if (t == 0) {
+        const unsigned bsel = off_b + (unsigned)(bs & 1) * b_bytes;
+        for (int e = sid; e < KC * N; e += 32 * GW_SPLIT) {
+          const int k4 = e / N, q = e - k4 * N;
+          float cv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int pp = 4 * k4 + u;
+            cv[u] = (pp < r_in && q < r_out) ? C[((size_t)i * r_in + pp) * r_out + q] : 0.f;
+          }
+          float4 hi, lo;
+          split4(cv, hi, lo);
+          const size_t o = (size_t)k4 * bstride + (size_t)q * 16;
+          *reinterpret_cast<float4*>(tsm + bsel + o) = hi;
+          *reinterpret_cast<float4*>(tsm + bsel + bhalf + o) = lo;
+        }
+      }
+      const float* stf = reinterpret_cast<const float*>(tsm + TC_BAR_BYTES + (size_t)s * stage_bytes);
+      unsigned char* a = tsm + off_a + (size_t)j * a_bytes;
+      const int nr = min(128, r1 - (r0 + 128 * (g * MT + t)));
+#pragma unroll
+      for (int q = 0; q < GW_IMAX; ++q) {
         if (ncol[q] < 0) continue;
         float x[4] = {0.f, 0.f, 0.f, 0.f};
         if (mrow[q] < nr) {
@@ -435,69 +571,65 @@ __global__ void __launch_bounds__(TC_T, 2)
         *reinterpret_cast<float4*>(a + dst[q]) = hi;
         *reinterpret_cast<float4*>(a + ahalf + dst[q]) = lo;
       }
-    }
-    proxy_fence();
-    tc_fence_before();
-    if (!__syncthreads_and(good ? 1 : 0)) {
-      ok = 0;
-      break;
-    }
-    landed = sidx + 1;
-    if (threadIdx.x == 0) issue(sidx + nst);           // the stage has been consumed
-    if (threadIdx.x == 32) {
-      tc_fence_after();
-      const unsigned ahi = base + off_a + (unsigned)j * a_bytes, alo = ahi + ahalf;
-      const unsigned bhi = base + bsel, blo = bhi + bhalf;
-      const unsigned d = tmem + (unsigned)(t * N);
-      for (int k8 = 0; k8 < KC / 2; ++k8)
-        mma_split3(d, kdesc(ahi + (unsigned)k8 * 4096u, 2048u, 128u), kdesc(alo + (unsigned)k8 * 4096u, 2048u, 128u),
-                   kdesc(bhi + (unsigned)k8 * 2u * bstride, bstride, 128u),
-                   kdesc(blo + (unsigned)k8 * 2u * bstride, bstride, 128u), idesc, (i > 0 || k8 > 0) ? 1 : 0);
-      mma_commit(bar_mma + 8 * j);
-    }
-  }
-  if (ok) {
-    const int ls = nstages - 1;
-    ok = __syncthreads_and(bar_wait(bar_mma + 8 * (ls % nl), (unsigned)((ls / nl) & 1)) ? 1 : 0);
-    tc_fence_after();
-    if (ok) {
-      const int q4 = warp & 3, grp = warp >> 2, lane = threadIdx.x & 31;
-      for (int t = grp; t < MT; t += TC_T / 128) {
-        float v[N];
-        const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(t * N);
-#pragma unroll
-        for (int c16 = 0; c16 < N / 16; ++c16) tmem_ld16(taddr + 16 * c16, v + 16 * c16);
-        const int row = r0 + 128 * t + 32 * q4 + lane;
-        if (row < r1) {
-          float* orow = out + (size_t)row * ldo;
-          const float* irow = in ? in + (size_t)row * ldo : nullptr;
-#pragma unroll
-          for (int q = 0; q < N; q += 4) {
-            if (q < ldo) {
-              float4 i4 = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (irow) i4 = *reinterpret_cast<const float4*>(irow + q);
-              float4 o4;
-              o4.x = q + 0 < r_out ? alpha * i4.x + v[q + 0] : 0.f;
-              o4.y = q + 1 < r_out ? alpha * i4.y + v[q + 1] : 0.f;
-              o4.z = q + 2 < r_out ? alpha * i4.z + v[q + 2] : 0.f;
-              o4.w = q + 3 < r_out ? alpha * i4.w + v[q + 3] : 0.f;
-              *reinterpret_cast<float4*>(orow + q) = o4;
-            }
-          }
-          for (int q = N; q < ldo; q += 4) *reinterpret_cast<float4*>(orow + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+      proxy_fence();                                   // generic writes -> visible to the tensor core
+      __syncwarp();
+      if (lane == 0) {
+        bar_arrive(bar_afull + 8 * j);
+        bar_arrive(bar_empty + 8 * s);
+        if (warp == 2) progress[1] = sidx + 1;
+      }
+      if (writer && i == kblocks - 1 && t == mt - 1) {
+        // ---- the group's last stage: once its MMAs (and so all of the
+        // group's) completed, write the group's rows out
+        if (!bar_wait_ab(bar_aempty + 8 * j, (unsigned)((sidx / nl) & 1), abort_flag)) {
+          *abort_flag = 1;
+          break;
         }
+        tc_fence_after();
+        const int q4 = warp & 3;                       // TMEM lanes 32 q4 .. 32 q4 + 31
+        for (int tt = 0; tt < mt; ++tt) {
+          float v[N];
+          const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(tt * N);
+#pragma unroll
+          for (int c16 = 0; c16 < N / 16; ++c16) tmem_ld16(taddr + 16 * c16, v + 16 * c16);
+          const int row = r0 + 128 * (g * MT + tt) + 32 * q4 + lane;
+          if (row < r1) {
+            float* orow = out + (size_t)row * ldo;
+            const float* irow = in ? in + (size_t)row * ldo : nullptr;
+#pragma unroll
+            for (int q = 0; q < N; q += 4) {
+              if (q < ldo) {
+                float4 i4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (irow) i4 = *reinterpret_cast<const float4*>(irow + q);
+                float4 o4;
+                o4.x = q + 0 < r_out ? alpha * i4.x + v[q + 0] : 0.f;
+                o4.y = q + 1 < r_out ? alpha * i4.y + v[q + 1] : 0.f;
+                o4.z = q + 2 < r_out ? alpha * i4.z + v[q + 2] : 0.f;
+                o4.w = q + 3 < r_out ? alpha * i4.w + v[q + 3] : 0.f;
+                *reinterpret_cast<float4*>(orow + q) = o4;
+              }
+            }
+            for (int q = N; q < ldo; q += 4) *reinterpret_cast<float4*>(orow + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(bar_tfree);
       }
     }
   }
-  if (!ok && threadIdx.x == 0) {
+  __syncthreads();
+  if (*abort_flag != 0 && threadIdx.x == 0) {
+    // a wait gave up: record it, let every copy and MMA in flight finish
+    // (bounded), and leave (out is not valid)
     atomicExch(err, 1);
-    for (int sl = landed; sl < min(nstages, landed + nst); ++sl)
-      bar_wait(bar_load + 8 * (sl % nst), (unsigned)((sl / nst) & 1));
-    if (landed > 0) bar_wait(bar_mma + 8 * ((landed - 1) % nl), (unsigned)(((landed - 1) / nl) & 1));
+    const int issued = progress[0], taken = progress[1], committed = progress[2];
+    for (int sl = taken; sl < issued; ++sl) bar_wait(bar_full + 8 * (sl % nst), (unsigned)((sl / nst) & 1));
+    if (committed > 0) bar_wait(bar_aempty + 8 * ((committed - 1) % nl), (unsigned)(((committed - 1) / nl) & 1));
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
     tmem_free(tmem, ncols);
   }
@@ -546,39 +678,35 @@ bool gram_tc_plan(int kblocks, int ld, int r, TcGramPlan& p) {
   p.nch = ld / 4;
   p.N = (r + 15) / 16 * 16;
   // blocks per CTA: their accumulators (M tiles of 128 stacked columns, N
-  // columns each) fit 256 TMEM columns, so two CTAs on one SM never wait
-  // for each other's tensor memory
+  // columns each) fit 256 TMEM columns
   p.kgroup = std::min(kblocks, std::max(1, (256 / p.N) * 128 / ld));
   while (p.kgroup > 1 && ((p.kgroup * ld + 127) / 128) * p.N > 256) --p.kgroup;
   for (; p.kgroup >= 1; --p.kgroup) {
     p.mtiles = (p.kgroup * ld + 127) / 128;
     p.ncols = 32;
     while ((int)p.ncols < p.mtiles * p.N) p.ncols *= 2;
-    // one CTA per SM with the largest tile that fits, deepest ring first
-    // (two CTAs per SM with 8-row tiles measured 123 against 119 us for 16
-    // blocks at J = 20)
-    for (int pass = 1; pass < 2; ++pass)
-      for (int nst = 3; nst >= 2; --nst)
-        for (int TR = 64; TR >= 8; TR -= 8) {
-          const size_t stage = (size_t)(p.kgroup + 1) * TR * ld * 4;
-          const size_t lay = 2 * (size_t)TR * 4 * (p.N + (size_t)p.mtiles * 128);   // hi + lo
-          const size_t off_lay = (TC_BAR_BYTES + nst * stage + 1023) / 1024 * 1024;
-          const size_t total = off_lay + 2 * lay;
-          const int items = (p.kgroup + 1) * ld * (TR / 4);
-          const size_t cap = pass == 0 ? TC_SMEM_TWO : TC_SMEM_MAX;
-          if (total <= cap && stage < (1u << 20) && items <= TC_IMAX * TC_T && (pass == 1 || nst == 3)) {
-            p.TR = TR;
-            p.nst = nst;
-            p.nl = 2;
-            p.stage_bytes = (unsigned)stage;
-            p.off_lay = (unsigned)off_lay;
-            p.lay_bytes = (unsigned)lay;
-            p.smem = total;
-            p.ngroups = (kblocks + p.kgroup - 1) / p.kgroup;
-            p.per_sm = pass == 0 ? 2 : 1;
-            return true;
-          }
+    // one CTA per SM, two operand buffers; the largest tile that leaves a
+    // ring of at least three stages, the deepest ring (at most 6) for it
+    for (int TR = 32; TR >= 8; TR -= 8)
+      for (int nst = 6; nst >= 3; --nst) {
+        const size_t stage = (size_t)(p.kgroup + 1) * TR * ld * 4;
+        const size_t lay = 2 * (size_t)TR * 4 * (p.N + (size_t)p.mtiles * 128);   // hi + lo
+        const size_t off_lay = (TC_BAR_BYTES + nst * stage + 1023) / 1024 * 1024;
+        const size_t total = off_lay + 2 * lay;
+        const int items = (p.kgroup + 1) * ld * (TR / 4);
+        if (total <= TC_SMEM_MAX && stage < (1u << 20) && items <= GW_IMAX * GW_SPLIT * 32) {
+          p.TR = TR;
+          p.nst = nst;
+          p.nl = 2;
+          p.stage_bytes = (unsigned)stage;
+          p.off_lay = (unsigned)off_lay;
+          p.lay_bytes = (unsigned)lay;
+          p.smem = total;
+          p.ngroups = (kblocks + p.kgroup - 1) / p.kgroup;
+          p.per_sm = 1;
+          return true;
         }
+      }
   }
   return false;
 }
@@ -612,33 +740,29 @@ bool combine_tc_plan(int n_rows, int ldv, int r_in, int r_out, int nsm, TcCombin
   if (r_in < 1 || r_out < 1 || r_out > 64 || ldv < r_in || ldv % 4 != 0 || ldv > 64 || n_rows < 1) return false;
   p.N = (r_out + 15) / 16 * 16;
   p.KC = (ldv + 7) / 8 * 2;                            // 16-byte K chunks, an even number (K steps of 8)
-  if ((ldv / 4) * 128 > TC_IMAX * TC_T) return false;
-  p.ncols = 0;
+  if ((ldv / 4) * 128 > GW_IMAX * GW_SPLIT * 32) return false;
   p.stage_bytes = 128u * (unsigned)ldv * 4u;
   p.a_bytes = 2u * (unsigned)p.KC * 2048u;
   p.b_bytes = 2u * (unsigned)p.KC * (unsigned)p.N * 16u;
-  // two CTAs per SM (rows split over 2 nsm CTAs, half the tensor memory and
-  // shared memory each) if a ring of 3 stages and 2 split buffers fits,
-  // else one: then as many split buffers (at most 4 and MT + 1) and as deep
-  // a ring (at most 6) as fit
-  for (int per_sm = 2; per_sm >= 1; --per_sm) {
-    const int mt_max = (512 / per_sm) / p.N;
-    if (mt_max < 1) continue;
-    const int nct = std::max(nsm, 1) * per_sm;
-    int rows = (n_rows + nct - 1) / nct;
-    rows = (rows + 127) / 128 * 128;
-    p.MT = std::max(1, std::min(mt_max, rows / 128));
-    p.rows_per_cta = 128 * p.MT;
-    p.nctas = (n_rows + p.rows_per_cta - 1) / p.rows_per_cta;
-    p.ncols = 32;
-    while ((int)p.ncols < p.MT * p.N) p.ncols *= 2;
-    const size_t cap = per_sm == 2 ? TC_SMEM_TWO : TC_SMEM_MAX;
-    for (int nl = std::min(per_sm == 2 ? 2 : 4, p.MT + 1); nl >= 1; --nl)
-      for (int nst = per_sm == 2 ? 3 : 6; nst >= 2; --nst) {
+  // one CTA per SM over an even share of the row tiles, walked in groups of
+  // MT tiles (MT N <= 512 tensor-memory columns)
+  const int tiles = (n_rows + 127) / 128;
+  const int per_cta = (tiles + std::max(nsm, 1) - 1) / std::max(nsm, 1);
+  p.rows_per_cta = 128 * per_cta;
+  p.nctas = (tiles + per_cta - 1) / per_cta;
+  p.MT = std::max(1, std::min(512 / p.N, per_cta));
+  p.ncols = 32;
+  while ((int)p.ncols < p.MT * p.N) p.ncols *= 2;
+  // as many A buffers (at most 4) and as deep a ring (at most 8) as fit,
+  // preferring two A buffers and three stages first
+  for (int pass = 0; pass < 2; ++pass)
+    for (int nl = 4; nl >= 1; --nl)
+      for (int nst = 8; nst >= 2; --nst) {
+        if (pass == 0 && (nl < 2 || nst < 3)) continue;
         const size_t off_a = (TC_BAR_BYTES + (size_t)nst * p.stage_bytes + 1023) / 1024 * 1024;
         const size_t off_b = off_a + (size_t)nl * p.a_bytes;
         const size_t total = off_b + 2 * (size_t)p.b_bytes;
-        if (total <= cap && (per_sm == 1 || (nl == 2 && nst == 3))) {
+        if (total <= TC_SMEM_MAX) {
           p.nl = nl;
           p.nst = nst;
           p.off_a = (unsigned)off_a;
@@ -647,7 +771,6 @@ bool combine_tc_plan(int n_rows, int ldv, int r_in, int r_out, int nsm, TcCombin
           return true;
         }
       }
-  }
   return false;
 }
 
@@ -662,7 +785,7 @@ bool launch_combine_tc(float* out, const float* in, float alpha, const float* V,
     return false;
 #define MHDE_TCC(NN)                                                                                              \
   launch_pdl(k_combine_tc<NN>, dim3(p.nctas), dim3(TC_T), p.smem, st, out, in, alpha, V, vstride, kblocks, r_in, C, \
-             r_out, n_rows, ldv, ldo, p.rows_per_cta, p.KC, p.ncols, p.stage_bytes, p.nst, p.nl, p.off_a,          \
+             r_out, n_rows, ldv, ldo, p.rows_per_cta, p.KC, p.MT, p.ncols, p.stage_bytes, p.nst, p.nl, p.off_a,    \
              p.a_bytes, p.off_b, p.b_bytes, err)
   switch (p.N) {
     case 16: MHDE_TCC(16); break;

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 # n_rows, ldv, r_in, r_out, ldo, kblocks
 CASES = [(148739, 20, 20, 20, 20, 16), (148739, 20, 20, 20, 20, 31), (177747, 52, 50, 50, 52, 16),
          (5003, 24, 23, 17, 20, 3), (129, 8, 5, 7, 8, 2), (700, 4, 3, 3, 4, 1), (1000, 64, 60, 40, 40, 2),
-         (40000, 20, 20, 20, 20, 1)]
+         (40000, 20, 20, 20, 20, 1), (400000, 20, 20, 20, 20, 5)]
 
 
 def _tol(nterms):
