@@ -125,7 +125,9 @@ typedef struct {
   double spmm_tuned_us[3];    /* its timings of one SpMM at 128, 256, 512 */
   int gram_tensor_cores;      /* 1 if the bind-time autotuner picked the tensor-core (tcgen05)
                                  kernel for the FP32 block Gram of the mixed path, 0 the
-                                 CUDA-core kernel (results agree to FP32 rounding) */
+                                 CUDA-core kernel; the tensor-core products are split TF32
+                                 (about 2^-21 relative against FP32's 2^-24), so that form is
+                                 picked only when it is at least 1.25x faster */
   int combine_tensor_cores;   /* the same choice for the FP32 block combination */
   double gram_tuned_us[2];    /* its timings of one Gram of restart/2 + 1 blocks: CUDA cores,
                                  tensor cores (0 where not timed) */

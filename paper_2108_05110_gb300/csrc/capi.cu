@@ -218,9 +218,13 @@ void to_rows(const mhde_ctx* c, const double* a, const double* b, double sgn, do
 // still zero at bind time; the access pattern and traffic are the real ones.
 // FP32 block Gram and block combination of the mixed path: time the
 // CUDA-core and the tensor-core kernels on this context's sizes (restart/2
-// basis blocks of the zeroed workspace; values do not change the timing) and
-// keep the faster; MHDE_GRAM_TC / MHDE_COMB_TC = 0 or 1 force the choice.
-// Both give the same results up to FP32 rounding.
+// basis blocks of the zeroed workspace; values do not change the timing);
+// MHDE_GRAM_TC / MHDE_COMB_TC = 0 or 1 force the choice.  The tensor-core
+// products carry relative errors of about 2^-21 (split TF32) against FP32's
+// 2^-24, and the Cholesky QR of the projected Gram feels that: on the
+// 128 x 128 cavity ensemble (J = 20) a 1.15x faster tensor-core Gram raised
+// the block iterations per step from 328 to 352.  So a tensor-core form is
+// kept only when it is at least 1.25x faster than the CUDA-core one.
 static int autotune_blockops(mhde_ctx* c) {
   c->gram_tc = c->comb_tc = false;
   if (c->opt.precision != MHDE_PREC_MIXED) return MHDE_OK;
@@ -266,7 +270,7 @@ static int autotune_blockops(mhde_ctx* c) {
     return fail(c, MHDE_ECUDA, "block-operation autotuner: a kernel failed");
   auto pick = [](const double us[2], const char* env) {
     if (const char* e = std::getenv(env)) return e[0] == '1';
-    return us[1] > 0.0 && (us[0] <= 0.0 || us[1] < us[0]);
+    return us[1] > 0.0 && (us[0] <= 0.0 || us[1] * 1.25 < us[0]);
   };
   c->gram_tc = pick(c->gram_tuned_us, "MHDE_GRAM_TC");
   c->comb_tc = pick(c->comb_tuned_us, "MHDE_COMB_TC");

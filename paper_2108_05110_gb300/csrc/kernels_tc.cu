@@ -8,7 +8,11 @@
 // x is split into hi = x with the low 13 mantissa bits cleared (exact in
 // TF32) and lo = x - hi (exact in FP32), and hi*hi + hi*lo + lo*hi is
 // accumulated: the dropped lo*lo term and the TF32 rounding of lo leave a
-// relative error of about 2^-21 per product.  Operands reach shared memory
+// relative error of about 2^-21 per product.  The B operand holds hi and lo
+// side by side along N, so two instructions per K step do it: A_hi [B_hi |
+// B_lo] into 2N accumulator columns and A_lo B_hi into the first N; the
+// epilogue adds the two halves.  (Issue of one instruction costs about as
+// much at N = 32 as at N = 64, so this is a third fewer than three.)  Operands reach shared memory
 // by TMA bulk copies (row-major, a ring of stages); all threads then write
 // the split operands in the canonical K-major no-swizzle layout (core
 // matrices of 8 rows x 16 bytes, 128 contiguous bytes), double-buffered so
@@ -27,7 +31,7 @@
 namespace mhde {
 namespace {
 
-constexpr int TC_T = 256;                        // 8 warps
+constexpr int TC_T = 320;                        // 10 warps: producer, MMA, 8 split warps
 constexpr size_t TC_SMEM_MAX = 225 * 1024;
 constexpr unsigned TC_BAR_BYTES = 1024;          // mbarriers and the TMEM address slot
 constexpr long long TC_SPIN = 1ll << 24;
@@ -86,13 +90,6 @@ __device__ __forceinline__ void mma_tf32(unsigned d_tmem, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-// hi*hi + hi*lo + lo*hi into d
-__device__ __forceinline__ void mma_split3(unsigned d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl,
-                                           uint32_t idesc, int accumulate) {
-  mma_tf32(d, ah, bh, idesc, accumulate);
-  mma_tf32(d, ah, bl, idesc, 1);
-  mma_tf32(d, al, bh, idesc, 1);
-}
 __device__ __forceinline__ void mma_commit(unsigned bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
 }
@@ -133,29 +130,31 @@ __device__ __forceinline__ void split4(const float x[4], float4& hi, float4& lo)
 // ------------------------------------------------------------ block Gram
 //   G_i[p][q] = sum_rows V_i[row][p] W[row][q],   i < kblocks,  p, q < r
 // is a GEMM contracting over the mesh rows: A = [V_0 | ... | V_{k-1}]
-// (stacked columns m = i ld + p, M = 128 per tile), B = W (N = r padded to
-// 16..64), K = rows.  The grid is (row ranges) x (groups of blocks whose
-// accumulators fit 256 TMEM columns).
+// (stacked columns m = i ld + p, M = 128 per tile), B = [W_hi | W_lo]
+// (2N rows: W padded to N = 16..64 columns, hi then lo), K = rows.  Per K
+// step and M tile, A_hi B into 2N accumulator columns and A_lo W_hi into
+// the first N.  The grid is (row ranges) x (groups of blocks whose
+// accumulators fit the 512 TMEM columns).
 //
 // Warp-specialised pipeline, one CTA per SM, no CTA-wide barrier in the
 // main loop:
 //   warp 0      fills a ring of nst stages (TR rows of every block and of W)
 //               with TMA bulk copies, each stage reused once the split warps
 //               have released it (mbarrier `empty`);
-//   warps 2..7  split a landed stage into one of nl operand buffers in the
-//               canonical K-major layout, hi then lo (4 rows of one column per
-//               item: consecutive threads take consecutive columns, so
-//               neither the reads nor the writes conflict in shared-memory
-//               banks), once the MMAs that last read that buffer completed
-//               (mbarrier `lempty`, arrived by tcgen05.commit), then release
-//               the stage and hand the buffer over (mbarrier `lfull`);
+//   warps 2..9  split a landed stage into one of nl operand buffers in the
+//               canonical K-major layout (4 rows of one column per item:
+//               consecutive threads take consecutive columns, so neither the
+//               reads nor the writes conflict in shared-memory banks), once
+//               the MMAs that last read that buffer completed (mbarrier
+//               `lempty`, arrived by tcgen05.commit), then release the stage
+//               and hand the buffer over (mbarrier `lfull`);
 //   warp 1      allocates the tensor memory and, on one lane, issues the
-//               3 mtiles TR/8 MMAs of each buffer and commits them.
-// All 8 warps read the accumulators out at the end.  A wait that gives up
+//               MMAs of each buffer and commits them.
+// Warps 0..7 read the accumulators out at the end.  A wait that gives up
 // raises a shared abort flag that the other roles poll, so every role
 // leaves its loop; the CTA then records the failure, waits (bounded) for
 // the copies and MMAs it has in flight, frees its tensor memory and returns.
-constexpr int GW_SPLIT = 6;                      // split warps
+constexpr int GW_SPLIT = 8;                      // split warps (2 .. 9)
 constexpr int GW_IMAX = 16;                      // split items per split thread and tile
 
 __device__ __forceinline__ void bar_arrive(unsigned bar) {
@@ -198,10 +197,10 @@ __global__ void __launch_bounds__(TC_T, 1)
       part[((size_t)blockIdx.x * kb_total + b0) * r * r + e] = 0.0;
     return;
   }
-  const unsigned KSTRW = (unsigned)N * 16u;            // bytes per K slice of the W part
+  const unsigned KSTRW = (unsigned)N * 32u;            // bytes per K slice of the W part: N hi rows, N lo rows
   const unsigned KSTR = (unsigned)mtiles * 2048u;      // bytes per K slice of the V part
-  const unsigned vpart = (unsigned)(TR / 4) * KSTRW;
-  const unsigned half = lay_bytes / 2;                 // lo after hi
+  const unsigned vpart = (unsigned)(TR / 4) * KSTRW;   // V hi, then V lo
+  const unsigned vlo = (unsigned)(TR / 4) * KSTR;
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
       bar_init(bar_full + 8 * s, 1);
@@ -243,9 +242,17 @@ __global__ void __launch_bounds__(TC_T, 1)
       if (lane == 0) progress[0] = tile + 1;
     }
   } else if (warp == 1) {
-    // ---- MMA issue: per buffer, per M tile, per K step of 8: hi*hi + hi*lo + lo*hi
+    // ---- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(128, N);
+      const uint32_t idesc2 = idesc_tf32(128, 2 * N), idesc1 = idesc_tf32(128, N);
+      // descriptors of buffer 0; every other operand is the same descriptor
+      // with its start address advanced (the 14-bit address field cannot
+      // overflow inside the CTA's shared memory): leading (K) offset between
+      // the two 4-row K slices of a step, stride offset between groups of 8
+      // rows
+      const uint64_t dA0 = kdesc(base + off_lay + vpart, KSTR, 128u);
+      const uint64_t dB0 = kdesc(base + off_lay, KSTRW, 128u);
+      const uint64_t dlo = (uint64_t)(vlo >> 4);
       for (int tile = 0; tile < ntiles; ++tile) {
         const int j = tile % nl;
         if (!bar_wait_ab(bar_lfull + 8 * j, (unsigned)((tile / nl) & 1), abort_flag)) {
@@ -253,17 +260,18 @@ __global__ void __launch_bounds__(TC_T, 1)
           break;
         }
         tc_fence_after();
-        const unsigned hi = base + off_lay + (unsigned)j * lay_bytes, lo = hi + half;
-        for (int t = 0; t < mtiles; ++t)
-          for (int k8 = 0; k8 < TR / 8; ++k8) {
-            // leading (K) offset between the two 4-row K chunks of the step,
-            // stride offset between groups of 8 columns
-            const unsigned aoff = vpart + (unsigned)(2 * k8) * KSTR + (unsigned)t * 2048u;
-            const unsigned boff = (unsigned)(2 * k8) * KSTRW;
-            mma_split3(tmem + (unsigned)(t * N), kdesc(hi + aoff, KSTR, 128u), kdesc(lo + aoff, KSTR, 128u),
-                       kdesc(hi + boff, KSTRW, 128u), kdesc(lo + boff, KSTRW, 128u), idesc,
-                       (tile > 0 || k8 > 0) ? 1 : 0);
+        const uint64_t dj = (uint64_t)(((unsigned)j * lay_bytes) >> 4);
+        for (int k8 = 0; k8 < TR / 8; ++k8) {
+          const uint64_t bk = dB0 + dj + (uint64_t)(((unsigned)(2 * k8) * KSTRW) >> 4);
+          const uint64_t ak = dA0 + dj + (uint64_t)(((unsigned)(2 * k8) * KSTR) >> 4);
+          const int acc = (tile > 0 || k8 > 0) ? 1 : 0;
+          for (int t = 0; t < mtiles; ++t) {
+            const uint64_t at = ak + (uint64_t)(t * 128);          // 2048 bytes per M tile
+            const unsigned d = tmem + (unsigned)(t * 2 * N);
+            mma_tf32(d, at, bk, idesc2, acc);                      // A_hi [W_hi | W_lo]
+            mma_tf32(d, at + dlo, bk, idesc1, 1);                  // A_lo W_hi
           }
+        }
         mma_commit(bar_lempty + 8 * j);
         progress[2] = tile + 1;
       }
@@ -276,7 +284,8 @@ __global__ void __launch_bounds__(TC_T, 1)
     const int sid = threadIdx.x - 64;
     const int cols = (kblocks + 1) * ld;
     const int items = cols * (TR / 4);
-    int src[GW_IMAX], dst[GW_IMAX], row0[GW_IMAX];
+    int src[GW_IMAX], dst[GW_IMAX], row0[GW_IMAX], dlo[GW_IMAX];
+    const int nq = (items - sid + 32 * GW_SPLIT - 1) / (32 * GW_SPLIT);   // items of this thread
 #pragma unroll
     for (int q = 0; q < GW_IMAX; ++q) {
       const int it = sid + q * 32 * GW_SPLIT;
@@ -284,6 +293,7 @@ __global__ void __launch_bounds__(TC_T, 1)
       const int b = col / ld, p = col - b * ld;
       src[q] = b * TR * ld + 4 * k4 * ld + p;
       row0[q] = 4 * k4;
+      dlo[q] = b == kblocks ? 16 * N : (int)vlo;      // lo beside hi along N (W), or the V lo part
       if (it >= items || (b == kblocks && p >= N)) {   // W columns past N never enter G
         dst[q] = -1;
       } else if (b == kblocks) {
@@ -304,16 +314,24 @@ __global__ void __launch_bounds__(TC_T, 1)
       const float* stf = reinterpret_cast<const float*>(tsm + TC_BAR_BYTES + (size_t)s * stage_bytes);
       unsigned char* lay = tsm + off_lay + (size_t)j * lay_bytes;
       const int nr = min(TR, r1 - (r0 + tile * TR));
+      // four items at a time: their sixteen loads are in flight together
 #pragma unroll
-      for (int q = 0; q < GW_IMAX; ++q) {
-        if (dst[q] < 0) continue;
-        float x[4];
+      for (int q0 = 0; q0 < GW_IMAX; q0 += 4) {
+        if (q0 >= nq) break;
+        float x[4][4];
 #pragma unroll
-        for (int jr = 0; jr < 4; ++jr) x[jr] = row0[q] + jr < nr ? stf[src[q] + jr * ld] : 0.f;
-        float4 hi, lo;
-        split4(x, hi, lo);
-        *reinterpret_cast<float4*>(lay + dst[q]) = hi;
-        *reinterpret_cast<float4*>(lay + half + dst[q]) = lo;
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int jr = 0; jr < 4; ++jr)
+            x[u][jr] = (dst[q0 + u] >= 0 && row0[q0 + u] + jr < nr) ? stf[src[q0 + u] + jr * ld] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (dst[q0 + u] < 0) continue;
+          float4 hi, lo;
+          split4(x[u], hi, lo);
+          *reinterpret_cast<float4*>(lay + dst[q0 + u]) = hi;
+          *reinterpret_cast<float4*>(lay + dlo[q0 + u] + dst[q0 + u]) = lo;
+        }
       }
       proxy_fence();                                   // generic writes -> visible to the tensor core
       __syncwarp();
@@ -332,14 +350,20 @@ __global__ void __launch_bounds__(TC_T, 1)
     good = bar_wait(bar_lempty + 8 * (lt % nl), (unsigned)((lt / nl) & 1)) ? 1 : 0;
   }
   good = __syncthreads_and(good);
-  if (good) {
+  if (good && warp < 8) {
     tc_fence_after();
     const int q4 = warp & 3, grp = warp >> 2;          // TMEM lanes 32 q4 .. 32 q4 + 31
-    for (int t = grp; t < mtiles; t += TC_T / 128) {
+    for (int t = grp; t < mtiles; t += 2) {
       float v[N];
-      const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(t * N);
+      const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(t * 2 * N);
 #pragma unroll
-      for (int c16 = 0; c16 < N / 16; ++c16) tmem_ld16(taddr + 16 * c16, v + 16 * c16);
+      for (int c16 = 0; c16 < N / 16; ++c16) {
+        float w[16];
+        tmem_ld16(taddr + 16 * c16, v + 16 * c16);
+        tmem_ld16(taddr + N + 16 * c16, w);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[16 * c16 + e] += w[e];
+      }
       const int m = 128 * t + 32 * q4 + lane;          // stacked column of the V blocks
       const int b = m / ld, p = m - b * ld;
       if (b < kblocks && p < r) {
@@ -349,7 +373,7 @@ __global__ void __launch_bounds__(TC_T, 1)
           if (q < r) d[q] = (double)v[q];
       }
     }
-  } else if (threadIdx.x == 0) {
+  } else if (!good && threadIdx.x == 0) {
     // a wait gave up: record it, let every copy and MMA in flight finish
     // (bounded), and leave without partial sums
     atomicExch(err, 1);
@@ -375,7 +399,7 @@ __global__ void __launch_bounds__(TC_T, 1)
 // the stages s = (block i, row tile t) run in block order.  Same warp roles
 // as the Gram:
 //   warp 0      one TMA bulk copy of 128 rows per stage into a ring of nst;
-//   warps 2..7  split a landed stage into one of nl A buffers (element (m, p)
+//   warps 2..9  split a landed stage into one of nl A buffers (element (m, p)
 //               at (p/4) 2048 + m 16 + (p%4) 4), and at a block's first tile
 //               its coefficients into B buffer (block sequence number) % 2
 //               (element (q, p) at (p/4) N 16 + q 16 + (p%4) 4), each buffer
@@ -413,7 +437,7 @@ __global__ void __launch_bounds__(TC_T, 1)
   const int nstages = kblocks * T;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = ldv / 4;                             // 16-byte chunks of a V row
-  const unsigned ahalf = a_bytes / 2, bhalf = b_bytes / 2;
+  const unsigned ahalf = a_bytes / 2;
   // stage sidx -> group g, block i, tile t of the group (mt tiles in it)
   auto decode = [&](int sidx, int& g, int& i, int& t, int& mt) {
     g = sidx / (kblocks * MT);
@@ -452,7 +476,7 @@ __global__ void __launch_bounds__(TC_T, 1)
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = *tmem_slot;
-  const unsigned bstride = (unsigned)N * 16u;          // between K chunks of a coefficient buffer
+  const unsigned bstride = (unsigned)N * 32u;          // between K chunks of a coefficient buffer (N hi, N lo rows)
 
   if (warp == 0) {
     // ---- producer
@@ -478,7 +502,11 @@ __global__ void __launch_bounds__(TC_T, 1)
   } else if (warp == 1) {
     // ---- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(128, N);
+      const uint32_t idesc2 = idesc_tf32(128, 2 * N), idesc1 = idesc_tf32(128, N);
+      // descriptors of A buffer 0 and B buffer 0, advanced per operand
+      const uint64_t dA0 = kdesc(base + off_a, 2048u, 128u);
+      const uint64_t dB0 = kdesc(base + off_b, bstride, 128u);
+      const uint64_t dla = (uint64_t)(ahalf >> 4);
       for (int sidx = 0; sidx < nstages; ++sidx) {
         int g, i, t, mt;
         decode(sidx, g, i, t, mt);
@@ -492,13 +520,15 @@ __global__ void __launch_bounds__(TC_T, 1)
           break;
         }
         tc_fence_after();
-        const unsigned ahi = base + off_a + (unsigned)j * a_bytes, alo = ahi + ahalf;
-        const unsigned bhi = base + off_b + (unsigned)(bs & 1) * b_bytes, blo = bhi + bhalf;
-        const unsigned d = tmem + (unsigned)(t * N);
-        for (int k8 = 0; k8 < KC / 2; ++k8)
-          mma_split3(d, kdesc(ahi + (unsigned)k8 * 4096u, 2048u, 128u), kdesc(alo + (unsigned)k8 * 4096u, 2048u, 128u),
-                     kdesc(bhi + (unsigned)k8 * 2u * bstride, bstride, 128u),
-                     kdesc(blo + (unsigned)k8 * 2u * bstride, bstride, 128u), idesc, (i > 0 || k8 > 0) ? 1 : 0);
+        const uint64_t aj = dA0 + (uint64_t)(((unsigned)j * a_bytes) >> 4);
+        const uint64_t bj = dB0 + (uint64_t)(((unsigned)(bs & 1) * b_bytes) >> 4);
+        const unsigned d = tmem + (unsigned)(t * 2 * N);
+        for (int k8 = 0; k8 < KC / 2; ++k8) {
+          const uint64_t ak = aj + (uint64_t)(k8 * 256);                    // 4096 bytes per K step
+          const uint64_t bk = bj + (uint64_t)((((unsigned)k8 * 2u) * bstride) >> 4);
+          mma_tf32(d, ak, bk, idesc2, (i > 0 || k8 > 0) ? 1 : 0);          // A_hi [C_hi | C_lo]
+          mma_tf32(d, ak + dla, bk, idesc1, 1);                             // A_lo C_hi
+        }
         mma_commit(bar_aempty + 8 * j);
         if (t == mt - 1) mma_commit(bar_bempty + 8 * (bs & 1));   // the block's coefficients are free
         progress[2] = sidx + 1;
@@ -506,9 +536,10 @@ __global__ void __launch_bounds__(TC_T, 1)
     }
     __syncwarp();
   } else {
-    // ---- split (warps 2..7); warps 2..5 also write out each group
+    // ---- split (warps 2..9); warps 2..5 also write out each group
     const int sid = threadIdx.x - 64;
     int src[GW_IMAX], dst[GW_IMAX], mrow[GW_IMAX], ncol[GW_IMAX];
+    const int nq = (nch * 128 - sid + 32 * GW_SPLIT - 1) / (32 * GW_SPLIT);   // items of this thread
 #pragma unroll
     for (int q = 0; q < GW_IMAX; ++q) {
       const int it = sid + q * 32 * GW_SPLIT;
@@ -546,30 +577,34 @@ __global__ void __launch_bounds__(TC_T, 1)
           split4(cv, hi, lo);
           const size_t o = (size_t)k4 * bstride + (size_t)q * 16;
           *reinterpret_cast<float4*>(tsm + bsel + o) = hi;
-          *reinterpret_cast<float4*>(tsm + bsel + bhalf + o) = lo;
+          *reinterpret_cast<float4*>(tsm + bsel + 16 * N + o) = lo;
         }
       }
       const float* stf = reinterpret_cast<const float*>(tsm + TC_BAR_BYTES + (size_t)s * stage_bytes);
       unsigned char* a = tsm + off_a + (size_t)j * a_bytes;
       const int nr = min(128, r1 - (r0 + 128 * (g * MT + t)));
+      // four items at a time: their loads are in flight together
 #pragma unroll
-      for (int q = 0; q < GW_IMAX; ++q) {
-        if (ncol[q] < 0) continue;
-        float x[4] = {0.f, 0.f, 0.f, 0.f};
-        if (mrow[q] < nr) {
-          const float4 v4 = *reinterpret_cast<const float4*>(stf + src[q]);
-          x[0] = v4.x;
-          x[1] = v4.y;
-          x[2] = v4.z;
-          x[3] = v4.w;
-        }
+      for (int q0 = 0; q0 < GW_IMAX; q0 += 4) {
+        if (q0 >= nq) break;
+        float4 v4[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (u >= ncol[q]) x[u] = 0.f;
-        float4 hi, lo;
-        split4(x, hi, lo);
-        *reinterpret_cast<float4*>(a + dst[q]) = hi;
-        *reinterpret_cast<float4*>(a + ahalf + dst[q]) = lo;
+          v4[u] = (ncol[q0 + u] > 0 && mrow[q0 + u] < nr) ? *reinterpret_cast<const float4*>(stf + src[q0 + u])
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u;
+          if (ncol[q] < 0) continue;
+          float x[4] = {v4[u].x, v4[u].y, v4[u].z, v4[u].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (e >= ncol[q]) x[e] = 0.f;
+          float4 hi, lo;
+          split4(x, hi, lo);
+          *reinterpret_cast<float4*>(a + dst[q]) = hi;
+          *reinterpret_cast<float4*>(a + ahalf + dst[q]) = lo;
+        }
       }
       proxy_fence();                                   // generic writes -> visible to the tensor core
       __syncwarp();
@@ -589,9 +624,15 @@ __global__ void __launch_bounds__(TC_T, 1)
         const int q4 = warp & 3;                       // TMEM lanes 32 q4 .. 32 q4 + 31
         for (int tt = 0; tt < mt; ++tt) {
           float v[N];
-          const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(tt * N);
+          const unsigned taddr = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(tt * 2 * N);
 #pragma unroll
-          for (int c16 = 0; c16 < N / 16; ++c16) tmem_ld16(taddr + 16 * c16, v + 16 * c16);
+          for (int c16 = 0; c16 < N / 16; ++c16) {
+            float w[16];
+            tmem_ld16(taddr + 16 * c16, v + 16 * c16);
+            tmem_ld16(taddr + N + 16 * c16, w);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[16 * c16 + e] += w[e];
+          }
           const int row = r0 + 128 * (g * MT + tt) + 32 * q4 + lane;
           if (row < r1) {
             float* orow = out + (size_t)row * ldo;
@@ -673,40 +714,61 @@ const TcDevice& tc_setup() {
 
 }  // namespace
 
+// Experiment knobs (environment, read once): MHDE_TC_TR, MHDE_TC_NL and
+// MHDE_TC_NST restrict the plans below to one tile height, buffer count or
+// ring depth (0: free).
+struct TcKnobs {
+  int TR = 0, nl = 0, nst = 0;
+};
+const TcKnobs& tc_knobs() {
+  static const TcKnobs k = [] {
+    TcKnobs v;
+    auto rd = [](const char* n) { const char* e = std::getenv(n); return e ? std::atoi(e) : 0; };
+    v.TR = rd("MHDE_TC_TR");
+    v.nl = rd("MHDE_TC_NL");
+    v.nst = rd("MHDE_TC_NST");
+    return v;
+  }();
+  return k;
+}
+
 bool gram_tc_plan(int kblocks, int ld, int r, TcGramPlan& p) {
   if (kblocks < 1 || r < 1 || r > 64 || ld < r || ld % 4 != 0 || ld > 64) return false;
   p.nch = ld / 4;
   p.N = (r + 15) / 16 * 16;
-  // blocks per CTA: their accumulators (M tiles of 128 stacked columns, N
-  // columns each) fit 256 TMEM columns
-  p.kgroup = std::min(kblocks, std::max(1, (256 / p.N) * 128 / ld));
-  while (p.kgroup > 1 && ((p.kgroup * ld + 127) / 128) * p.N > 256) --p.kgroup;
+  // blocks per CTA: their accumulators (M tiles of 128 stacked columns, 2N
+  // columns each) fit the 512 TMEM columns of the SM
+  p.kgroup = std::min(kblocks, std::max(1, (512 / (2 * p.N)) * 128 / ld));
+  while (p.kgroup > 1 && ((p.kgroup * ld + 127) / 128) * 2 * p.N > 512) --p.kgroup;
   for (; p.kgroup >= 1; --p.kgroup) {
     p.mtiles = (p.kgroup * ld + 127) / 128;
     p.ncols = 32;
-    while ((int)p.ncols < p.mtiles * p.N) p.ncols *= 2;
-    // one CTA per SM, two operand buffers; the largest tile that leaves a
+    while ((int)p.ncols < p.mtiles * 2 * p.N) p.ncols *= 2;
+    // one CTA per SM, nl operand buffers; the largest tile that leaves a
     // ring of at least three stages, the deepest ring (at most 6) for it
+    const TcKnobs& kn = tc_knobs();
     for (int TR = 32; TR >= 8; TR -= 8)
-      for (int nst = 6; nst >= 3; --nst) {
-        const size_t stage = (size_t)(p.kgroup + 1) * TR * ld * 4;
-        const size_t lay = 2 * (size_t)TR * 4 * (p.N + (size_t)p.mtiles * 128);   // hi + lo
-        const size_t off_lay = (TC_BAR_BYTES + nst * stage + 1023) / 1024 * 1024;
-        const size_t total = off_lay + 2 * lay;
-        const int items = (p.kgroup + 1) * ld * (TR / 4);
-        if (total <= TC_SMEM_MAX && stage < (1u << 20) && items <= GW_IMAX * GW_SPLIT * 32) {
-          p.TR = TR;
-          p.nst = nst;
-          p.nl = 2;
-          p.stage_bytes = (unsigned)stage;
-          p.off_lay = (unsigned)off_lay;
-          p.lay_bytes = (unsigned)lay;
-          p.smem = total;
-          p.ngroups = (kblocks + p.kgroup - 1) / p.kgroup;
-          p.per_sm = 1;
-          return true;
+      for (int nl = 4; nl >= 2; --nl)
+        for (int nst = 6; nst >= 3; --nst) {
+          if ((kn.TR && TR != kn.TR) || (kn.nst && nst != kn.nst) || nl != (kn.nl ? kn.nl : 2)) continue;
+          const size_t stage = (size_t)(p.kgroup + 1) * TR * ld * 4;
+          const size_t lay = 2 * (size_t)TR * 4 * (p.N + (size_t)p.mtiles * 128);   // W hi+lo, V hi, V lo
+          const size_t off_lay = (TC_BAR_BYTES + nst * stage + 1023) / 1024 * 1024;
+          const size_t total = off_lay + nl * lay;
+          const int items = (p.kgroup + 1) * ld * (TR / 4);
+          if (total <= TC_SMEM_MAX && stage < (1u << 20) && items <= GW_IMAX * GW_SPLIT * 32) {
+            p.TR = TR;
+            p.nst = nst;
+            p.nl = nl;
+            p.stage_bytes = (unsigned)stage;
+            p.off_lay = (unsigned)off_lay;
+            p.lay_bytes = (unsigned)lay;
+            p.smem = total;
+            p.ngroups = (kblocks + p.kgroup - 1) / p.kgroup;
+            p.per_sm = 1;
+            return true;
+          }
         }
-      }
   }
   return false;
 }
@@ -745,20 +807,21 @@ bool combine_tc_plan(int n_rows, int ldv, int r_in, int r_out, int nsm, TcCombin
   p.a_bytes = 2u * (unsigned)p.KC * 2048u;
   p.b_bytes = 2u * (unsigned)p.KC * (unsigned)p.N * 16u;
   // one CTA per SM over an even share of the row tiles, walked in groups of
-  // MT tiles (MT N <= 512 tensor-memory columns)
+  // MT tiles (MT 2N <= 512 tensor-memory columns)
   const int tiles = (n_rows + 127) / 128;
   const int per_cta = (tiles + std::max(nsm, 1) - 1) / std::max(nsm, 1);
   p.rows_per_cta = 128 * per_cta;
   p.nctas = (tiles + per_cta - 1) / per_cta;
-  p.MT = std::max(1, std::min(512 / p.N, per_cta));
+  p.MT = std::max(1, std::min(256 / p.N, per_cta));
   p.ncols = 32;
-  while ((int)p.ncols < p.MT * p.N) p.ncols *= 2;
+  while ((int)p.ncols < p.MT * 2 * p.N) p.ncols *= 2;
   // as many A buffers (at most 4) and as deep a ring (at most 8) as fit,
   // preferring two A buffers and three stages first
   for (int pass = 0; pass < 2; ++pass)
     for (int nl = 4; nl >= 1; --nl)
       for (int nst = 8; nst >= 2; --nst) {
         if (pass == 0 && (nl < 2 || nst < 3)) continue;
+        if ((tc_knobs().nl && nl != tc_knobs().nl) || (tc_knobs().nst && nst != tc_knobs().nst)) continue;
         const size_t off_a = (TC_BAR_BYTES + (size_t)nst * p.stage_bytes + 1023) / 1024 * 1024;
         const size_t off_b = off_a + (size_t)nl * p.a_bytes;
         const size_t total = off_b + 2 * (size_t)p.b_bytes;
