@@ -123,18 +123,18 @@ typedef struct {
                                  saddle SpMM (128, 256 or 512; results do not
                                  depend on it) */
   double spmm_tuned_us[3];    /* its timings of one SpMM at 128, 256, 512 */
-  int gram_tensor_cores;      /* 1 if the bind-time autotuner picked the tensor-core (tcgen05)
-                                 kernel for the FP32 block Gram of the mixed path, 0 the
-                                 CUDA-core kernel; the tensor-core products are split TF32
-                                 (about 2^-21 relative against FP32's 2^-24), so that form is
-                                 picked only when it is at least 1.25x faster */
-  int combine_tensor_cores;   /* the same choice for the FP32 block combination */
+  int gram_tensor_cores;      /* 1 if the FP32 block Gram of the mixed path runs on the tensor
+                                 cores (tcgen05, split TF32: about 2^-21 relative against FP32's
+                                 2^-24), 0 on the CUDA cores; tensor cores for J > 32, so that
+                                 the choice never depends on a timing */
+  int combine_tensor_cores;   /* the same for the FP32 block combination */
   double gram_tuned_us[2];    /* its timings of one Gram of restart/2 + 1 blocks: CUDA cores,
                                  tensor cores (0 where not timed) */
   double combine_tuned_us[2]; /* the same for one combination of restart/2 blocks */
-  int inner_persistent;       /* 1 if the bind-time autotuner picked the persistent (one cooperative
-                                 launch, grid barriers) form of the mixed path's inner GMRES on F,
-                                 0 the chain of per-phase launches */
+  int inner_persistent;       /* 1 if the mixed path's inner GMRES on F runs as the persistent
+                                 form (one cooperative launch, grid barriers; chosen only through
+                                 the environment, MHDE_INNER_GRID=1), 0 the chain of per-phase
+                                 launches (the default) */
   double inner_tuned_us[2];   /* its timings of one inner solve: launch chain, persistent
                                  (0 where not timed) */
 } mhde_stats;

@@ -216,15 +216,18 @@ void to_rows(const mhde_ctx* c, const double* a, const double* b, double sgn, do
 // order whatever the CTA size, so the choice never changes a result bit (a
 // resumed run stays bit-identical to an uninterrupted one).  F's values are
 // still zero at bind time; the access pattern and traffic are the real ones.
-// FP32 block Gram and block combination of the mixed path: time the
-// CUDA-core and the tensor-core kernels on this context's sizes (restart/2
-// basis blocks of the zeroed workspace; values do not change the timing);
-// MHDE_GRAM_TC / MHDE_COMB_TC = 0 or 1 force the choice.  The tensor-core
-// products carry relative errors of about 2^-21 (split TF32) against FP32's
-// 2^-24, and the Cholesky QR of the projected Gram feels that: on the
-// 128 x 128 cavity ensemble (J = 20) a 1.15x faster tensor-core Gram raised
-// the block iterations per step from 328 to 352.  So a tensor-core form is
-// kept only when it is at least 1.25x faster than the CUDA-core one.
+// FP32 block Gram and block combination of the mixed path: the CUDA-core
+// and the tensor-core kernels are timed on this context's sizes (restart/2
+// basis blocks of the zeroed workspace; values do not change the timing) and
+// the timings reported in the stats, but the choice follows the member
+// count alone, so that two contexts given the same data always compute the
+// same bits: tensor cores for more than 32 members (12.5 FMA per byte at
+// J = 50, where they were 4x faster), CUDA cores up to 32.  At J = 20 the
+// tensor-core Gram was 1.15x faster, but its split-TF32 products (about
+// 2^-21 relative against FP32's 2^-24) feed the Cholesky QR of the
+// projected Gram and raised the block iterations per step on the 128 x 128
+// cavity ensemble from 328 to 352.  MHDE_GRAM_TC / MHDE_COMB_TC = 0 or 1
+// force the choice.
 static int autotune_blockops(mhde_ctx* c) {
   c->gram_tc = c->comb_tc = false;
   if (c->opt.precision != MHDE_PREC_MIXED) return MHDE_OK;
@@ -268,9 +271,9 @@ static int autotune_blockops(mhde_ctx* c) {
   count_launch(launch_count() - launches0 > 0 ? -(launch_count() - launches0) : 0);   // not part of any step
   if (take_async_error(s.d_err, st) != 0 || cudaGetLastError() != cudaSuccess)
     return fail(c, MHDE_ECUDA, "block-operation autotuner: a kernel failed");
-  auto pick = [](const double us[2], const char* env) {
-    if (const char* e = std::getenv(env)) return e[0] == '1';
-    return us[1] > 0.0 && (us[0] <= 0.0 || us[1] * 1.25 < us[0]);
+  auto pick = [c](const double us[2], const char* env) {
+    if (const char* e = std::getenv(env)) return e[0] == '1' && us[1] > 0.0;
+    return us[1] > 0.0 && c->J > 32;
   };
   c->gram_tc = pick(c->gram_tuned_us, "MHDE_GRAM_TC");
   c->comb_tc = pick(c->comb_tuned_us, "MHDE_COMB_TC");
@@ -278,10 +281,13 @@ static int autotune_blockops(mhde_ctx* c) {
 }
 
 // Inner GMRES on F of the mixed path: the persistent form (one cooperative
-// launch, grid barriers) against the launch chain, timed on this context's
-// sizes (subproblem v's buffers and current operator values); the faster is
-// kept.  MHDE_INNER_GRID = 0 or 1 forces the choice.  Both forms compute the
-// same method with the same step count (rounding differs).
+// launch, grid barriers) and the launch chain, timed on this context's
+// sizes (subproblem v's buffers and current operator values) for the stats.
+// Both compute the same method with the same step count but round
+// differently, so the choice is fixed rather than timed (two contexts given
+// the same data compute the same bits): the launch chain, which was the
+// faster on every workload measured; MHDE_INNER_GRID = 1 selects the
+// persistent form, 0 skips it.
 int autotune_inner(mhde_ctx* c) {
   c->inner_grid = false;
   c->ig_P = 0;
@@ -330,10 +336,7 @@ int autotune_inner(mhde_ctx* c) {
     c->inner_tuned_us[1] = 0.0;
     return MHDE_OK;
   }
-  if (env && env[0] == '1')
-    c->inner_grid = true;
-  else
-    c->inner_grid = c->inner_tuned_us[1] > 0.0 && c->inner_tuned_us[1] < c->inner_tuned_us[0];
+  c->inner_grid = env && env[0] == '1';
   return MHDE_OK;
 }
 
