@@ -13,7 +13,9 @@ linear systems, all in float64.
 Discrete setting (where the paper leaves a choice open, this is the reading
 taken):
 * Taylor-Hood P2 velocity / P1 pressure on a conforming triangulation
-  (Section 2, eq. infsup: any inf-sup stable pair);
+  (Section 2, eq. infsup: any inf-sup stable pair), or the paper's
+  Scott-Vogelius pair P2 / P1disc on barycenter-refined meshes (Section 2,
+  Section 4; ``OracleRun(..., element="SV")``);
 * a 7-point degree-5 triangle quadrature derived in :mod:`oracle.quadrature`;
 * skew-symmetric convection form by default (Section 2, trilinear form b);
 * Dirichlet data by identity rows, pressure pinned at node 0 then shifted to

@@ -1,12 +1,21 @@
-"""Taylor-Hood P2/P1 finite element space, element integrals and global
+"""P2 velocity spaces with a P1 pressure, element integrals and global
 assembly (oracle; test infrastructure only).
+
+Two pressure spaces (Section 2: the analysis takes the Scott-Vogelius pair,
+any inf-sup stable pair is allowed):
+* ``"P1"``: continuous P1 pressure (Taylor-Hood P2/P1);
+* ``"P1disc"``: discontinuous P1 pressure (Scott-Vogelius P2/P1disc, stable on
+  barycenter-refined meshes); the divergence of every P2 field lies in
+  P1disc, so a velocity that satisfies the discrete continuity equation is
+  divergence-free at every point.
 
 Numbering convention (also the convention of the library's C ABI):
 * P2 node k < nv is mesh vertex k;
 * P2 node nv + e is the midpoint of edge e, where the edges are the distinct
   unordered vertex pairs of the triangulation sorted lexicographically by
   (smaller vertex, larger vertex);
-* P1 pressure node i is vertex i.
+* continuous P1 pressure node i is vertex i; discontinuous P1 pressure dof
+  3e + i is the barycentric coordinate of local vertex i on triangle e.
 Local P2 node order on a triangle (v0, v1, v2): v0, v1, v2, then the
 midpoints of (v0,v1), (v1,v2), (v2,v0).
 
@@ -50,10 +59,14 @@ def p2_bary_derivs(lam):
 
 
 class P2Space:
-    """P2 velocity (per component) and P1 pressure on a triangulation."""
+    """P2 velocity (per component) and a continuous (``pressure="P1"``) or
+    discontinuous (``pressure="P1disc"``) P1 pressure on a triangulation."""
 
-    def __init__(self, mesh):
+    def __init__(self, mesh, pressure="P1"):
+        if pressure not in ("P1", "P1disc"):
+            raise ValueError(pressure)
         self.mesh = mesh
+        self.pressure = pressure
         xy, tri = mesh.xy, mesh.tri.astype(np.int64)
         nv, nt = xy.shape[0], tri.shape[0]
         self.nv, self.nt = nv, nt
@@ -64,7 +77,12 @@ class P2Space:
         self.edges = uniq
         self.ne = uniq.shape[0]
         self.n2 = nv + self.ne
-        self.np_ = nv
+        if pressure == "P1":
+            self.np_ = nv
+            self.pdofs = tri                                 # [nt, 3] pressure dof per local vertex
+        else:
+            self.np_ = 3 * nt
+            self.pdofs = np.arange(3 * nt, dtype=np.int64).reshape(nt, 3)
         edge_of = inv.reshape(3, nt).T                     # [nt, 3] edge index per local edge
         self.dofs = np.concatenate([tri, nv + edge_of], axis=1)   # [nt, 6]
         # node coordinates
@@ -150,17 +168,22 @@ class P2Space:
 
     def divergence(self):
         """(Bx, By), each [np, n2]."""
-        tri = self.mesh.tri.astype(np.int64)
         out = []
         for d in range(2):
             loc = -np.einsum("tq,qi,tqa->tia", self.wq, self.psi, self.gphi[..., d])
-            out.append(self._assemble(loc, tri, self.dofs, self.np_, self.n2))
+            out.append(self._assemble(loc, self.pdofs, self.dofs, self.np_, self.n2))
         return out
 
     def pressure_mass(self):
-        tri = self.mesh.tri.astype(np.int64)
         loc = np.einsum("tq,qi,qk->tik", self.wq, self.psi, self.psi)
-        return self._assemble(loc, tri, tri, self.np_, self.np_)
+        return self._assemble(loc, self.pdofs, self.pdofs, self.np_, self.np_)
+
+    def divergence_sq(self, z):
+        """||div z||^2 of a P2 vector field z [n2, 2], integrated exactly
+        (div z is linear on each triangle, the rule is of degree 5)."""
+        g = self.grad_at_quad(z)                             # [nt, nq, comp, dir]
+        dv = g[..., 0, 0] + g[..., 1, 1]
+        return float(np.sum(self.wq * dv * dv))
 
     # ------------------------------------------------------------------ norms
     def l2_sq(self, M, z):

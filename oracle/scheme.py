@@ -12,7 +12,8 @@ Algorithm 1:
       F_w = M/dt + N(<v>) + (nubar+nubar_m)/2 K + K_T(2 mu dt l_v^2)
     (left-hand sides of eq. weaknew1 / weaknew2) inside the saddle-point
     matrix [[F, 0, Bx^T], [0, F, By^T], [Bx, By, 0]] with identity rows for
-    Dirichlet velocity nodes and pressure node 0 pinned;
+    Dirichlet velocity nodes and pressure dof 0 pinned (P1 pressure:
+    continuous, Taylor-Hood, or discontinuous, Scott-Vogelius);
  4. for every member j the right-hand side of eq. weaknew1
       M f1_j + M v_j^n / dt - N(w'_j) v_j^n - (nu_j - nu_m,j)/2 K w_j^n
         - (nu'_j + nu'_m,j)/2 K v_j^n
@@ -67,12 +68,17 @@ def skew_action(space, a_nodal, u_nodal, form="skew"):
 class OracleRun:
     """State and one-step update of Algorithm 1 for an ``workloads.Ensemble``."""
 
-    def __init__(self, ens, form="skew", lu_per_member=False, mu=None):
+    def __init__(self, ens, form="skew", lu_per_member=False, mu=None, element="TH"):
+        """``element``: "TH" (Taylor-Hood P2/P1) or "SV" (Scott-Vogelius
+        P2/P1disc, for barycenter-refined meshes; Section 2 and Section 4)."""
+        if element not in ("TH", "SV"):
+            raise ValueError(element)
         self.ens = ens
         self.form = form
         self.lu_per_member = lu_per_member
         self.mu = ens.mu if mu is None else mu
-        self.S = P2Space(ens.mesh)
+        self.element = element
+        self.S = P2Space(ens.mesh, pressure="P1" if element == "TH" else "P1disc")
         S = self.S
         self.M = S.mass()
         self.K = S.stiffness()

@@ -1,0 +1,168 @@
+"""Pins of the oracle's Scott-Vogelius element (P2 velocity, discontinuous P1
+pressure, on barycenter-refined meshes; Section 2 and Section 4) against what
+the paper and the mathematics fix:
+
+* barycenter refinement: counts, orientation, areas, barycenters;
+* the patch solution of the Taylor-Hood pins (linear pressures, exact in
+  P1disc) is reproduced exactly, velocities and pressures;
+* the discrete velocity is divergence-free at every point (div P2 lies in
+  P1disc), where Taylor-Hood on the same mesh is not;
+* pressure robustness: a gradient force grad(phi) with grad(phi) in P2 leaves
+  the velocity unchanged and moves the pressure by the L2 projection of phi
+  onto P1disc, computed here triangle by triangle;
+* the spatial errors of Tables 1 and 3 of Section 4.1, computed with the
+  paper's own exact pressure, and their second-order rates.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle.scheme import OracleRun
+from oracle.norms import l2h1_errors
+from workloads.ensembles import lid_cavity, convergence_study, manufactured
+from workloads.mesh import unit_square, channel_step, barycentric_refine
+from tests.test_oracle_scheme import patch_ensemble
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _area(xy, tri):
+    a, b, c = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    return 0.5 * ((b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0]))
+
+
+@pytest.mark.parametrize("mesh", [unit_square(3), channel_step(cells_per_unit=1)])
+def test_barycentric_refinement(mesh):
+    r = barycentric_refine(mesh)
+    nv, nt = mesh.nv, mesh.nt
+    assert r.nv == nv + nt and r.nt == 3 * nt
+    assert np.array_equal(r.xy[:nv], mesh.xy)
+    assert np.allclose(r.xy[nv:], mesh.xy[mesh.tri].mean(axis=1), rtol=0, atol=1e-15)
+    child = _area(r.xy, r.tri).reshape(nt, 3)
+    parent = _area(mesh.xy, mesh.tri)
+    assert np.all(child > 0)
+    # the barycenter splits a triangle into three of equal area
+    assert np.allclose(child, parent[:, None] / 3.0, rtol=1e-13)
+    # child k of triangle e keeps the parent's local edge k
+    for k in range(3):
+        assert np.array_equal(r.tri[k::3, :2], mesh.tri[:, [k, (k + 1) % 3]])
+
+
+@pytest.mark.parametrize("mesh", [barycentric_refine(unit_square(3)),
+                                  barycentric_refine(channel_step(cells_per_unit=1))])
+def test_sv_patch_solution_is_exact(mesh):
+    ens, v, w = patch_ensemble(mesh)
+    run = OracleRun(ens, element="SV")
+    S = run.S
+    assert S.np_ == 3 * mesh.nt
+    xy = S.node_xy
+    # pressure dof 3e + i sits at local vertex i of triangle e
+    pxy = mesh.xy[mesh.tri].reshape(-1, 2)
+    for _ in range(ens.nsteps):
+        run.step()
+        t = run.n * ens.dt
+        assert np.abs(run.V - v(xy, t)[None]).max() < 1e-11 * np.abs(v(xy, t)).max()
+        assert np.abs(run.W - w(xy, t)[None]).max() < 1e-11
+        qe = run.zero_mean((pxy[:, 0] - pxy[:, 1])[None])[0]
+        re = run.zero_mean((2 * pxy[:, 0] + pxy[:, 1])[None])[0]
+        assert np.abs(run.zero_mean(run.Q) - qe).max() < 1e-9
+        assert np.abs(run.zero_mean(run.R) - re).max() < 1e-9
+
+
+def test_sv_velocity_is_pointwise_divergence_free():
+    """||div v_h||^2 at rounding level for Scott-Vogelius; O(1) for
+    Taylor-Hood on the same barycenter-refined mesh (the lid's corner
+    singularity)."""
+    ens = lid_cavity(N=6, J=3, s=1.0, dt=0.01, Re=500.0, barycentric=True)
+    out = {}
+    for el in ("SV", "TH"):
+        run = OracleRun(ens, element=el)
+        for _ in range(3):
+            run.step()
+        S = run.S
+        out[el] = max(S.divergence_sq(Z[j]) / S.h1semi_sq(run.K, Z[j])
+                      for Z in (run.V, run.W) for j in range(ens.J))
+    assert out["SV"] < 1e-24
+    assert out["TH"] > 1e-4
+
+
+def _phi(x, y):
+    return x * x * y - y ** 3 / 3.0
+
+
+def _grad_phi(x, y):
+    return np.stack([2 * x * y, x * x - y * y], axis=-1)
+
+
+def test_sv_is_pressure_robust():
+    """Adding grad(phi) to f (phi cubic, so grad(phi) is in P2 and its nodal
+    interpolant is exact) changes no velocity (grad(phi) is L2-orthogonal to
+    the pointwise divergence-free discrete velocities) and shifts every
+    pressure by the L2 projection of phi onto P1disc.  Taylor-Hood's velocity
+    does move."""
+    J = 2
+    mesh = barycentric_refine(unit_square(4))
+    nu = np.array([0.01, 0.012])
+    c = np.array([1.0, 1.001])
+
+    def build(extra):
+        ens = manufactured(4, J, nu, nu * 10, c, dt=0.01, nsteps=2, s=1.0, mesh=mesh)
+        if extra:
+            f0 = ens.f
+            ens.f = lambda p, t: f0(p, t) + _grad_phi(p[:, 0], p[:, 1])[None]
+        return ens
+
+    res = {}
+    for el in ("SV", "TH"):
+        for extra in (False, True):
+            run = OracleRun(build(extra), element=el)
+            for _ in range(2):
+                run.step()
+            res[el, extra] = run
+    a, b = res["SV", False], res["SV", True]
+    scale = np.abs(a.V).max()
+    assert np.abs(b.V - a.V).max() < 1e-12 * scale and np.abs(b.W - a.W).max() < 1e-12 * scale
+    assert np.abs(res["TH", True].V - res["TH", False].V).max() > 1e-6 * scale
+    # L2 projection of phi onto P1disc, triangle by triangle
+    S = a.S
+    x, y = S.qpts[..., 0], S.qpts[..., 1]
+    rhs = np.einsum("tq,tq,qi->ti", S.wq, _phi(x, y), S.psi)          # (phi, lambda_i)
+    Mloc = (S.area[:, None, None] / 12.0) * (np.ones((3, 3)) + np.eye(3))
+    proj = np.linalg.solve(Mloc, rhs[..., None])[..., 0].ravel()
+    want = a.zero_mean(proj[None])[0]
+    for P0, P1 in ((a.Q, b.Q), (a.R, b.R)):
+        d = a.zero_mean(P1 - P0)
+        assert np.abs(d - want[None]).max() < 1e-10 * np.abs(want).max()
+
+
+def _rates(e):
+    e = np.asarray(e)
+    return np.log2(e[:-1] / e[1:])
+
+
+def _sv_errors(N, J, eps, sample):
+    ens = convergence_study(N, J, dt=0.001 / 8, nsteps=8, eps=eps, sample=sample,
+                            mesh=barycentric_refine(unit_square(N)))
+    a, b, _, _ = l2h1_errors(lambda e: OracleRun(e, element="SV"), ens, 8)
+    return a, b
+
+
+def test_spatial_errors_match_table1_with_pressure():
+    """Table 1 (eps = 0, sample 1) with the paper's element, mesh and exact
+    pressure: the printed errors to 1 % and rate 2 (Taylor-Hood needs the
+    pressure removed to match)."""
+    g = json.load(open(os.path.join(GOLDEN, "table1_spatial_eps0.json")))
+    ev, ew = zip(*[_sv_errors(N, 2, 0.0, 1) for N in (4, 8, 16)])
+    assert np.allclose(ev, g["e_v"][:3], rtol=0.01)
+    assert np.allclose(ew, g["e_w"][:3], rtol=0.01)
+    assert np.all(np.abs(_rates(ev) - 2.0) < 0.05) and np.all(np.abs(_rates(ew) - 2.0) < 0.05)
+
+
+def test_spatial_errors_match_table3():
+    """Table 3 (eps = 0.01, J = 20, sample 2): the printed errors to 1 %."""
+    g = json.load(open(os.path.join(GOLDEN, "table3_spatial_eps0_01.json")))["sample2"]
+    ev, ew = zip(*[_sv_errors(N, 20, 0.01, 2) for N in (4, 8, 16)])
+    assert np.allclose(ev, g["e_v"][:3], rtol=0.01)
+    assert np.allclose(ew, g["e_w"][:3], rtol=0.01)

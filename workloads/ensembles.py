@@ -16,7 +16,7 @@ from typing import Callable, Optional
 
 import numpy as np
 
-from .mesh import unit_square, channel_step, Mesh
+from .mesh import unit_square, channel_step, barycentric_refine, Mesh
 
 
 @dataclass
@@ -100,14 +100,15 @@ def manufactured_forcing(x, y, t, c, nu, nu_m, with_pressure=True):
 
 
 def manufactured(N, J, nu, nu_m, c, dt, nsteps, s=1.0, mu=1.0, name="manufactured",
-                 homogeneous=False, zero_forcing=False, with_pressure=True):
+                 homogeneous=False, zero_forcing=False, with_pressure=True, mesh=None):
     """Ensemble whose member j has the exact Elsaesser fields c_j v, c_j w.
 
     Primitive data follow from u = (v+w)/2 and sqrt(s) B = (v-w)/2, and
     f = (f1+f2)/2, sqrt(s) curl g = (f1-f2)/2 (Section 1).
     ``homogeneous`` / ``zero_forcing`` give the energy test of Section 4.2.
+    ``mesh`` replaces the N x N unit square (e.g. by its barycenter refinement).
     """
-    mesh = unit_square(N)
+    mesh = unit_square(N) if mesh is None else mesh
     nu = np.asarray(nu, dtype=np.float64)
     nu_m = np.asarray(nu_m, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
@@ -166,7 +167,8 @@ def config_manufactured_small():
                         name="manufactured-16x16-J3")
 
 
-def convergence_study(N, J, dt, nsteps, eps=0.0, sample=1, seed=0, with_pressure=True):
+def convergence_study(N, J, dt, nsteps, eps=0.0, sample=1, seed=0, with_pressure=True,
+                      mesh=None):
     """Section 4.1: (nu_j, nu_m,j) uniform in [0.009,0.011] x [0.09,0.11]
     (sample 1) or [0.009,0.011] x [0.0009,0.0011] (sample 2); c_j from
     :func:`perturbation_factor`."""
@@ -175,7 +177,7 @@ def convergence_study(N, J, dt, nsteps, eps=0.0, sample=1, seed=0, with_pressure
     nu_m = rng.uniform(0.09, 0.11, J) if sample == 1 else rng.uniform(0.0009, 0.0011, J)
     c = perturbation_factor(J, eps)
     return manufactured(N, J, nu, nu_m, c, dt=dt, nsteps=nsteps, s=1.0,
-                        name=f"convergence-N{N}-J{J}", with_pressure=with_pressure)
+                        name=f"convergence-N{N}-J{J}", with_pressure=with_pressure, mesh=mesh)
 
 
 def energy_study(N=32, J=20, dt=0.05, nsteps=20, seed=0):
@@ -198,7 +200,8 @@ def _stream_perturbation(pts):
     return np.stack([py, -px], axis=-1)
 
 
-def lid_cavity(N=128, J=20, s=1.0, dt=0.01, nsteps=200, Re=15000.0, seed=2, spread=0.1):
+def lid_cavity(N=128, J=20, s=1.0, dt=0.01, nsteps=200, Re=15000.0, seed=2, spread=0.1,
+               barycentric=False):
     """Lid-driven-cavity-shaped workload (shape of Section 4.3).
 
     Unit square N x N right-diagonal; nu_j = nu_m,j = (1/Re)(1+delta_j),
@@ -206,6 +209,8 @@ def lid_cavity(N=128, J=20, s=1.0, dt=0.01, nsteps=200, Re=15000.0, seed=2, spre
     two top corners take the wall value 0), u = 0 on the other sides;
     B = (0, 1) on the whole boundary; initial u_j = eps_j curl(psi),
     B_j = eps'_j curl(psi), eps, eps' ~ N(0, sigma = 1e-3); no forcing.
+    ``barycentric=True`` takes the barycenter refinement of the N x N mesh
+    (the meshes of Section 4, for the Scott-Vogelius element).
     """
     rng = np.random.default_rng(seed)
     delta = rng.uniform(-spread, spread, J)
@@ -214,6 +219,8 @@ def lid_cavity(N=128, J=20, s=1.0, dt=0.01, nsteps=200, Re=15000.0, seed=2, spre
     eps_u = rng.normal(0.0, 1e-3, J)
     eps_B = rng.normal(0.0, 1e-3, J)
     mesh = unit_square(N)
+    if barycentric:
+        mesh = barycentric_refine(mesh)
 
     def u0(pts):
         return eps_u[:, None, None] * _stream_perturbation(pts)[None]
@@ -235,7 +242,7 @@ def lid_cavity(N=128, J=20, s=1.0, dt=0.01, nsteps=200, Re=15000.0, seed=2, spre
 
     # the amplitudes are read when u0 / B0 are called, so a caller may change
     # info["eps_u"] / info["eps_B"] in place (finite-difference perturbations)
-    return Ensemble(name=f"lid-cavity-N{N}-J{J}-s{s:g}", mesh=mesh, nu=nu, nu_m=nu_m, s=float(s),
+    return Ensemble(name=f"lid-cavity-N{N}{'-bary' if barycentric else ''}-J{J}-s{s:g}", mesh=mesh, nu=nu, nu_m=nu_m, s=float(s),
                     dt=float(dt), nsteps=int(nsteps), u0=u0, B0=B0, u_bc=u_bc, B_bc=B_bc,
                     info={"N": N, "Re": Re, "seed": seed, "eps_u": eps_u, "eps_B": eps_B,
                           "perturbation_shape": _stream_perturbation})

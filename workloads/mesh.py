@@ -140,3 +140,23 @@ def channel_step(cells_per_unit=7, length=40.0, height=10.0, step=(5.0, 6.0, 1.0
     tri = np.asarray(tris, dtype=np.int32)
     assert np.all(_ccw(xy, tri) > 0)
     return Mesh(xy, tri)
+
+
+def barycentric_refine(mesh):
+    """Barycenter refinement (Alfeld split) of a triangulation: every triangle
+    (a, b, c) gets a new vertex at its barycenter g and is replaced by the
+    three triangles (a, b, g), (b, c, g), (c, a, g), all counter-clockwise.
+    New vertex nv + e is the barycenter of old triangle e; new triangle
+    3e + k is the one on old local edge k.  This is the mesh on which the
+    Scott-Vogelius pair (P2, P1disc) is inf-sup stable in 2D (Section 2)."""
+    xy, tri = mesh.xy, mesh.tri.astype(np.int64)
+    nv, nt = xy.shape[0], tri.shape[0]
+    g = xy[tri].mean(axis=1)
+    new_xy = np.concatenate([xy, g], axis=0)
+    c = nv + np.arange(nt, dtype=np.int64)
+    a, b, d = tri[:, 0], tri[:, 1], tri[:, 2]
+    new_tri = np.stack([np.stack([a, b, c], axis=1), np.stack([b, d, c], axis=1),
+                        np.stack([d, a, c], axis=1)], axis=1).reshape(3 * nt, 3)
+    new_tri = new_tri.astype(np.int32)
+    assert np.all(_ccw(new_xy, new_tri) > 0)
+    return Mesh(new_xy, new_tri)
