@@ -29,17 +29,26 @@ METRIC = "ensemble member-steps/s at rel L2 <=1e-8 vs FP64 oracle"
 UNIT = "member-steps/s"
 WORKLOAD = dict(N=128, J=20, s=1.0, dt=0.01, Re=15000.0)
 CHANNEL = dict(J=50, s=0.01, dt=0.05, nu=1.0 / 600)
+SV_N = 64
+
+
+def element_of(workload):
+    """Finite element pair of a workload: Scott-Vogelius (P2, P1disc) for the
+    barycenter-refined cavity, Taylor-Hood P2-P1 otherwise."""
+    return "SV" if workload == "sv" else "TH"
 
 
 def make_ensemble(workload, N, J, seed=None):
     """The benchmark's synthetic ensembles: the lid-driven-cavity-shaped one
-    (the metric's workload) or the channel-past-a-step-shaped one."""
+    (the metric's workload), the same cavity on the barycenter refinement of
+    an N x N mesh for the Scott-Vogelius element, or the
+    channel-past-a-step-shaped one."""
     from workloads.ensembles import lid_cavity, channel
     if workload == "channel":
         return channel(J=J, dt=CHANNEL["dt"], s=CHANNEL["s"], nu=CHANNEL["nu"], nu_m=CHANNEL["nu"],
                        seed=3 if seed is None else seed)
     return lid_cavity(N=N, J=J, s=WORKLOAD["s"], dt=WORKLOAD["dt"], Re=WORKLOAD["Re"],
-                      seed=2 if seed is None else seed)
+                      seed=2 if seed is None else seed, barycentric=(workload == "sv"))
 
 
 def parse():
@@ -51,8 +60,10 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-separate", action="store_true", help="skip the separate-solve comparator")
-    p.add_argument("--workload", default="cavity", choices=["cavity", "channel", "batched", "adjoint"],
-                   help="cavity: the metric's workload; channel: the channel-past-a-step ensemble; "
+    p.add_argument("--workload", default="cavity", choices=["cavity", "sv", "channel", "batched", "adjoint"],
+                   help="cavity: the metric's workload; sv: the cavity ensemble with the Scott-Vogelius "
+                        "element on the barycenter refinement of an N x N mesh (default N = 64); "
+                        "channel: the channel-past-a-step ensemble; "
                         "batched: uneven independent ensembles; adjoint: forward and forward + discrete "
                         "adjoint of the sensitivity workload")
     p.add_argument("--batch-count", type=int, default=64)
@@ -72,11 +83,13 @@ def parse():
                         "step, a process pool over members) on the workload's first step, print one JSON line")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--oracle-check", default=None, help=argparse.SUPPRESS)
-    p.add_argument("--N", type=int, default=WORKLOAD["N"])
+    p.add_argument("--N", type=int, default=None, help="cells per side (default 128 cavity, 64 sv)")
     p.add_argument("--J", type=int, default=None, help="members (default 20 cavity, 50 channel)")
     a = p.parse_args()
     if a.J is None:
         a.J = CHANNEL["J"] if a.workload == "channel" else WORKLOAD["J"]
+    if a.N is None:
+        a.N = SV_N if a.workload == "sv" else WORKLOAD["N"]
     return a
 
 
@@ -86,11 +99,18 @@ def config(args, extra=None):
                          f"graded jittered cells, Taylor-Hood P2-P1 (157,838 velocity DOFs), J={args.J}, "
                          f"nu=nu_m=1/600, s=0.01, dt=0.05, inflow scaled by 1+eps_j",
              "mesh": "channel 280x70 cells minus step", "J": args.J, "s": CHANNEL["s"], "dt": CHANNEL["dt"]}
+    elif args.workload == "sv":
+        c = {"workload": f"lid-driven-cavity-shaped ensemble, barycenter refinement of the unit square "
+                         f"{args.N}x{args.N} right-diagonal mesh, Scott-Vogelius P2-P1disc, J={args.J}, "
+                         f"Re=15000, s=1, dt=0.01",
+             "mesh": f"{args.N}x{args.N} barycenter-refined", "J": args.J, "s": WORKLOAD["s"],
+             "dt": WORKLOAD["dt"]}
     else:
         c = {"workload": f"lid-driven-cavity-shaped ensemble, unit square {args.N}x{args.N} "
                          f"right-diagonal, Taylor-Hood P2-P1, J={args.J}, Re=15000, s=1, dt=0.01",
              "mesh": f"{args.N}x{args.N}", "J": args.J, "s": WORKLOAD["s"], "dt": WORKLOAD["dt"]}
-    c.update({"element": "P2-P1", "l2": "per-step working set (Krylov basis 31 blocks + states) > 129 MB L2",
+    c.update({"element": "P2-P1disc" if args.workload == "sv" else "P2-P1",
+              "l2": "per-step working set (Krylov basis 31 blocks + states) > 129 MB L2",
               "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"})
     if extra:
         c.update(extra)
@@ -106,7 +126,7 @@ def cpu_sample(workload, N, J_total):
     from oracle.scheme import OracleRun, ensemble_mean, mixing_length_sq
     from scipy.sparse.linalg import splu
     ens = make_ensemble(workload, N, J_total)
-    run = OracleRun(ens, lu_per_member=True)
+    run = OracleRun(ens, lu_per_member=True, element=element_of(workload))
     t0 = time.perf_counter()
     mv, mw = ensemble_mean(run.V), ensemble_mean(run.W)
     Wp = run.W - mw
@@ -148,7 +168,7 @@ def oracle_step_check(path, workload, N, J):
     from oracle.scheme import OracleRun
     d = np.load(path)
     ens = make_ensemble(workload, N, J)
-    run = OracleRun(ens)
+    run = OracleRun(ens, element=element_of(workload))
     run.V, run.W, run.n = d["v0"].copy(), d["w0"].copy(), int(d["n"])
     t0 = time.perf_counter()
     run.step()
@@ -193,7 +213,7 @@ def fp64_same_steps(args, ens, state0, device):
     first steps of the timed region, from the same post-warm-up state."""
     import torch
     from paper_2108_05110_gb300 import ensemble_io, PREC_FP64
-    sol = ensemble_io.solver_for(ens, precision=PREC_FP64, device=device)
+    sol = ensemble_io.solver_for(ens, precision=PREC_FP64, device=device, element=element_of(args.workload))
     ensemble_io.feed_initial(sol, ens)
     ensemble_io.feed_step_data(sol, ens, ens.dt)
     sol.load_state(state0)
@@ -203,7 +223,15 @@ def fp64_same_steps(args, ens, state0, device):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(sol.stream_v)
     st0 = sol.stats()
-    sol.advance(k)
+    try:
+        sol.advance(k)
+    except Exception as e:          # a step that does not converge is reported, not fatal
+        torch.cuda.synchronize()
+        st1 = sol.stats()
+        sol.close()
+        return {"error": str(e)[:200], "steps_done": int(st1.steps - st0.steps),
+                "what": "FP64 Krylov, SpMM and preconditioner (the plain FP64 GPU form), same post-warm-up "
+                        "state and first steps of the timed region"}
     ev1.record(sol.stream_v)
     torch.cuda.synchronize()
     st1 = sol.stats()
@@ -223,7 +251,7 @@ def _v_system(workload, N, J):
     (saddle matrix, right-hand sides of all members)."""
     from oracle.scheme import OracleRun, ensemble_mean, mixing_length_sq
     ens = make_ensemble(workload, N, J)
-    run = OracleRun(ens)
+    run = OracleRun(ens, element=element_of(workload))
     mw = ensemble_mean(run.W)
     Wp = run.W - mw
     A = run.saddle(run.shared_matrix(mw, mixing_length_sq(run.S, Wp)))
@@ -501,7 +529,8 @@ def adjoint_arm(args, local_rank):
         "workload": "sensitivity: unit square 64x64, P2-P1, J=8, nu, nu_m = 0.005(1+delta), s=0.5, dt=0.01, "
                     "K=40 steps, checkpoint every 5", "mesh": "64x64", "J": ens.J}, "data": "synthetic"}
     for name, prec in (("fp64", PREC_FP64), ("mixed", PREC_MIXED)):
-        sol = ensemble_io.solver_for(ens, precision=prec, device=f"cuda:{local_rank}")
+        sol = ensemble_io.solver_for(ens, precision=prec, device=f"cuda:{local_rank}",
+                                 element=element_of(args.workload))
         ensemble_io.feed_initial(sol, ens)
         ensemble_io.feed_step_data(sol, ens, ens.dt)
         state = sol.save_state()
@@ -538,6 +567,13 @@ def spmm_bytes(sz, prec_bytes):
     return matrix + vectors
 
 
+def laplacian_bytes(sz, prec_bytes):
+    """Algorithmic bytes of one residual b - L x on the finest pressure level:
+    L's values and column indices and its row pointers once, x and b read and
+    the residual written once, J_pad columns each."""
+    return sz.nnz_L * (prec_bytes + 4) + (sz.np + 1) * 4 + 3 * sz.np * sz.J_pad * prec_bytes
+
+
 def gram_bytes(sz, restart, prec_bytes):
     """Algorithmic bytes of the block Gram timed by kernel id 8: restart/2
     basis blocks and W (n_rows x J_pad each) read once, the (k+1) J x J Gram
@@ -564,7 +600,8 @@ def our_arm(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     prec = PREC_MIXED if args.precision == "mixed" else PREC_FP64
     ens = make_ensemble(args.workload, args.N, args.J, seed=(3 if args.workload == "channel" else 2) + rank)
-    sol = ensemble_io.solver_for(ens, precision=prec, device=f"cuda:{local_rank}")
+    sol = ensemble_io.solver_for(ens, precision=prec, device=f"cuda:{local_rank}",
+                                 element=element_of(args.workload))
     ensemble_io.feed_initial(sol, ens)
     ensemble_io.feed_step_data(sol, ens, ens.dt)     # constant lid / field data
     sol.advance(args.warmup)
@@ -644,6 +681,20 @@ def our_arm(args, rank, world, local_rank):
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "bytes_per_launch": alg, "ms_per_launch": gram_ms,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    if args.workload == "sv":
+        # with the discontinuous pressure the dominant kernel of the step is the
+        # pressure-Laplacian CSR product of the V-cycle (k_csr, a third of the
+        # device time in the ncu launch list); its finest-level residual
+        # b - L x is timed alone: L read once, x, b read and r written once
+        lb = laplacian_bytes(sol.sizes, pbytes)
+        l_ms = sol.time_kernel(0, 9, reps=50)
+        l_ach = lb / (l_ms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"pressure-Laplacian residual b - L x on the finest level "
+                    f"(k_csr<{'float' if pbytes == 4 else 'double'}>, L = B D^-1 B^T, nnz {sol.sizes.nnz_L})",
+                    "achieved": l_ach, "peak": peak, "unit": "GB/s", "frac": l_ach / peak, "traffic": None,
+                    "bytes_per_launch": lb, "ms_per_launch": l_ms,
+                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                    "block_gram": {"achieved": achieved, "frac": achieved / peak, "ms_per_launch": gram_ms}}
     # the Krylov operator (saddle SpMM), for reference
     kid = 1 if prec == PREC_MIXED else 0
     spmm_ms = sol.time_kernel(0, kid, reps=50)

@@ -10,14 +10,20 @@
  * f1 = f + sqrt(s) curl g and f2 = f - sqrt(s) curl g (Section 1) and converts
  * at the boundary of every call.
  *
- * Discretisation: Taylor-Hood P2 velocity / P1 pressure on the given
- * triangulation (Section 2, eq. infsup: any inf-sup stable pair), a
- * 7-point degree-5 quadrature, Dirichlet data by identity rows, pressure node
- * 0 pinned and pressures reported with mean zero (Q = L^2_0, Section 2).
+ * Discretisation: P2 velocity on the given triangulation with either a
+ * continuous P1 pressure (Taylor-Hood; Section 2, eq. infsup: any inf-sup
+ * stable pair) or a discontinuous P1 pressure (Scott-Vogelius P2/P1disc, the
+ * paper's element: Section 2 and Section 4, stable on barycenter-refined
+ * meshes, velocities divergence-free at every point); options.element picks
+ * one.  A 7-point degree-5 quadrature, Dirichlet data by identity rows,
+ * pressure dof 0 pinned and pressures reported with mean zero (Q = L^2_0,
+ * Section 2).
  *
  * Numbering: P2 node k < nv is mesh vertex k; node nv + e is the midpoint of
  * edge e, the edges being the distinct unordered vertex pairs sorted
- * lexicographically by (smaller vertex, larger vertex).  P1 node i = vertex i.
+ * lexicographically by (smaller vertex, larger vertex).  Continuous P1
+ * pressure node i = vertex i; discontinuous P1 pressure dof 3t + i = the
+ * barycentric coordinate of local vertex i of triangle t.
  * Nodal arrays are row-major: [J][n2][2] for member vector fields,
  * [n2][2] for one field, [J][np] for member pressures.
  *
@@ -91,17 +97,26 @@ typedef struct {
                            sweep per AMG level cost more outer iterations than 8 and 2 but
                            less time per step) */
   int schur;            /* pressure Schur approximation: 0 Cahouet-Chabard, 1 pressure
-                           convection-diffusion (adds the mean-field P1 convection); default 1 */
+                           convection-diffusion (adds the mean-field P1 convection; continuous
+                           pressure only), 2 least-squares commutator
+                           (L^{-1} B D^{-1} F D^{-1} B^T L^{-1} with L = B D^{-1} B^T, D the
+                           diagonal of the P2 mass on interior nodes); default 1.  With the
+                           discontinuous pressure the Laplacian is always B D^{-1} B^T (0 or 2;
+                           1 is rejected with MHDE_EINVAL) */
   int strict;           /* 1: reject alpha_j <= 0 or mu <= 1/2 with MHDE_ESTAB; default 0 */
   int inner_fp16;       /* 1: the mixed path keeps the inner GMRES basis in FP16 (scaled by
                            sqrt(n2); arithmetic stays FP32), halving the basis traffic of the
                            inner solve; ignored on the FP64 path; default 0 (on the 128x128
                            cavity ensemble the inner solve is bound by its chain of dependent
                            launches, not by traffic: 283 vs 286 us per application) */
+  int element;          /* 0 Taylor-Hood P2/P1 (default); 1 Scott-Vogelius P2/P1disc (give a
+                           barycenter-refined mesh; on other meshes the pair need not be
+                           inf-sup stable and the solve may fail) */
 } mhde_options;
 
 typedef struct {
-  int nv, nt, ne, n2, np;   /* vertices, triangles, edges, P2 nodes, P1 pressure nodes */
+  int nv, nt, ne, n2, np;   /* vertices, triangles, edges, P2 nodes, pressure dofs (nv for
+                               Taylor-Hood, 3 nt for Scott-Vogelius) */
   int n_rows;               /* rows of one saddle system: 2 n2 + np */
   int J, J_pad;             /* members, padded row width of the device multi-vectors */
   long long nnz_F;          /* nonzeros of the scalar P2 block F */
@@ -109,6 +124,7 @@ typedef struct {
   long long nnz_saddle;     /* nonzeros of the full saddle matrix (2 nnz_F + 4 nnz_B + 1) */
   int n_boundary;           /* Dirichlet P2 nodes */
   int amg_levels;           /* levels of the pressure-Laplacian hierarchy */
+  long long nnz_L;          /* nonzeros of its finest operator (P1 stiffness or B D^{-1} B^T) */
 } mhde_sizes;
 
 typedef struct {
@@ -303,7 +319,9 @@ int mhde_probe_inner(mhde_ctx* ctx, int which, int form, const double* R, double
  * 5 block preconditioner (Krylov precision), 6 block Gram of restart/2
  * basis blocks against one block (Krylov precision), 7 block combination
  * sum_i V_i C_i of restart/2 basis blocks (Krylov precision), 8 the partial
- * sums of kernel 6 alone (its dominant launch, without the final reduction). */
+ * sums of kernel 6 alone (its dominant launch, without the final reduction),
+ * 9 the residual b - L x of the pressure Laplacian on the finest level of
+ * the V-cycle (Krylov precision; nnz(L) = sizes.nnz_L). */
 int mhde_time_kernel(mhde_ctx* ctx, int which, int kernel, int reps, double* ms);
 
 /* ------------------------------------------------------------------------

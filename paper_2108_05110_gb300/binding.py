@@ -38,14 +38,17 @@ class Options(C.Structure):
                 ("max_iter", C.c_int), ("max_refine", C.c_int), ("jacobi_sweeps", C.c_int),
                 ("jacobi_omega", C.c_double), ("amg_sweeps", C.c_int), ("amg_cycles", C.c_int),
                 ("inner_iters", C.c_int),
-                ("schur", C.c_int), ("strict", C.c_int), ("inner_fp16", C.c_int)]
+                ("schur", C.c_int), ("strict", C.c_int), ("inner_fp16", C.c_int),
+                ("element", C.c_int)]
+
+ELEMENTS = {"TH": 0, "SV": 1}     # Taylor-Hood P2/P1, Scott-Vogelius P2/P1disc
 
 
 class Sizes(C.Structure):
     _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("ne", C.c_int), ("n2", C.c_int), ("np", C.c_int),
                 ("n_rows", C.c_int), ("J", C.c_int), ("J_pad", C.c_int), ("nnz_F", C.c_longlong),
                 ("nnz_B", C.c_longlong), ("nnz_saddle", C.c_longlong), ("n_boundary", C.c_int),
-                ("amg_levels", C.c_int)]
+                ("amg_levels", C.c_int), ("nnz_L", C.c_longlong)]
 
 
 class Stats(C.Structure):
@@ -161,9 +164,23 @@ def _f64(a, shape=None):
 
 
 def default_options(**kw):
+    """mhde_default_options with fields replaced by keyword.  ``element`` may
+    be given as "TH" / "SV"; unless given otherwise, the Scott-Vogelius
+    element takes the Cahouet-Chabard Schur approximation (schur = 0) with
+    two smoothing sweeps per level (amg_sweeps = 2): on the 64 x 64
+    barycenter-refined cavity ensemble (J = 20) 240 ms per step against 275
+    ms with one sweep and 400 ms for the least-squares commutator (schur = 2,
+    two sweeps and two cycles), which takes fewer iterations (313 against
+    416) at twice the cost per application."""
     lib = load_library()
     o = Options()
     lib.mhde_default_options(C.byref(o))
+    kw = dict(kw)
+    if isinstance(kw.get("element"), str):
+        kw["element"] = ELEMENTS[kw["element"]]
+    if kw.get("element", 0) == 1:
+        kw.setdefault("schur", 0)
+        kw.setdefault("amg_sweeps", 2)
     for k, v in kw.items():
         if not hasattr(o, k):
             raise KeyError(k)

@@ -82,8 +82,10 @@ size_t layout(mhde_ctx* c, char* base) {
   c->BT.val = w.take<double>(2 * nb);
   c->BT.valf = w.take<float>(2 * nb);
   c->d_btsrc = w.take<int>(nb);
-  c->d_p1slot_ptr = w.take<int>(fe.Kp.nnz() + 1);
-  c->d_p1slot = w.take<int>(nt * 9);
+  c->d_p1slot_ptr = w.take<int>(fe.p1_gather_ptr.size());
+  c->d_p1slot = w.take<int>(fe.p1_gather_slot.size());
+  c->d_lsc_dinv = w.take<double>(n2);
+  c->d_lsc_dinvf = w.take<float>(n2);
   c->d_node_ptr = w.take<int>(n2 + 1);
   c->d_node_slot = w.take<int>(nt * 6);
   c->d_mp = w.take<double>(np);
@@ -112,6 +114,14 @@ size_t layout(mhde_ctx* c, char* base) {
     if (l + 1 < amg.levels.size()) {
       mk(H.P, D.P, false);
       mk(H.R, D.R, false);
+      if (H.bs > 0) {
+        D.bs = H.bs;
+        D.nb = H.A.nrows / H.bs;
+        D.blk_omega = H.blk_omega;
+        D.blk_idx = w.take<int>(H.blk_idx.size());
+        D.blk_inv = w.take<double>(H.blk_inv.size());
+        D.blk_invf = w.take<float>(H.blk_inv.size());
+      }
     }
   }
   c->d_ig_rows = w.take<int>(IG_PMAX + 1);
@@ -159,8 +169,9 @@ size_t layout(mhde_ctx* c, char* base) {
     s.colsq = w.take<double>((size_t)c->nchunk * Jp);
     s.dscale = w.take<double>(2 * Jp);
     s.d_err = w.take<int>(1);                 // zeroed with the workspace at bind
-    s.Np = w.take<double>(fe.Kp.nnz());
-    s.Npf = w.take<float>(fe.Kp.nnz());
+    const size_t nnp = c->opt.schur == 1 ? (size_t)fe.Kp.nnz() : 0;   // PCD's pressure convection
+    s.Np = w.take<double>(nnp);
+    s.Npf = w.take<float>(nnp);
     {
       const int kin = std::max(1, c->opt.inner_iters);
       const size_t C2 = 2 * Jp;
@@ -413,6 +424,7 @@ void mhde_default_options(mhde_options* o) {
   o->schur = 1;
   o->strict = 0;
   o->inner_fp16 = 0;
+  o->element = 0;
 }
 
 int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu_m, double s, double dt,
@@ -434,12 +446,15 @@ int mhde_create(const mhde_mesh* mesh, int J, const double* nu, const double* nu
       (c->opt.precision != MHDE_PREC_FP64 && c->opt.precision != MHDE_PREC_MIXED) ||
       (c->opt.conv_form != 0 && c->opt.conv_form != 1) || c->opt.inner_iters < 0 ||
       c->opt.amg_cycles < 1 ||
-      c->opt.inner_iters > mhde::KIN_MAX || (c->opt.schur != 0 && c->opt.schur != 1) ||
-      (c->opt.inner_fp16 != 0 && c->opt.inner_fp16 != 1)) {
+      c->opt.inner_iters > mhde::KIN_MAX || c->opt.schur < 0 || c->opt.schur > 2 ||
+      (c->opt.inner_fp16 != 0 && c->opt.inner_fp16 != 1) ||
+      (c->opt.element != 0 && c->opt.element != 1) ||
+      (c->opt.element == 1 && c->opt.schur == 1)) {   // PCD needs a continuous pressure
     delete c;
     return MHDE_EINVAL;
   }
-  std::string e = build_fe(mesh, c->fe);
+  std::string e = build_fe(mesh, c->fe, c->opt.element);
+  if (e.empty() && (c->opt.element == 1 || c->opt.schur == 2)) e = build_algebraic_laplacian(c->fe);
   if (e.empty()) e = build_amg(c->fe, 512);
   if (!e.empty()) {
     // keep the message reachable through a NULL-safe path
@@ -511,6 +526,7 @@ int mhde_get_sizes(const mhde_ctx* c, mhde_sizes* z) {
   z->nnz_saddle = 2 * z->nnz_F + 4 * z->nnz_B + 1;
   z->n_boundary = (int)c->fe.bnd_nodes.size();
   z->amg_levels = c->amg_levels;
+  z->nnz_L = c->fe.Kp.nnz();
   return MHDE_OK;
 }
 
@@ -574,6 +590,13 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
   CU(up(c->d_node_ptr, fe.node_ptr, st));
   CU(up(c->d_node_slot, fe.node_slot, st));
   CU(up(c->d_mp, fe.mp_lumped, st));
+  {
+    std::vector<double> di = fe.lsc_dinv;
+    di.resize(fe.n2, 0.0);
+    std::vector<float> dif(di.begin(), di.end());
+    CU(up(c->d_lsc_dinv, di, st));
+    CU(up(c->d_lsc_dinvf, dif, st));
+  }
   std::vector<float> mpf(fe.mp_lumped.begin(), fe.mp_lumped.end());
   CU(up(c->d_mpf, mpf, st));
   std::vector<double> cc(c->Jp, 0.0), cs(c->Jp, 0.0);
@@ -606,6 +629,12 @@ int mhde_bind(mhde_ctx* c, void* ws, size_t bytes, void* stream_v, void* stream_
     if (l + 1 < fe.amg.levels.size()) {
       CU(put(H.P, D.P, nullptr));
       CU(put(H.R, D.R, nullptr));
+      if (D.bs > 0) {
+        CU(up(D.blk_idx, H.blk_idx, st));
+        CU(up(D.blk_inv, H.blk_inv, st));
+        keep_f.emplace_back(H.blk_inv.begin(), H.blk_inv.end());
+        CU(up(D.blk_invf, keep_f.back(), st));
+      }
     }
   }
   CU(up(c->d_coarse_inv, fe.amg.coarse_inv, st));
@@ -1201,7 +1230,7 @@ int mhde_probe_spmm(mhde_ctx* c, int which, int precision, const double* X, doub
 int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
   int rc = probe_assemble(c, which);
   if (rc) return rc;
-  if (!ms || reps < 1 || kernel < 0 || kernel > 8) return fail(c, MHDE_EINVAL, "bad kernel id, reps or ms");
+  if (!ms || reps < 1 || kernel < 0 || kernel > 9) return fail(c, MHDE_EINVAL, "bad kernel id, reps or ms");
   Sub& s = c->sub[which];
   cudaStream_t st = s.stream;
   const size_t vs = (size_t)c->n_rows * c->Jp;
@@ -1211,7 +1240,7 @@ int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
   double* yd = s.X;
   CU(cudaMemcpyAsync(xd, s.S, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const bool fp64 = c->opt.precision == MHDE_PREC_FP64;
-  const bool block_input = kernel == 5 || kernel == 6 || kernel == 7 || kernel == 8;
+  const bool block_input = kernel == 5 || kernel == 6 || kernel == 7 || kernel == 8 || kernel == 9;
   if (kernel == 1 || (!fp64 && block_input)) launch_d2f(xd, (float*)s.Wk, vs, st);
   if (fp64 && block_input)
     CU(cudaMemcpyAsync(s.Wk, xd, vs * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1271,6 +1300,19 @@ int mhde_time_kernel(mhde_ctx* c, int which, int kernel, int reps, double* ms) {
       case 8:
         gram_any(c, which, s.basis, vs, kb, s.Wk, false);
         break;
+      case 9: {
+        // residual b - L x on the finest pressure level (pressure parts of
+        // the block input and output)
+        const size_t poff = (size_t)2 * c->fe.n2 * c->Jp;
+        const DevCsr& L = c->amg_ops[0].A;
+        if (fp64)
+          launch_csr<double>(L.nrows, L.rowptr, L.col, L.val, nullptr, 0.0, (const double*)s.Wk + poff,
+                             (const double*)s.Wk + poff, (double*)s.Zk + poff, 1, c->Jp, st);
+        else
+          launch_csr<float>(L.nrows, L.rowptr, L.col, L.valf, nullptr, 0.f, (const float*)s.Wk + poff,
+                            (const float*)s.Wk + poff, (float*)s.Zk + poff, 1, c->Jp, st);
+        break;
+      }
     }
   };
   once();

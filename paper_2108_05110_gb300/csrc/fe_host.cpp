@@ -65,8 +65,10 @@ void invert_map(const std::vector<int>& slot_nnz, long long nnz, std::vector<int
 
 }  // namespace
 
-std::string build_fe(const mhde_mesh* mesh, FeHost& fe) {
+std::string build_fe(const mhde_mesh* mesh, FeHost& fe, int element) {
   if (!mesh || !mesh->xy || !mesh->tri) return "mesh pointers are NULL";
+  if (element != 0 && element != 1) return "element must be 0 or 1";
+  fe.element = element;
   if (mesh->nv < 3 || mesh->nt < 1) return "mesh needs at least 3 vertices and 1 triangle";
   fe.nv = mesh->nv;
   fe.nt = mesh->nt;
@@ -105,7 +107,11 @@ std::string build_fe(const mhde_mesh* mesh, FeHost& fe) {
   unique_keys(ekeys, fe.edges, eid);
   fe.ne = (int)fe.edges.size();
   fe.n2 = nv + fe.ne;
-  fe.np = nv;
+  fe.np = element == 1 ? 3 * nt : nv;
+  // pressure dof of local vertex i on triangle e
+  auto prow = [&](int e, int i) -> long long {
+    return element == 1 ? 3LL * e + i : (long long)fe.tri[3 * e + i];
+  };
   fe.edge_count.assign(fe.ne, 0);
   for (int id : eid) fe.edge_count[id]++;
   for (int c : fe.edge_count)
@@ -153,8 +159,7 @@ std::string build_fe(const mhde_mesh* mesh, FeHost& fe) {
     for (int e = 0; e < nt; ++e)
       for (int i = 0; i < 3; ++i)
         for (int a = 0; a < 6; ++a)
-          keys[18 * (size_t)e + 6 * i + a] =
-              (long long)fe.tri[3 * e + i] * fe.n2 + fe.dofs[6 * (size_t)e + a];
+          keys[18 * (size_t)e + 6 * i + a] = prow(e, i) * fe.n2 + fe.dofs[6 * (size_t)e + a];
     std::vector<long long> uniq;
     std::vector<int> slot_nnz;
     unique_keys(keys, uniq, slot_nnz);
@@ -179,16 +184,18 @@ std::string build_fe(const mhde_mesh* mesh, FeHost& fe) {
     for (size_t s = 0; s < slot_node.size(); ++s) slot_node[s] = fe.dofs[s];
     invert_map(slot_node, fe.n2, fe.node_ptr, fe.node_slot);
   }
-  // pressure Laplacian (P1 stiffness, node 0 pinned) and lumped pressure mass
-  {
+  // lumped pressure mass: area / 3 per local vertex, summed per pressure dof
+  fe.mp_lumped.assign(fe.np, 0.0);
+  for (int e = 0; e < nt; ++e)
+    for (int i = 0; i < 3; ++i) fe.mp_lumped[prow(e, i)] += 0.5 * fe.geom[8 * (size_t)e + 6] / 3.0;
+  // pressure Laplacian of the continuous pressure (P1 stiffness, node 0 pinned)
+  if (element == 0) {
     std::vector<long long> keys((size_t)nt * 9);
     std::vector<double> vals((size_t)nt * 9);
-    fe.mp_lumped.assign(fe.np, 0.0);
     for (int e = 0; e < nt; ++e) {
       const double* g = &fe.geom[8 * (size_t)e];
       double area = 0.5 * g[6];
       for (int i = 0; i < 3; ++i) {
-        fe.mp_lumped[fe.tri[3 * e + i]] += area / 3.0;
         for (int k = 0; k < 3; ++k) {
           keys[9 * (size_t)e + 3 * i + k] = (long long)fe.tri[3 * e + i] * fe.np + fe.tri[3 * e + k];
           vals[9 * (size_t)e + 3 * i + k] = area * (g[2 * i] * g[2 * k] + g[2 * i + 1] * g[2 * k + 1]);
@@ -377,6 +384,161 @@ bool dense_inverse(int n, std::vector<double> A, std::vector<double>& inv) {
 
 }  // namespace
 
+std::string build_algebraic_laplacian(FeHost& fe) {
+  const int nt = fe.nt, n2 = fe.n2, np = fe.np;
+  // D: the diagonal of the P2 mass matrix scaled on every triangle so that
+  // its entries sum to the area (vertices area/19, edge midpoints
+  // 16 area/57: the diagonal entries area/30 and 8 area/45 times 30/19)
+  std::vector<double> D(n2, 0.0);
+  for (int e = 0; e < nt; ++e) {
+    const double area = 0.5 * fe.geom[8 * (size_t)e + 6];
+    for (int a = 0; a < 3; ++a) D[fe.dofs[6 * (size_t)e + a]] += area / 19.0;
+    for (int a = 3; a < 6; ++a) D[fe.dofs[6 * (size_t)e + a]] += 16.0 * area / 57.0;
+  }
+  fe.lsc_dinv.assign(n2, 0.0);
+  for (int k = 0; k < n2; ++k)
+    if (!fe.is_bnd[k] && D[k] > 0.0) fe.lsc_dinv[k] = 1.0 / D[k];
+  // element values of B_d (slot 18e + 6i + a): -(d phi_a / d x_d, lambda_i),
+  // integrated exactly with (lambda_i, lambda_k) = area (1 + delta_ik) / 12:
+  // vertex a: -(area/3) delta_ai grad lambda_a; midpoint of edge (p, q):
+  // -(area/3) ((1 + delta_pi) grad lambda_q + (1 + delta_qi) grad lambda_p)
+  std::vector<double> loc[2] = {std::vector<double>((size_t)nt * 18), std::vector<double>((size_t)nt * 18)};
+  for (int e = 0; e < nt; ++e) {
+    const double* g = &fe.geom[8 * (size_t)e];
+    const double a3 = 0.5 * g[6] / 3.0;
+    for (int i = 0; i < 3; ++i)
+      for (int d = 0; d < 2; ++d) {
+        double* v = &loc[d][18 * (size_t)e + 6 * i];
+        for (int a = 0; a < 3; ++a) v[a] = (a == i) ? -a3 * g[2 * a + d] : 0.0;
+        for (int l = 0; l < 3; ++l) {
+          const int p = LE[l][0], q = LE[l][1];
+          v[3 + l] = -a3 * ((1.0 + (p == i)) * g[2 * q + d] + (1.0 + (q == i)) * g[2 * p + d]);
+        }
+      }
+  }
+  // Bs = [Bx | By] (np x 2 n2), assembled in B's pattern (slots summed in
+  // ascending order), and W = diag(D^{-1}, D^{-1}) Bs^T
+  const long long nb = fe.B.nnz();
+  HostCsr Bs;
+  Bs.nrows = np;
+  Bs.ncols = 2 * n2;
+  Bs.rowptr.assign(np + 1, 0);
+  Bs.col.resize(2 * (size_t)nb);
+  Bs.val.resize(2 * (size_t)nb);
+  for (int r = 0; r < np; ++r) {
+    const int k0 = fe.B.rowptr[r], k1 = fe.B.rowptr[r + 1];
+    const size_t o = 2 * (size_t)k0;
+    for (int d = 0; d < 2; ++d)
+      for (int k = k0; k < k1; ++k) {
+        double sum = 0.0;
+        for (int t = fe.b_gather_ptr[k]; t < fe.b_gather_ptr[k + 1]; ++t) sum += loc[d][fe.b_gather_slot[t]];
+        const size_t w = o + (size_t)d * (k1 - k0) + (k - k0);
+        Bs.col[w] = fe.B.col[k] + d * n2;
+        Bs.val[w] = sum;
+      }
+    Bs.rowptr[r + 1] = 2 * k1;
+  }
+  HostCsr W;
+  csr_transpose(Bs, W);
+  for (int r = 0; r < W.nrows; ++r)
+    for (int k = W.rowptr[r]; k < W.rowptr[r + 1]; ++k) W.val[k] *= fe.lsc_dinv[r % n2];
+  csr_matmul(Bs, W, fe.Kp);
+  // pin dof 0: identity row and column
+  for (int r = 0; r < np; ++r)
+    for (int k = fe.Kp.rowptr[r]; k < fe.Kp.rowptr[r + 1]; ++k) {
+      const int c = fe.Kp.col[k];
+      if (r == 0 || c == 0) fe.Kp.val[k] = (r == c) ? 1.0 : 0.0;
+    }
+  for (int r = 1; r < np; ++r) {
+    bool diag = false;
+    for (int k = fe.Kp.rowptr[r]; k < fe.Kp.rowptr[r + 1]; ++k)
+      if (fe.Kp.col[k] == r && fe.Kp.val[k] > 0.0) diag = true;
+    if (!diag) return "pressure dof " + std::to_string(r) + " is not coupled to any interior velocity node";
+  }
+  fe.p1_gather_ptr.clear();
+  fe.p1_gather_slot.clear();
+  return "";
+}
+
+namespace {
+
+// Smoother blocks of the discontinuous pressure: the nine dofs of every macro
+// triangle when the mesh is a barycenter refinement (every triangle has one
+// vertex that is interior, has exactly three triangles around it and sits at
+// the mean of their other vertices), else the three dofs of every triangle.
+void pressure_blocks(const FeHost& fe, int& bs, std::vector<int>& idx) {
+  const int nv = fe.nv, nt = fe.nt;
+  std::vector<int> cnt(nv + 1, 0);
+  for (int t = 0; t < 3 * nt; ++t) cnt[fe.tri[t] + 1]++;
+  for (int v = 0; v < nv; ++v) cnt[v + 1] += cnt[v];
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1), vt(3 * (size_t)nt);
+  for (int t = 0; t < 3 * nt; ++t) vt[fill[fe.tri[t]]++] = t / 3;
+  std::vector<int> owner(nt, -1);
+  std::vector<int> macro;
+  bool ok = true;
+  for (int v = 0; v < nv && ok; ++v) {
+    if (fe.is_bnd[v] || cnt[v + 1] - cnt[v] != 3) continue;
+    int ts[3] = {vt[cnt[v]], vt[cnt[v] + 1], vt[cnt[v] + 2]};
+    double mx = 0.0, my = 0.0, ext = 0.0;
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        int u = fe.tri[3 * ts[k] + l];
+        if (u == v) continue;
+        mx += fe.xy[2 * u] / 6.0;          // each outer vertex is seen from two triangles
+        my += fe.xy[2 * u + 1] / 6.0;
+        ext = std::max(ext, std::fabs(fe.xy[2 * u] - fe.xy[2 * v]) + std::fabs(fe.xy[2 * u + 1] - fe.xy[2 * v + 1]));
+      }
+    if (std::fabs(mx - fe.xy[2 * v]) + std::fabs(my - fe.xy[2 * v + 1]) > 1e-9 * ext) continue;
+    for (int k = 0; k < 3; ++k) {
+      if (owner[ts[k]] >= 0) ok = false;
+      owner[ts[k]] = v;
+      macro.push_back(ts[k]);
+    }
+  }
+  for (int t = 0; t < nt && ok; ++t)
+    if (owner[t] < 0) ok = false;
+  idx.clear();
+  if (ok) {
+    bs = 9;
+    for (int t : macro)
+      for (int i = 0; i < 3; ++i) idx.push_back(3 * t + i);
+  } else {
+    bs = 3;
+    for (int d = 0; d < 3 * nt; ++d) idx.push_back(d);
+  }
+}
+
+double spectral_radius_BinvA(const HostCsr& A, int bs, const std::vector<int>& idx, const std::vector<double>& inv) {
+  const int n = A.nrows, nb = n / bs;
+  std::vector<double> x(n), y(n), ax(n);
+  for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * std::sin(1.7 * i + 0.3);
+  double lam = 1.0;
+  for (int it = 0; it < 40; ++it) {
+    double nx = 0.0;
+    for (double v : x) nx += v * v;
+    nx = std::sqrt(nx);
+    for (double& v : x) v /= nx;
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) s += A.val[k] * x[A.col[k]];
+      ax[i] = s;
+    }
+    for (int b = 0; b < nb; ++b)
+      for (int i = 0; i < bs; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < bs; ++j) s += inv[((size_t)b * bs + i) * bs + j] * ax[idx[(size_t)b * bs + j]];
+        y[idx[(size_t)b * bs + i]] = s;
+      }
+    double ny = 0.0;
+    for (double v : y) ny += v * v;
+    lam = std::sqrt(ny);
+    x.swap(y);
+  }
+  return lam * 1.05;
+}
+
+}  // namespace
+
 std::string build_amg(FeHost& fe, int coarse_max) {
   AmgHost& amg = fe.amg;
   amg.levels.clear();
@@ -390,6 +552,50 @@ std::string build_amg(FeHost& fe, int coarse_max) {
     L.omega = 4.0 / (3.0 * rho);
     int n = L.A.nrows;
     if (n <= coarse_max) break;
+    if (lev == 0 && fe.element == 1) {
+      // discontinuous pressure: the first coarse space is the continuous P1
+      // space on the mesh vertices, injected into P1disc (P: dof 3t + i takes
+      // the value at vertex tri[3t + i]; the pinned dof 0 takes none), and
+      // the fine level is smoothed by block Jacobi over macro triangles
+      HostCsr P;
+      P.nrows = n;
+      P.ncols = fe.nv;
+      P.rowptr.assign(n + 1, 0);
+      for (int d = 0; d < n; ++d) {
+        if (d != 0) {
+          P.col.push_back(fe.tri[d]);
+          P.val.push_back(1.0);
+        }
+        P.rowptr[d + 1] = (int)P.col.size();
+      }
+      pressure_blocks(fe, L.bs, L.blk_idx);
+      const int bs = L.bs, nb = n / bs;
+      std::vector<int> pos(n, -1);
+      L.blk_inv.assign((size_t)nb * bs * bs, 0.0);
+      for (int b = 0; b < nb; ++b) {
+        for (int i = 0; i < bs; ++i) pos[L.blk_idx[(size_t)b * bs + i]] = i;
+        std::vector<double> blk((size_t)bs * bs, 0.0), inv;
+        for (int i = 0; i < bs; ++i) {
+          const int r = L.blk_idx[(size_t)b * bs + i];
+          for (int k = L.A.rowptr[r]; k < L.A.rowptr[r + 1]; ++k)
+            if (pos[L.A.col[k]] >= 0) blk[(size_t)i * bs + pos[L.A.col[k]]] = L.A.val[k];
+        }
+        for (int i = 0; i < bs; ++i) pos[L.blk_idx[(size_t)b * bs + i]] = -1;
+        if (!dense_inverse(bs, blk, inv)) return "singular pressure smoother block " + std::to_string(b);
+        std::copy(inv.begin(), inv.end(), L.blk_inv.begin() + (size_t)b * bs * bs);
+      }
+      L.blk_omega = 1.6 / spectral_radius_BinvA(L.A, bs, L.blk_idx, L.blk_inv);
+      HostCsr R, RA, Ac;
+      csr_transpose(P, R);
+      csr_matmul(R, L.A, RA);
+      csr_matmul(RA, P, Ac);
+      L.P = P;
+      L.R = R;
+      AmgLevelHost next;
+      next.A = Ac;
+      amg.levels.push_back(next);
+      continue;
+    }
     std::vector<int> agg;
     int na = aggregate(L.A, 0.08, agg);
     if (na >= n || na < 1) break;

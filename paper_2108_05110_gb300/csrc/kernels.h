@@ -101,6 +101,18 @@ void launch_precond_p(int np, int Jp, const T* x, const T* rp, const T* mp, T in
 template <typename T>
 void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp, T* tu, int ld,
                      cudaStream_t st);
+// block-Jacobi sweep x_out = x_in + omega Binv r over nb blocks of bs dofs
+// (idx [nb][bs], inv [nb][bs][bs]); x_in null means zero; x_out may be x_in
+template <typename T>
+void launch_block_jacobi(int nb, int bs, const int* idx, const T* inv, T omega, const T* x_in, const T* r,
+                         T* x_out, int Jp, cudaStream_t st);
+// least-squares commutator middle product z = B D^{-1} F D^{-1} B^T y:
+// t = D^{-1} B^T y and s = D^{-1} F t (velocity rows, D^{-1} = dinv, zero on
+// Dirichlet rows), z = B s (pressure rows); y's dof 0 is taken as zero and
+// z_0 = 0 (the pinned dof)
+template <typename T>
+void launch_lsc_middle(const mhde_ctx* c, const T* Fval, const T* BTval, const T* Bval, const T* dinv,
+                       const T* y, T* t, T* s, T* z, int ld, cudaStream_t st);
 // Gram partial sums: part[chunk][i][p][q] = sum_rows V_i[row][p] W[row][q].
 // err: the calling subproblem's device error word; with it the FP32 Gram may
 // take the TMA-staged kernel, which sets *err = 1 when a stage never lands

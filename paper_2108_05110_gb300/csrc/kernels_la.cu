@@ -489,6 +489,141 @@ void launch_bt_apply(const mhde_ctx* c, const T* BTval, const T* ru, const T* zp
              c->fe.n2, nch, c->BT.rowptr, c->BT.col, BTval, c->d_isbnd, ru, zp, tu);
 }
 
+// ------------------------------------------------------------ block-Jacobi smoothing
+// x_out = x_in + omega Binv r over blocks of bs dofs (idx[b][i]); x_in null
+// means x_in = 0.  Every thread reads x_in and writes x_out at its own row
+// only, so x_out may be x_in; r must be another buffer.
+template <typename T>
+__global__ void k_block_jacobi(int nb, int bs, int nch, const int* __restrict__ idx, const T* __restrict__ inv,
+                               T omega, const T* x_in, const T* __restrict__ r, T* x_out) {
+  pdl_wait();
+  pdl_trigger();
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)nb * bs * nch) return;
+  const int b = (int)(tid / ((long long)bs * nch));
+  const int rem = (int)(tid % ((long long)bs * nch));
+  const int i = rem / nch, ch = rem % nch;
+  const int* id = idx + (size_t)b * bs;
+  const T* Bi = inv + ((size_t)b * bs + i) * bs;
+  const V* rv = reinterpret_cast<const V*>(r);
+  V acc = vzero(V());
+  for (int j = 0; j < bs; ++j) vfma(acc, Bi[j], rv[(size_t)id[j] * nch + ch]);
+  const size_t o = (size_t)id[i] * nch + ch;
+  V* xo = reinterpret_cast<V*>(x_out);
+  if (x_in) {
+    const V xi = reinterpret_cast<const V*>(x_in)[o];
+    xo[o] = vaxpby(T(1), xi, omega, acc);
+  } else {
+    xo[o] = vaxpby(omega, acc, T(0), vzero(V()));
+  }
+}
+
+template <typename T>
+void launch_block_jacobi(int nb, int bs, const int* idx, const T* inv, T omega, const T* x_in, const T* r,
+                         T* x_out, int Jp, cudaStream_t st) {
+  count_launch();
+  const int nch = Jp / Vec<T>::W;
+  const long long n = (long long)nb * bs * nch;
+  launch_pdl(k_block_jacobi<T>, dim3(nblk(n, 256)), dim3(256), 0, st, nb, bs, nch, idx, inv, omega, x_in, r, x_out);
+}
+
+// ------------------------------------------------------------ least-squares commutator
+// The three products between the two pressure-Laplacian solves of
+//   S^{-1} ~ L^{-1} (B D^{-1} F D^{-1} B^T) L^{-1},  L = B D^{-1} B^T,
+// with D^{-1} zero on Dirichlet nodes (their velocities are fixed) and the
+// pinned pressure dof 0 taken as zero on both sides.
+template <typename T>
+__global__ void k_lsc_bt(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
+                         const T* __restrict__ BT, const T* __restrict__ dinv, const T* __restrict__ y,
+                         T* __restrict__ t) {
+  pdl_wait();
+  pdl_trigger();
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)n2 * nch) return;
+  const int a = (int)(tid / nch), ch = (int)(tid % nch);
+  const V* yv = reinterpret_cast<const V*>(y);
+  V* tv = reinterpret_cast<V*>(t);
+  const size_t o0 = ((size_t)(2 * a)) * nch + ch, o1 = o0 + nch;
+  V acc0 = vzero(V()), acc1 = vzero(V());
+  const T di = dinv[a];
+  if (di != T(0)) {
+    for (int k = rp[a]; k < rp[a + 1]; ++k) {
+      const int j = col[k];
+      if (j == 0) continue;
+      const V yj = yv[(size_t)j * nch + ch];
+      vfma(acc0, BT[2 * (size_t)k], yj);
+      vfma(acc1, BT[2 * (size_t)k + 1], yj);
+    }
+  }
+  tv[o0] = vaxpby(di, acc0, T(0), vzero(V()));
+  tv[o1] = vaxpby(di, acc1, T(0), vzero(V()));
+}
+
+template <typename T>
+__global__ void k_lsc_f(int n2, int nch, const int* __restrict__ rp, const int* __restrict__ col,
+                        const T* __restrict__ F, const T* __restrict__ dinv, const T* __restrict__ t,
+                        T* __restrict__ s) {
+  pdl_wait();
+  pdl_trigger();
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)n2 * nch) return;
+  const int a = (int)(tid / nch), ch = (int)(tid % nch);
+  const V* tv = reinterpret_cast<const V*>(t);
+  V* sv = reinterpret_cast<V*>(s);
+  const size_t o0 = ((size_t)(2 * a)) * nch + ch, o1 = o0 + nch;
+  V acc0 = vzero(V()), acc1 = vzero(V());
+  const T di = dinv[a];
+  if (di != T(0)) {
+    for (int k = rp[a]; k < rp[a + 1]; ++k) {
+      const size_t b = (size_t)(2 * col[k]) * nch + ch;
+      vfma(acc0, F[k], tv[b]);
+      vfma(acc1, F[k], tv[b + nch]);
+    }
+  }
+  sv[o0] = vaxpby(di, acc0, T(0), vzero(V()));
+  sv[o1] = vaxpby(di, acc1, T(0), vzero(V()));
+}
+
+template <typename T>
+__global__ void k_lsc_b(int np, int nch, const int* __restrict__ rp, const int* __restrict__ col,
+                        const T* __restrict__ B, const T* __restrict__ s, T* __restrict__ z) {
+  pdl_wait();
+  pdl_trigger();
+  using V = typename Vec<T>::type;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)np * nch) return;
+  const int i = (int)(tid / nch), ch = (int)(tid % nch);
+  const V* sv = reinterpret_cast<const V*>(s);
+  V acc = vzero(V());
+  if (i != 0) {
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const size_t b = (size_t)(2 * col[k]) * nch + ch;
+      vfma(acc, B[2 * (size_t)k], sv[b]);
+      vfma(acc, B[2 * (size_t)k + 1], sv[b + nch]);
+    }
+  }
+  reinterpret_cast<V*>(z)[tid] = acc;
+}
+
+template <typename T>
+void launch_lsc_middle(const mhde_ctx* c, const T* Fval, const T* BTval, const T* Bval, const T* dinv,
+                       const T* y, T* t, T* s, T* z, int ld, cudaStream_t st) {
+  const int nch = ld / Vec<T>::W;
+  const long long nv = (long long)c->fe.n2 * nch, np = (long long)c->fe.np * nch;
+  count_launch();
+  launch_pdl(k_lsc_bt<T>, dim3(nblk(nv, 256)), dim3(256), 0, st, c->fe.n2, nch, c->BT.rowptr, c->BT.col, BTval,
+             dinv, y, t);
+  count_launch();
+  launch_pdl(k_lsc_f<T>, dim3(nblk(nv, 256)), dim3(256), 0, st, c->fe.n2, nch, c->F.rowptr, c->F.col, Fval, dinv,
+             (const T*)t, s);
+  count_launch();
+  launch_pdl(k_lsc_b<T>, dim3(nblk(np, 256)), dim3(256), 0, st, c->fe.np, nch, c->B.rowptr, c->B.col, Bval,
+             (const T*)s, z);
+}
+
 // ------------------------------------------------------------ block Gram
 // CTA `chunk` covers a contiguous range of rows.  For every basis block i the
 // CTA streams 64-row tiles of V_i and W (contiguous in memory) into shared
@@ -1559,6 +1694,10 @@ void launch_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
   template void launch_precond_p<T>(int, int, const T*, const T*, const T*, T, T, const int*, const int*,  \
                                     const T*, T*, cudaStream_t);                                        \
   template void launch_bt_apply<T>(const mhde_ctx*, const T*, const T*, const T*, T*, int, cudaStream_t); \
+  template void launch_block_jacobi<T>(int, int, const int*, const T*, T, const T*, const T*, T*, int,      \
+                                      cudaStream_t);                                                   \
+  template void launch_lsc_middle<T>(const mhde_ctx*, const T*, const T*, const T*, const T*, const T*, T*, \
+                                     T*, T*, int, cudaStream_t);                                        \
   template void launch_gram<T>(const T*, size_t, int, const T*, int, int, int, int, double*, double*, \
                                cudaStream_t, bool, int*, bool);                                      \
   template void launch_make_coef<T>(const double*, const double*, int, int, T*, cudaStream_t);       \

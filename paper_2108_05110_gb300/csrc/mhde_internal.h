@@ -34,6 +34,14 @@ struct AmgLevelHost {
   std::vector<double> dinv;   // 1 / diag(A)
   double omega = 0.0;         // Jacobi damping 4 / (3 rho(D^-1 A))
   HostCsr P, R;               // prolongation to this level from the next, R = P^T
+  // block-Jacobi smoother instead of point Jacobi (level 0 of the
+  // discontinuous pressure): bs > 0 gives blocks of bs dofs
+  // blk_idx[b*bs + i] with dense inverses of A's diagonal blocks
+  // blk_inv[b][bs][bs] and damping blk_omega = 1.6 / rho(Binv A)
+  int bs = 0;
+  std::vector<int> blk_idx;
+  std::vector<double> blk_inv;
+  double blk_omega = 0.0;
 };
 
 struct AmgHost {
@@ -44,6 +52,7 @@ struct AmgHost {
 
 struct FeHost {
   int nv = 0, nt = 0, ne = 0, n2 = 0, np = 0;
+  int element = 0;                        // 0 continuous P1 pressure, 1 discontinuous (3 dofs per triangle)
   std::vector<double> xy;                 // [nv][2]
   std::vector<int> tri;                   // [nt][3]
   std::vector<long long> edges;           // sorted keys a * nv + b, a < b
@@ -72,18 +81,27 @@ struct FeHost {
   std::vector<int> node_ptr;              // [n2 + 1]
   std::vector<int> node_slot;             // [nt*6]
 
-  // pressure Laplacian (P1 stiffness, node 0 pinned) and lumped pressure mass;
-  // the element -> nnz map of its P1 pattern (slots e*9 + 3i + k) also
-  // assembles the pressure convection matrix of the PCD Schur approximation
+  // pressure Laplacian (dof 0 pinned) and lumped pressure mass.  Either the
+  // P1 stiffness of the continuous pressure, whose element -> nnz map (slots
+  // e*9 + 3i + k) also assembles the pressure convection matrix of the PCD
+  // Schur approximation, or the algebraic B D^{-1} B^T (build_algebraic_laplacian)
   HostCsr Kp;
-  std::vector<int> p1_gather_ptr;         // [nnzKp + 1]
+  std::vector<int> p1_gather_ptr;         // [nnzKp + 1] (P1 stiffness only)
   std::vector<int> p1_gather_slot;        // [nt*9]
   std::vector<double> mp_lumped;          // [np]
+  std::vector<double> lsc_dinv;           // [n2] 1/D on interior P2 nodes, 0 on Dirichlet nodes
   AmgHost amg;
 };
 
-// Builds everything above; returns an empty string or an error message.
-std::string build_fe(const mhde_mesh* mesh, FeHost& fe);
+// Builds everything above but Kp for element 1 (see below); returns an empty
+// string or an error message.  element: 0 continuous P1 pressure
+// (Taylor-Hood), 1 discontinuous P1 pressure (Scott-Vogelius).
+std::string build_fe(const mhde_mesh* mesh, FeHost& fe, int element);
+// Replaces Kp by L = sum_d B_d D^{-1} B_d^T over the interior P2 nodes (D the
+// diagonal of the P2 mass matrix scaled to the element areas), dof 0 pinned:
+// the pressure Laplacian of the discontinuous pressure and of the
+// least-squares commutator.  Fills lsc_dinv.
+std::string build_algebraic_laplacian(FeHost& fe);
 std::string build_amg(FeHost& fe, int coarse_max);
 
 // ----------------------------------------------------------------- small dense (host, FP64)
@@ -132,6 +150,10 @@ struct DevCsr {
 struct DevAmgLevel {
   DevCsr A, P, R;
   double omega = 0.0;
+  int bs = 0, nb = 0;                           // block-Jacobi smoother (bs > 0): nb blocks of bs dofs
+  int* blk_idx = nullptr;                       // [nb][bs]
+  double* blk_inv = nullptr;  float* blk_invf = nullptr;   // [nb][bs][bs]
+  double blk_omega = 0.0;
   double* x = nullptr;  float* xf = nullptr;   // [n][Jp] work vectors
   double* b = nullptr;  float* bf = nullptr;
   double* r = nullptr;  float* rf = nullptr;
@@ -240,6 +262,8 @@ struct mhde_ctx {
   int* d_p1slot = nullptr;
   int* d_node_ptr = nullptr;
   int* d_node_slot = nullptr;
+  double* d_lsc_dinv = nullptr;        // [n2] 1/D of the least-squares commutator (0 on Dirichlet nodes)
+  float* d_lsc_dinvf = nullptr;
   double* d_mp = nullptr;              // lumped pressure mass [np]
   float* d_mpf = nullptr;
   double* d_Mloc = nullptr;            // scratch for the constant assembly [nt][36]

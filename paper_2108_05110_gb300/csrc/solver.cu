@@ -56,9 +56,11 @@ template <> struct Prec<double> {
   static const double* B(const mhde_ctx* c) { return c->B.val; }
   static const double* BT(const mhde_ctx* c) { return c->BT.val; }
   static const double* mp(const mhde_ctx* c) { return c->d_mp; }
+  static const double* lscd(const mhde_ctx* c) { return c->d_lsc_dinv; }
   static const double* Aval(const DevCsr& A) { return A.val; }
   static const double* Adinv(const DevCsr& A) { return A.dinv; }
   static double* x(DevAmgLevel& L) { return L.x; }
+  static const double* blkinv(const DevAmgLevel& L) { return L.blk_inv; }
   static double* b(DevAmgLevel& L) { return L.b; }
   static double* r(DevAmgLevel& L) { return L.r; }
   static const double* cinv(const mhde_ctx* c) { return c->d_coarse_inv; }
@@ -72,9 +74,11 @@ template <> struct Prec<float> {
   static const float* B(const mhde_ctx* c) { return c->B.valf; }
   static const float* BT(const mhde_ctx* c) { return c->BT.valf; }
   static const float* mp(const mhde_ctx* c) { return c->d_mpf; }
+  static const float* lscd(const mhde_ctx* c) { return c->d_lsc_dinvf; }
   static const float* Aval(const DevCsr& A) { return A.valf; }
   static const float* Adinv(const DevCsr& A) { return A.dinvf; }
   static float* x(DevAmgLevel& L) { return L.xf; }
+  static const float* blkinv(const DevAmgLevel& L) { return L.blk_invf; }
   static float* b(DevAmgLevel& L) { return L.bf; }
   static float* r(DevAmgLevel& L) { return L.rf; }
   static const float* cinv(const mhde_ctx* c) { return c->d_coarse_invf; }
@@ -96,6 +100,30 @@ static void vcycle(const mhde_ctx* c, Sub& s, int l, const T* b, T* x, int Jp) {
   const DevCsr& A = op.A;
   const T om = (T)op.omega;
   const int nsw = std::max(1, c->opt.amg_sweeps);
+  if (op.bs > 0) {
+    // block-Jacobi smoothing in place on x; residuals are staged in this
+    // level's right-hand-side buffer, which the finest level (the only one
+    // with blocks; its right-hand side comes from the caller) leaves unused
+    T* tmp = Prec<T>::b(w);
+    const T bom = (T)op.blk_omega;
+    launch_block_jacobi<T>(op.nb, op.bs, op.blk_idx, Prec<T>::blkinv(op), bom, nullptr, b, x, Jp, st);
+    for (int k = 1; k < nsw; ++k) {
+      launch_csr<T>(A.nrows, A.rowptr, A.col, Prec<T>::Aval(A), nullptr, T(0), x, b, tmp, 1, Jp, st);
+      launch_block_jacobi<T>(op.nb, op.bs, op.blk_idx, Prec<T>::blkinv(op), bom, x, tmp, x, Jp, st);
+    }
+    DevAmgLevel& wn = s.amg[l + 1];
+    launch_csr<T>(A.nrows, A.rowptr, A.col, Prec<T>::Aval(A), nullptr, T(0), x, b, tmp, 1, Jp, st);
+    launch_csr<T>(op.R.nrows, op.R.rowptr, op.R.col, Prec<T>::Aval(op.R), nullptr, T(0), tmp, nullptr,
+                  Prec<T>::b(wn), 0, Jp, st);
+    vcycle<T>(c, s, l + 1, Prec<T>::b(wn), Prec<T>::x(wn), Jp);
+    launch_csr<T>(op.P.nrows, op.P.rowptr, op.P.col, Prec<T>::Aval(op.P), nullptr, T(0), Prec<T>::x(wn), nullptr, x,
+                  4, Jp, st);
+    for (int k = 0; k < nsw; ++k) {
+      launch_csr<T>(A.nrows, A.rowptr, A.col, Prec<T>::Aval(A), nullptr, T(0), x, b, tmp, 1, Jp, st);
+      launch_block_jacobi<T>(op.nb, op.bs, op.blk_idx, Prec<T>::blkinv(op), bom, x, tmp, x, Jp, st);
+    }
+    return;
+  }
   T* cur = x;
   T* other = Prec<T>::r(w);
   // pre-smoothing from zero
@@ -136,6 +164,24 @@ static void vcycle(const mhde_ctx* c, Sub& s, int l, const T* b, T* x, int Jp) {
     cudaMemcpyAsync(x, cur, (size_t)A.nrows * Jp * sizeof(T), cudaMemcpyDeviceToDevice, st);
 }
 
+// x0 = L^{-1} rhs approximated by amg_cycles V-cycles on the pressure
+// Laplacian; further cycles work on the residual, x0 += V(rhs - L x0),
+// staged in the pressure parts of the preconditioner temporaries Tk / Pk
+template <typename T>
+static void amg_solve(const mhde_ctx* c, Sub& s, const T* rhs, T* x0, int Jp) {
+  const size_t poff = (size_t)2 * c->fe.n2 * Jp;
+  cudaStream_t st = s.stream;
+  vcycle<T>(c, s, 0, rhs, x0, Jp);
+  for (int cyc = 1; cyc < c->opt.amg_cycles; ++cyc) {
+    const DevCsr& A0 = c->amg_ops[0].A;
+    T* res = (T*)s.Tk + poff;
+    T* corr = (T*)s.Pk + poff;
+    launch_csr<T>(A0.nrows, A0.rowptr, A0.col, Prec<T>::Aval(A0), nullptr, T(0), x0, rhs, res, 1, Jp, st);
+    vcycle<T>(c, s, 0, res, corr, Jp);
+    launch_axpby<T>(x0, T(1), x0, T(1), corr, (size_t)A0.nrows * Jp, st);
+  }
+}
+
 template <typename T>
 static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out, int Jp) {
   const size_t poff = (size_t)2 * c->fe.n2 * Jp;
@@ -144,21 +190,23 @@ static void apply_prec_raw(const mhde_ctx* c, Sub& s, const T* in, T* out, int J
   T* pk = (T*)s.Pk;
   const T* rp = in + poff;
   T* x0 = Prec<T>::x(s.amg[0]);
-  vcycle<T>(c, s, 0, rp, x0, Jp);
-  for (int cyc = 1; cyc < c->opt.amg_cycles; ++cyc) {
-    // further V-cycles on the residual: x0 += V(rp - L x0), staged in the
-    // preconditioner temporaries (velocity part of tk/pk is still free here)
-    const DevCsr& A0 = c->amg_ops[0].A;
-    T* res = tk + poff;
-    T* corr = (T*)s.Pk + poff;
-    launch_csr<T>(A0.nrows, A0.rowptr, A0.col, Prec<T>::Aval(A0), nullptr, T(0), x0, rp, res, 1, Jp, st);
-    vcycle<T>(c, s, 0, res, corr, Jp);
-    launch_axpby<T>(x0, T(1), x0, T(1), corr, (size_t)A0.nrows * Jp, st);
-  }
-  const double nu_hat = 0.5 * (c->nubar + c->nubar_m);
   const DevCsr& Kp = c->amg_ops[0].A;
-  launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), (T)(1.0 / c->dt), (T)nu_hat, Kp.rowptr, Kp.col,
-                      c->opt.schur == 1 ? Prec<T>::Np(s) : (const T*)nullptr, out + poff, st);
+  amg_solve<T>(c, s, rp, x0, Jp);
+  if (c->opt.schur == 2) {
+    // least-squares commutator: x0 = L^{-1} (B D^{-1} F D^{-1} B^T) L^{-1} rp,
+    // zp = -x0; the middle product passes through the velocity parts of
+    // Tk / Pk (free until the B^T apply below) and the pressure part of out
+    T* zmid = out + poff;
+    launch_lsc_middle<T>(c, Prec<T>::F(s), Prec<T>::BT(c), Prec<T>::B(c), Prec<T>::lscd(c), x0, tk, pk, zmid, Jp,
+                         st);
+    amg_solve<T>(c, s, zmid, x0, Jp);
+    launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), T(1), T(0), Kp.rowptr, Kp.col, (const T*)nullptr,
+                        out + poff, st);
+  } else {
+    const double nu_hat = 0.5 * (c->nubar + c->nubar_m);
+    launch_precond_p<T>(c->fe.np, Jp, x0, rp, Prec<T>::mp(c), (T)(1.0 / c->dt), (T)nu_hat, Kp.rowptr, Kp.col,
+                        c->opt.schur == 1 ? Prec<T>::Np(s) : (const T*)nullptr, out + poff, st);
+  }
   launch_bt_apply<T>(c, Prec<T>::BT(c), in, out + poff, tk, Jp, st);
   if (c->opt.inner_iters > 0) {
     launch_inner_gmres<T>(c, s, Prec<T>::FD(s), Prec<T>::Fd(s), tk, out, Jp, c->opt.inner_iters, st);

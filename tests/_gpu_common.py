@@ -28,7 +28,7 @@ def saddle_from_probe(rp, col, val, n2):
     return sp.csr_matrix((val, col, rp), shape=(n2, n2))
 
 
-def oracle_first_step_sampled(ens, members, form="skew"):
+def oracle_first_step_sampled(ens, members, form="skew", element="TH"):
     """The first step of Algorithm 1 by the oracle for a subset of members:
     the ensemble means and mixing lengths use all members, the two shared
     saddle matrices are factorised once (SuperLU) and solved for the chosen
@@ -36,7 +36,7 @@ def oracle_first_step_sampled(ens, members, form="skew"):
     known).  Returns the oracle run (its P2 space and matrices) and the new
     v, w of the chosen members [len(members), n2, 2]."""
     from scipy.sparse.linalg import splu
-    run = OracleRun(ens, form=form)
+    run = OracleRun(ens, form=form, element=element)
     S, n2 = run.S, run.S.n2
     mv, mw = ensemble_mean(run.V), ensemble_mean(run.W)
     Vp, Wp = run.V - mv, run.W - mw

@@ -13,7 +13,7 @@ import paper_2108_05110_gb300 as P
 from paper_2108_05110_gb300 import ensemble_io
 from oracle.fe import P2Space
 from workloads.ensembles import lid_cavity, channel
-from workloads.mesh import unit_square, channel_step
+from workloads.mesh import unit_square, channel_step, barycentric_refine
 
 
 def test_library_exports_every_declared_function():
@@ -67,10 +67,34 @@ def test_create_rejects_bad_input():
     with pytest.raises(P.MhdeError):
         P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, strict=1, mu=0.4)
     # option fields outside their ranges
-    for bad_opt in (dict(inner_fp16=2), dict(inner_iters=17), dict(schur=2)):
+    for bad_opt in (dict(inner_fp16=2), dict(inner_iters=17), dict(schur=3), dict(element=2),
+                    dict(element=1, schur=1)):
         with pytest.raises(P.MhdeError):
             P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, **bad_opt)
     P.EnsembleSolver(m.xy, m.tri, [0.01], [0.01], 1.0, 0.1, bind=False, inner_fp16=1).close()
+
+
+@pytest.mark.parametrize("kw", [dict(element="SV"), dict(element="SV", schur=0), dict(schur=2)])
+def test_discontinuous_pressure_and_algebraic_laplacian_host_build(kw):
+    """Scott-Vogelius: three pressure dofs per triangle and the divergence
+    pattern of the oracle's P1disc space; the algebraic pressure Laplacian
+    B D^{-1} B^T (also taken by the least-squares commutator on Taylor-Hood)
+    coarsens into a hierarchy."""
+    mesh = barycentric_refine(unit_square(6))
+    s = P.EnsembleSolver(mesh.xy, mesh.tri, [0.01, 0.02], [0.01, 0.03], 0.5, 0.01, bind=False, **kw)
+    sv = kw.get("element") == "SV"
+    S = P2Space(mesh, pressure="P1disc" if sv else "P1")
+    assert s.options.element == (1 if sv else 0)
+    assert s.options.schur == kw.get("schur", 0 if sv else 1)
+    assert s.options.amg_sweeps == (2 if sv else 1)
+    assert s.sizes.np == S.np_ == (3 * mesh.nt if sv else mesh.nv)
+    Bx, _ = S.divergence()
+    Bpat = Bx.copy()
+    Bpat.data[:] = 1.0
+    assert s.sizes.nnz_B == Bpat.nnz
+    assert s.sizes.n_rows == 2 * S.n2 + S.np_
+    assert s.sizes.amg_levels >= (2 if sv else 1)      # 648 / 121 pressure dofs, coarsest <= 512
+    s.close()
 
 
 def test_calls_before_bind_fail_cleanly():
