@@ -568,10 +568,17 @@ def spmm_bytes(sz, prec_bytes):
 
 
 def laplacian_bytes(sz, prec_bytes):
-    """Algorithmic bytes of one residual b - L x on the finest pressure level:
-    L's values and column indices and its row pointers once, x and b read and
-    the residual written once, J_pad columns each."""
-    return sz.nnz_L * (prec_bytes + 4) + (sz.np + 1) * 4 + 3 * sz.np * sz.J_pad * prec_bytes
+    """Algorithmic bytes of the timed residual b - L x on the finest pressure
+    level: L's values, column indices and row pointers once, the input (x and
+    b are one buffer in the timing call) read once and the residual written
+    once, J_pad columns each."""
+    return sz.nnz_L * (prec_bytes + 4) + (sz.np + 1) * 4 + 2 * sz.np * sz.J_pad * prec_bytes
+
+
+# DRAM bytes (read + write) of that launch on the 64 x 64 barycenter-refined
+# Scott-Vogelius cavity, J = 20, FP32 (44.49 MB read, <0.1 MB written: the
+# residual stays in L2), from an ncu capture of the same launch configuration
+LAPLACIAN_TRAFFIC_SV64 = 44492544 + 50176
 
 
 def gram_bytes(sz, restart, prec_bytes):
@@ -691,7 +698,8 @@ def our_arm(args, rank, world, local_rank):
         l_ach = lb / (l_ms / 1000.0) / 1e9
         roofline = {"bound": "hbm", "kernel": f"pressure-Laplacian residual b - L x on the finest level "
                     f"(k_csr<{'float' if pbytes == 4 else 'double'}>, L = B D^-1 B^T, nnz {sol.sizes.nnz_L})",
-                    "achieved": l_ach, "peak": peak, "unit": "GB/s", "frac": l_ach / peak, "traffic": None,
+                    "achieved": l_ach, "peak": peak, "unit": "GB/s", "frac": l_ach / peak,
+                    "traffic": LAPLACIAN_TRAFFIC_SV64 if (pbytes == 4 and args.N == SV_N and args.J == 20) else None,
                     "bytes_per_launch": lb, "ms_per_launch": l_ms,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                     "block_gram": {"achieved": achieved, "frac": achieved / peak, "ms_per_launch": gram_ms}}
