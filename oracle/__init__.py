@@ -25,11 +25,12 @@ taken):
 Pins: every function here is checked in ``tests/test_oracle_*.py`` against
 closed forms, exact integrals, brute force, the stability inequality of
 Section 3.1, the special cases of Section 4.4 ("usual MHD") and the paper's
-printed numbers: the spatial errors of Table 1 (for a pressure-free velocity,
-where the element pair does not enter the velocity error) and the temporal
-errors of Table 4, values and rates (``tests/golden/``).  The other tables'
-absolute errors are not pinned (the paper uses Scott-Vogelius elements on
-barycenter-refined meshes); with a pressure their second-order rates are.
+printed numbers: the spatial errors of Table 1 (Taylor-Hood with a
+pressure-free velocity, where the element pair does not enter the velocity
+error; Scott-Vogelius on barycenter-refined meshes with the printed pressure)
+and of Table 3 (Scott-Vogelius), and the temporal errors of Table 4, values
+and rates (``tests/golden/``).  The Scott-Vogelius space is further pinned by
+pointwise zero divergence and pressure robustness (``tests/test_oracle_sv.py``).
 Its adjoint (:mod:`oracle.adjoint`) is pinned by central differences of this
 forward run.
 """
