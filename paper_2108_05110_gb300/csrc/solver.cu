@@ -456,7 +456,14 @@ static int gmres_cycle(mhde_ctx* c, Sub& s, const std::vector<double>& C0, const
     // new block column of the Hessenberg matrix, row-major: [H_0; ...; H_k; S]
     std::vector<double> hblk((size_t)(k + 2) * rr, 0.0);
     std::copy(Hsum.begin(), Hsum.begin() + (size_t)(k + 1) * rr, hblk.begin());
-    if (!breakdown) std::copy(Sn.begin(), Sn.begin() + rr, hblk.begin() + (size_t)(k + 1) * rr);
+    // at a breakdown the rk significant directions of the projected block
+    // (rows of Sn) still enter the least-squares problem: the cycle ends, but
+    // its correction must minimise the true residual, not one that takes the
+    // whole new block to lie in the basis
+    if (!breakdown)
+      std::copy(Sn.begin(), Sn.begin() + rr, hblk.begin() + (size_t)(k + 1) * rr);
+    else
+      std::copy(Sn.begin(), Sn.begin() + (size_t)rk * r, hblk.begin() + (size_t)(k + 1) * rr);
     bool ok = ls.add(hblk.data());
     pc4.stop(5);
     used++;
@@ -553,7 +560,11 @@ static int solve_sub_t(mhde_ctx* c, int which, bool zero_guess) {
     Gs.assign((size_t)J * J, 0.0);
     for (int i = 0; i < J; ++i)
       for (int j = 0; j < J; ++j) Gs[(size_t)i * J + j] = G[(size_t)i * J + j] * sc[i] * sc[j];
-    const double tau = 0.1 * tol_in / std::sqrt((double)J);
+    // directions of the unit-scaled residual block below tau start in a later
+    // sweep; on the FP64 path tau has a floor, because nearly parallel member
+    // residuals kept down to rounding make the Krylov blocks rank-deficient
+    // after a few iterations and end every cycle early
+    const double tau = 0.1 * (fp64 ? std::max(tol_in, 1e-10) : tol_in) / std::sqrt((double)J);
     const int r = svqb(J, Gs, std::max(tau * tau, 1e-30), Tm, Sm);
     if (r == 0) return MHDE_OK;
     if (c->trace) std::fprintf(stderr, "[mhde] sub %d sweep %d block width %d\n", which, s.refine, r);
