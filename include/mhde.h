@@ -125,6 +125,9 @@ typedef struct {
   int n_boundary;           /* Dirichlet P2 nodes */
   int amg_levels;           /* levels of the pressure-Laplacian hierarchy */
   long long nnz_L;          /* nonzeros of its finest operator (P1 stiffness or B D^{-1} B^T) */
+  int smoother_block;       /* smoother of that finest level: 0 point Jacobi, 3 block Jacobi
+                               over the dofs of each triangle, 9 over each macro triangle of a
+                               barycenter refinement (discontinuous pressure) */
 } mhde_sizes;
 
 typedef struct {
@@ -288,6 +291,14 @@ int mhde_probe_mean_l2(mhde_ctx* ctx, double* mean_v, double* mean_w, double* l2
 /* Shared matrix F of eq. weaknew1 (which = 0) or weaknew2 (which = 1) with
  * Dirichlet identity rows, in CSR: rowptr [n2+1], col [nnz_F], val [nnz_F]. */
 int mhde_probe_matrix_F(mhde_ctx* ctx, int which, int* rowptr, int* col, double* val);
+
+/* Finest operator L of the pressure-Laplacian hierarchy, host data (callable
+ * before bind): the P1 stiffness of the continuous pressure, or
+ * L = sum_d B_d D^{-1} B_d^T over the interior P2 nodes (D the P2 mass
+ * diagonal scaled to the element areas) for the discontinuous pressure and
+ * the least-squares commutator; dof 0 pinned (identity row and column).
+ * CSR: rowptr [np+1], col [nnz_L], val [nnz_L]; any pointer may be NULL. */
+int mhde_probe_laplacian(const mhde_ctx* ctx, int* rowptr, int* col, double* val);
 
 /* Right-hand sides of eq. weaknew1 / weaknew2 for all members:
  * velocity part [J][n2][2] (boundary rows hold the Dirichlet values). */

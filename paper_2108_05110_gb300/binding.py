@@ -48,7 +48,7 @@ class Sizes(C.Structure):
     _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("ne", C.c_int), ("n2", C.c_int), ("np", C.c_int),
                 ("n_rows", C.c_int), ("J", C.c_int), ("J_pad", C.c_int), ("nnz_F", C.c_longlong),
                 ("nnz_B", C.c_longlong), ("nnz_saddle", C.c_longlong), ("n_boundary", C.c_int),
-                ("amg_levels", C.c_int), ("nnz_L", C.c_longlong)]
+                ("amg_levels", C.c_int), ("nnz_L", C.c_longlong), ("smoother_block", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -98,6 +98,7 @@ SIGNATURES = {
     "mhde_destroy": (None, [_P]),
     "mhde_probe_mean_l2": (C.c_int, [_P, _D, _D, _D, _D]),
     "mhde_probe_matrix_F": (C.c_int, [_P, C.c_int, _I, _I, _D]),
+    "mhde_probe_laplacian": (C.c_int, [_P, _I, _I, _D]),
     "mhde_probe_rhs": (C.c_int, [_P, C.c_int, _D]),
     "mhde_probe_spmm": (C.c_int, [_P, C.c_int, C.c_int, _D, _D]),
     "mhde_probe_inner": (C.c_int, [_P, C.c_int, C.c_int, _D, _D]),
@@ -512,6 +513,16 @@ class EnsembleSolver:
         val = np.empty(self.sizes.nnz_F)
         self._check(self.lib.mhde_probe_matrix_F(self.ctx, int(which), rp.ctypes.data_as(_I),
                                                  col.ctypes.data_as(_I), _dptr(val)), "mhde_probe_matrix_F")
+        return rp, col, val
+
+    def probe_laplacian(self):
+        """Finest pressure-Laplacian operator (host data; works before bind)."""
+        np_ = self.sizes.np
+        rp = np.empty(np_ + 1, dtype=np.int32)
+        col = np.empty(self.sizes.nnz_L, dtype=np.int32)
+        val = np.empty(self.sizes.nnz_L)
+        self._check(self.lib.mhde_probe_laplacian(self.ctx, rp.ctypes.data_as(_I), col.ctypes.data_as(_I),
+                                                  _dptr(val)), "mhde_probe_laplacian")
         return rp, col, val
 
     def probe_rhs(self, which):

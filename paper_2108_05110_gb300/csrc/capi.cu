@@ -527,6 +527,7 @@ int mhde_get_sizes(const mhde_ctx* c, mhde_sizes* z) {
   z->n_boundary = (int)c->fe.bnd_nodes.size();
   z->amg_levels = c->amg_levels;
   z->nnz_L = c->fe.Kp.nnz();
+  z->smoother_block = c->fe.amg.levels.empty() ? 0 : c->fe.amg.levels[0].bs;
   return MHDE_OK;
 }
 
@@ -1132,6 +1133,15 @@ int mhde_probe_matrix_F(mhde_ctx* c, int which, int* rowptr, int* col, double* v
   if (rowptr) std::copy(F.rowptr.begin(), F.rowptr.end(), rowptr);
   if (col) std::copy(F.col.begin(), F.col.end(), col);
   if (val) CU(cudaMemcpy(val, c->sub[which].Fval, F.nnz() * sizeof(double), cudaMemcpyDeviceToHost));
+  return MHDE_OK;
+}
+
+int mhde_probe_laplacian(const mhde_ctx* c, int* rowptr, int* col, double* val) {
+  if (!c) return MHDE_EINVAL;
+  const HostCsr& L = c->fe.Kp;
+  if (rowptr) std::copy(L.rowptr.begin(), L.rowptr.end(), rowptr);
+  if (col) std::copy(L.col.begin(), L.col.end(), col);
+  if (val) std::copy(L.val.begin(), L.val.end(), val);
   return MHDE_OK;
 }
 

@@ -97,6 +97,49 @@ def test_discontinuous_pressure_and_algebraic_laplacian_host_build(kw):
     s.close()
 
 
+def _pinned(L):
+    L = sp.lil_matrix(L)
+    L[0, :] = 0.0
+    L[:, 0] = 0.0
+    L[0, 0] = 1.0
+    return sp.csr_matrix(L)
+
+
+@pytest.mark.parametrize("kw,bary", [(dict(element="SV"), True), (dict(element="SV"), False),
+                                     (dict(schur=2), True), (dict(), True)])
+def test_pressure_laplacian_matches_oracle_matrices(kw, bary):
+    """The library's finest pressure operator (host-built) against one formed
+    here from the oracle's matrices: the P1 stiffness of the continuous
+    pressure from the oracle's barycentric gradients, or B D^{-1} B^T with
+    the oracle's divergence blocks B_x, B_y and D = (30/19) diag(M) on the
+    interior P2 nodes (the P2 mass diagonal, area/30 at vertices and
+    8 area/45 at edge midpoints, scaled to sum to the area); dof 0 pinned.
+    Also the smoother's block size: 9 on barycenter-refined meshes with the
+    discontinuous pressure, 3 on other meshes, 0 (point Jacobi) otherwise."""
+    # more than 512 pressure dofs in the discontinuous case (648 and 600), so
+    # that the finest level is not already the dense coarsest one
+    mesh = barycentric_refine(unit_square(6)) if bary else unit_square(10)
+    s = P.EnsembleSolver(mesh.xy, mesh.tri, [0.01, 0.02], [0.01, 0.03], 0.5, 0.01, bind=False, **kw)
+    sv = kw.get("element") == "SV"
+    S = P2Space(mesh, pressure="P1disc" if sv else "P1")
+    rp, col, val = s.probe_laplacian()
+    L = sp.csr_matrix((val, col, rp), shape=(S.np_, S.np_))
+    if sv or kw.get("schur") == 2:
+        Bx, By = S.divergence()
+        d = S.mass().diagonal() * (30.0 / 19.0)
+        dinv = sp.diags(np.where(S.is_boundary, 0.0, 1.0 / d))
+        ref = _pinned(Bx @ dinv @ Bx.T + By @ dinv @ By.T)
+    else:
+        g = S.grad_lambda                                   # [nt, 3, 2]
+        loc = S.area[:, None, None] * np.einsum("tid,tkd->tik", g, g)
+        ref = _pinned(S._assemble(loc, S.pdofs, S.pdofs, S.np_, S.np_))
+    diff = abs(L - ref).max()
+    assert diff <= 1e-12 * abs(ref).max(), diff
+    want_block = (9 if bary else 3) if sv else 0
+    assert s.sizes.smoother_block == want_block
+    s.close()
+
+
 def test_calls_before_bind_fail_cleanly():
     ens = lid_cavity(N=4, J=2, nsteps=1)
     s = ensemble_io.solver_for(ens, bind=False)
