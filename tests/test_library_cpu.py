@@ -182,3 +182,28 @@ def test_block_gram_entry_points_reject_more_blocks_than_grid_rows():
     assert lib.mhde_block_gram_scratch_bytes(100, 1, 65536, C.byref(nbytes)) == -1
     assert lib.mhde_block_gram(fake, 400, 65536, fake, 100, 4, 1, fake, fake, 1 << 30, None) == -1
     assert lib.mhde_block_gram_noalloc(fake, 400, 65536, fake, 100, 4, 1, fake, None) == -1
+
+
+def test_concurrent_host_builds_are_identical():
+    """mhde_create from many threads at once (ctypes releases the GIL): the
+    host-built structures (numbering, patterns, the pressure-Laplacian
+    hierarchy and its smoother blocks) come out identical to a serial build,
+    for both elements."""
+    from concurrent.futures import ThreadPoolExecutor
+    meshes = [(barycentric_refine(unit_square(6)), dict(element="SV")), (unit_square(12), dict()),
+              (channel_step(cells_per_unit=2), dict(schur=2))]
+
+    def build(i):
+        mesh, kw = meshes[i % len(meshes)]
+        s = P.EnsembleSolver(mesh.xy, mesh.tri, [0.01, 0.02], [0.01, 0.03], 0.5, 0.01, bind=False, **kw)
+        sz = s.sizes
+        out = (i % len(meshes), sz.n2, sz.np, sz.nnz_F, sz.nnz_B, sz.amg_levels, sz.nnz_L, sz.smoother_block,
+               s.probe_laplacian()[2].tobytes(), s.p2_nodes()[0].tobytes())
+        s.close()
+        return out
+
+    serial = {r[0]: r for r in map(build, range(len(meshes)))}
+    with ThreadPoolExecutor(max_workers=12) as ex:
+        results = list(ex.map(build, range(48)))
+    for r in results:
+        assert r == serial[r[0]]

@@ -166,3 +166,21 @@ def test_spatial_errors_match_table3():
     ev, ew = zip(*[_sv_errors(N, 20, 0.01, 2) for N in (4, 8, 16)])
     assert np.allclose(ev, g["e_v"][:3], rtol=0.01)
     assert np.allclose(ew, g["e_w"][:3], rtol=0.01)
+
+
+def test_temporal_errors_match_table4_sample1():
+    """Table 4 (eps = 0, J = 20, sample 1, T = 1, dt = T/2, T/4, T/8) with
+    the paper's element: the printed errors to 2 % (the temporal error
+    dominates, so the refined 16 x 16 mesh stands in for the paper's
+    h = 1/64; the rest is the draw of the 20 viscosity pairs, whose sample
+    means differ from the paper's) and first-order decay."""
+    g = json.load(open(os.path.join(GOLDEN, "table4_temporal_eps0.json")))["sample1"]
+    ev, ew = [], []
+    for k in (2, 4, 8):
+        ens = convergence_study(16, 20, dt=1.0 / k, nsteps=k, eps=0.0, sample=1,
+                                mesh=barycentric_refine(unit_square(16)))
+        a, b, _, _ = l2h1_errors(lambda e: OracleRun(e, element="SV"), ens, k)
+        ev.append(a); ew.append(b)
+    assert np.allclose(ev, g["e_v"][:3], rtol=0.02)
+    assert np.allclose(ew, g["e_w"][:3], rtol=0.02)
+    assert np.all((_rates(ev) > 0.9) & (_rates(ev) < 1.1))
