@@ -131,11 +131,11 @@ def reverse_step(run, Vn, Wn, Xv, Xw, seed_v, seed_w):
     return lamV, lamW, g_nu, g_nu_m
 
 
-def energy_gradient(ens, nsteps, form="skew"):
+def energy_gradient(ens, nsteps, form="skew", element="TH"):
     """L = E_h^K after ``nsteps`` steps of Algorithm 1 and its gradient:
     returns (L, dL/d nu [J], dL/d nu_m [J], dL/d u0 [J, n2, 2], dL/d B0 [J, n2, 2])
-    with u0, B0 the nodal initial fields."""
-    run = OracleRun(ens, form=form)
+    with u0, B0 the nodal initial fields; ``element`` as in OracleRun."""
+    run = OracleRun(ens, form=form, element=element)
     states = [(run.V.copy(), run.W.copy())]
     for _ in range(nsteps):
         run.step()

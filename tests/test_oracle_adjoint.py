@@ -12,8 +12,8 @@ from oracle.scheme import OracleRun
 from workloads.ensembles import sensitivity
 
 
-def _loss(ens, nsteps, form="skew"):
-    run = OracleRun(ens, form=form)
+def _loss(ens, nsteps, form="skew", element="TH"):
+    run = OracleRun(ens, form=form, element=element)
     for _ in range(nsteps):
         run.step()
     return run.energy()
@@ -28,7 +28,7 @@ def _amplitude_grads(ens, du0, dB0):
     return np.einsum("jnd,nd->j", du0, psi), np.einsum("jnd,nd->j", dB0, psi)
 
 
-def _fd(ens, nsteps, which, k, h, form="skew"):
+def _fd(ens, nsteps, which, k, h, form="skew", element="TH"):
     """Central difference of L in one parameter (h absolute, FP64)."""
     vals = []
     for sgn in (+1.0, -1.0):
@@ -36,13 +36,13 @@ def _fd(ens, nsteps, which, k, h, form="skew"):
             arr = getattr(ens, which).copy()
             arr[k] += sgn * h
             e = dataclasses.replace(ens, **{which: arr})
-            vals.append(_loss(e, nsteps, form))
+            vals.append(_loss(e, nsteps, form, element))
         else:
             amp = ens.info[which]
             old = amp[k]
             amp[k] = old + sgn * h
             try:
-                vals.append(_loss(ens, nsteps, form))
+                vals.append(_loss(ens, nsteps, form, element))
             finally:
                 amp[k] = old
     return (vals[0] - vals[1]) / (2.0 * h)
@@ -76,6 +76,24 @@ def test_adjoint_matches_central_differences(form):
         assert scale > 0.0
         for k in range(3):
             fd = _fd(ens, K, name, k, 1e-6, form)
+            assert abs(fd - g[k]) <= 1e-6 * scale, (name, k, fd, g[k])
+
+
+def test_adjoint_matches_central_differences_scott_vogelius():
+    """The same check with the discontinuous pressure on the barycenter
+    refinement of a 3x3 mesh (2 steps, 2 members)."""
+    from workloads.mesh import barycentric_refine
+    base = sensitivity(N=3, J=2, s=0.5, nsteps=2)
+    ens = dataclasses.replace(base, mesh=barycentric_refine(base.mesh))
+    K = 2
+    L, gnu, gnum, du0, dB0 = energy_gradient(ens, K, element="SV")
+    assert np.isclose(L, _loss(ens, K, element="SV"), rtol=1e-13)
+    gu, gB = _amplitude_grads(ens, du0, dB0)
+    for name, g in (("nu", gnu), ("nu_m", gnum), ("eps_u", gu), ("eps_B", gB)):
+        scale = np.abs(g).max()
+        assert scale > 0.0
+        for k in range(2):
+            fd = _fd(ens, K, name, k, 1e-6, element="SV")
             assert abs(fd - g[k]) <= 1e-6 * scale, (name, k, fd, g[k])
 
 
