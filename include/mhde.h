@@ -111,7 +111,11 @@ typedef struct {
                            launches, not by traffic: 283 vs 286 us per application) */
   int element;          /* 0 Taylor-Hood P2/P1 (default); 1 Scott-Vogelius P2/P1disc (give a
                            barycenter-refined mesh; on other meshes the pair need not be
-                           inf-sup stable and the solve may fail) */
+                           inf-sup stable and the solve may fail).  Element 1 needs schur 0 or
+                           2; schur 0 with amg_sweeps 2 was the fastest measured (64x64
+                           refined cavity, J = 20: 240 ms per step against 275 ms with one
+                           sweep and 400 ms for schur 2) and is what the Python binding sets
+                           for this element unless told otherwise */
 } mhde_options;
 
 typedef struct {
