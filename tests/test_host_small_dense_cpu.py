@@ -53,6 +53,42 @@ def test_block_least_squares_matches_numpy_lstsq(checker, r, J, m):
     assert np.allclose(Y, Yref, rtol=1e-8, atol=1e-10 * np.abs(Yref).max())
 
 
+@pytest.mark.parametrize("r,rk", [(4, 2), (6, 1), (20, 13)])
+def test_block_least_squares_with_a_rank_deficient_last_block(checker, r, rk):
+    """The block column a GMRES cycle adds when its new Krylov block turns out
+    numerically rank-deficient: only rk of the r rows of its subdiagonal
+    factor S are nonzero (the significant directions of the SVQB factor), and
+    the cycle ends there.  BlockLS must give the least-squares residuals of
+    exactly that matrix, as numpy does, and they differ from those of the
+    matrix whose whole S block is zero: keeping the rk rows changes the
+    correction that the cycle returns."""
+    J, m = r, 3
+    rng = np.random.default_rng(7 + r + rk)
+    S0 = rng.standard_normal((r, J))
+    blocks = [rng.standard_normal(((k + 2) * r, r)) for k in range(m)]
+    last = blocks[-1]
+    last[(m) * r + rk:, :] = 0.0                     # rows rk..r-1 of the last S block
+    text = f"L {r} {J} {m}\n" + " ".join(repr(float(v)) for v in S0.ravel()) + "\n"
+    text += "".join(" ".join(repr(float(v)) for v in b.ravel()) + "\n" for b in blocks)
+    out = subprocess.run([checker], input=text, capture_output=True, text=True, check=True).stdout.split()
+    Hbar = np.zeros(((m + 1) * r, m * r))
+    for k, b in enumerate(blocks):
+        Hbar[:(k + 2) * r, k * r:(k + 1) * r] = b
+    B = np.zeros(((m + 1) * r, J))
+    B[:r] = S0
+    pos = (1 + J) * (m - 1)
+    assert int(out[pos]) == 1
+    res = np.array([float(v) for v in out[pos + 1:pos + 1 + J]])
+    Y = np.linalg.lstsq(Hbar, B, rcond=None)[0]
+    want = np.linalg.norm(B - Hbar @ Y, axis=0)
+    assert np.allclose(res, want, rtol=1e-9, atol=1e-12 * np.linalg.norm(S0))
+    dropped = Hbar.copy()
+    dropped[m * r:, (m - 1) * r:] = 0.0
+    Yd = np.linalg.lstsq(dropped, B, rcond=None)[0]
+    true_resid_of_dropped = np.linalg.norm(B - Hbar @ Yd, axis=0)
+    assert np.all(true_resid_of_dropped >= want - 1e-12) and np.any(true_resid_of_dropped > want * (1 + 1e-6))
+
+
 def _cholqr(exe, G, thresh):
     r = G.shape[0]
     text = f"Q {r} {thresh!r}\n" + " ".join(repr(float(v)) for v in G.ravel()) + "\n"
