@@ -304,6 +304,19 @@ int mhde_probe_matrix_F(mhde_ctx* ctx, int which, int* rowptr, int* col, double*
  * CSR: rowptr [np+1], col [nnz_L], val [nnz_L]; any pointer may be NULL. */
 int mhde_probe_laplacian(const mhde_ctx* ctx, int* rowptr, int* col, double* val);
 
+/* Level `level` (0 = finest) of the pressure-Laplacian hierarchy, host data
+ * (callable before bind).  counts[6] receives: rows n, nnz(A), nnz(P),
+ * nnz(R), the smoother's block size bs (0: damped point Jacobi) and the
+ * number of levels; scal[2] the Jacobi damping and the block damping.  Each
+ * non-NULL array receives a copy: A in CSR (a_rowptr [n+1], a_col, a_val),
+ * the prolongation from the next level P (n x n_next) and the restriction
+ * R = P^T in CSR, the blocks (blk_idx [n], blk_inv [n/bs][bs][bs]).  The
+ * coarsest level has no P, R or blocks (it is solved by a dense inverse).
+ * MHDE_EINVAL for a NULL ctx or counts, or a level out of range. */
+int mhde_probe_amg_level(const mhde_ctx* ctx, int level, long long* counts, double* scal, int* a_rowptr,
+                         int* a_col, double* a_val, int* p_rowptr, int* p_col, double* p_val, int* r_rowptr,
+                         int* r_col, double* r_val, int* blk_idx, double* blk_inv);
+
 /* Right-hand sides of eq. weaknew1 / weaknew2 for all members:
  * velocity part [J][n2][2] (boundary rows hold the Dirichlet values). */
 int mhde_probe_rhs(mhde_ctx* ctx, int which, double* rhs);

@@ -99,6 +99,8 @@ SIGNATURES = {
     "mhde_probe_mean_l2": (C.c_int, [_P, _D, _D, _D, _D]),
     "mhde_probe_matrix_F": (C.c_int, [_P, C.c_int, _I, _I, _D]),
     "mhde_probe_laplacian": (C.c_int, [_P, _I, _I, _D]),
+    "mhde_probe_amg_level": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), _D, _I, _I, _D, _I, _I, _D, _I, _I,
+                                       _D, _I, _D]),
     "mhde_probe_rhs": (C.c_int, [_P, C.c_int, _D]),
     "mhde_probe_spmm": (C.c_int, [_P, C.c_int, C.c_int, _D, _D]),
     "mhde_probe_inner": (C.c_int, [_P, C.c_int, C.c_int, _D, _D]),
@@ -524,6 +526,39 @@ class EnsembleSolver:
         self._check(self.lib.mhde_probe_laplacian(self.ctx, rp.ctypes.data_as(_I), col.ctypes.data_as(_I),
                                                   _dptr(val)), "mhde_probe_laplacian")
         return rp, col, val
+
+    def probe_amg_level(self, level):
+        """One level of the pressure-Laplacian hierarchy (host data; works
+        before bind): dict with A, P, R (scipy CSR; P, R None on the coarsest
+        level), omega, block size bs, block damping, blk_idx, blk_inv, levels."""
+        import scipy.sparse as sp
+        counts = (C.c_longlong * 6)()
+        scal = (C.c_double * 2)()
+        self._check(self.lib.mhde_probe_amg_level(self.ctx, int(level), counts, scal, *([None] * 11)),
+                    "mhde_probe_amg_level")
+        n, nnzA, nnzP, nnzR, bs, nlev = (int(v) for v in counts)
+        nxt = None
+        if nnzP:
+            c2 = (C.c_longlong * 6)()
+            self._check(self.lib.mhde_probe_amg_level(self.ctx, int(level) + 1, c2, None, *([None] * 11)),
+                        "mhde_probe_amg_level")
+            nxt = int(c2[0])
+        arr = {}
+        for name, rows, nnz in (("A", n, nnzA), ("P", n, nnzP), ("R", nxt or 0, nnzR)):
+            arr[name] = (np.zeros(rows + 1, dtype=np.int32), np.zeros(nnz, dtype=np.int32), np.zeros(nnz))
+        bidx = np.zeros(n if bs else 0, dtype=np.int32)
+        binv = np.zeros((n // bs) * bs * bs if bs else 0)
+        ptrs = []
+        for name in ("A", "P", "R"):
+            rp, col, val = arr[name]
+            ptrs += [rp.ctypes.data_as(_I), col.ctypes.data_as(_I), _dptr(val)]
+        self._check(self.lib.mhde_probe_amg_level(self.ctx, int(level), counts, scal, *ptrs,
+                                                  bidx.ctypes.data_as(_I), _dptr(binv)), "mhde_probe_amg_level")
+        A = sp.csr_matrix((arr["A"][2], arr["A"][1], arr["A"][0]), shape=(n, n))
+        P = sp.csr_matrix((arr["P"][2], arr["P"][1], arr["P"][0]), shape=(n, nxt)) if nnzP else None
+        R = sp.csr_matrix((arr["R"][2], arr["R"][1], arr["R"][0]), shape=(nxt, n)) if nnzP else None
+        return {"A": A, "P": P, "R": R, "omega": scal[0], "bs": bs, "blk_omega": scal[1],
+                "blk_idx": bidx, "blk_inv": binv.reshape(-1, bs, bs) if bs else None, "levels": nlev}
 
     def probe_rhs(self, which):
         out = np.empty((self.J, self.n2, 2))

@@ -1145,6 +1145,36 @@ int mhde_probe_laplacian(const mhde_ctx* c, int* rowptr, int* col, double* val) 
   return MHDE_OK;
 }
 
+int mhde_probe_amg_level(const mhde_ctx* c, int level, long long* counts, double* scal, int* a_rowptr,
+                         int* a_col, double* a_val, int* p_rowptr, int* p_col, double* p_val, int* r_rowptr,
+                         int* r_col, double* r_val, int* blk_idx, double* blk_inv) {
+  if (!c || !counts) return MHDE_EINVAL;
+  const auto& levels = c->fe.amg.levels;
+  if (level < 0 || level >= (int)levels.size()) return MHDE_EINVAL;
+  const AmgLevelHost& L = levels[level];
+  counts[0] = L.A.nrows;
+  counts[1] = L.A.nnz();
+  counts[2] = L.P.nnz();
+  counts[3] = L.R.nnz();
+  counts[4] = L.bs;
+  counts[5] = (long long)levels.size();
+  if (scal) {
+    scal[0] = L.omega;
+    scal[1] = L.blk_omega;
+  }
+  auto put = [](const HostCsr& M, int* rp, int* col, double* val) {
+    if (rp && !M.rowptr.empty()) std::copy(M.rowptr.begin(), M.rowptr.end(), rp);
+    if (col) std::copy(M.col.begin(), M.col.end(), col);
+    if (val) std::copy(M.val.begin(), M.val.end(), val);
+  };
+  put(L.A, a_rowptr, a_col, a_val);
+  put(L.P, p_rowptr, p_col, p_val);
+  put(L.R, r_rowptr, r_col, r_val);
+  if (blk_idx) std::copy(L.blk_idx.begin(), L.blk_idx.end(), blk_idx);
+  if (blk_inv) std::copy(L.blk_inv.begin(), L.blk_inv.end(), blk_inv);
+  return MHDE_OK;
+}
+
 int mhde_probe_rhs(mhde_ctx* c, int which, double* rhs) {
   int rc = probe_assemble(c, which);
   if (rc) return rc;
