@@ -466,7 +466,7 @@ namespace {
 // triangle when the mesh is a barycenter refinement (every triangle has one
 // vertex that is interior, has exactly three triangles around it and sits at
 // the mean of their other vertices), else the three dofs of every triangle.
-void pressure_blocks(const FeHost& fe, int& bs, std::vector<int>& idx) {
+void pressure_blocks(const FeHost& fe, int& bs, std::vector<int>& idx, std::vector<int>* macro_out = nullptr) {
   const int nv = fe.nv, nt = fe.nt;
   std::vector<int> cnt(nv + 1, 0);
   for (int t = 0; t < 3 * nt; ++t) cnt[fe.tri[t] + 1]++;
@@ -498,6 +498,7 @@ void pressure_blocks(const FeHost& fe, int& bs, std::vector<int>& idx) {
   for (int t = 0; t < nt && ok; ++t)
     if (owner[t] < 0) ok = false;
   idx.clear();
+  if (macro_out) *macro_out = ok ? macro : std::vector<int>();
   if (ok) {
     bs = 9;
     for (int t : macro)
@@ -552,6 +553,76 @@ std::string build_amg(FeHost& fe, int coarse_max) {
     L.omega = 4.0 / (3.0 * rho);
     int n = L.A.nrows;
     if (n <= coarse_max) break;
+    if (lev == 0 && fe.element == 0) {
+      // continuous pressure on a barycenter refinement: the first coarse space
+      // is P1 on the parent mesh (a parent vertex keeps its value, a
+      // barycenter takes the mean of its triangle's three vertices; the
+      // pinned node 0 takes none), then smoothed aggregation as usual
+      int bs = 0;
+      std::vector<int> idx, macro;
+      pressure_blocks(fe, bs, idx, &macro);
+      if (bs == 9) {
+        std::vector<char> is_bary(fe.nv, 0);
+        std::vector<int> outer((size_t)fe.nv * 3, -1);
+        for (size_t q = 0; q < macro.size(); q += 3) {
+          const int t0 = macro[q];
+          int g = -1;
+          for (int l = 0; l < 3 && g < 0; ++l) {       // the vertex shared by the three children
+            const int v = fe.tri[3 * t0 + l];
+            bool all = true;
+            for (int k = 1; k < 3; ++k) {
+              const int t = macro[q + k];
+              all = all && (fe.tri[3 * t] == v || fe.tri[3 * t + 1] == v || fe.tri[3 * t + 2] == v);
+            }
+            if (all) g = v;
+          }
+          is_bary[g] = 1;
+          int no = 0;
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) {
+              const int u = fe.tri[3 * macro[q + k] + l];
+              bool seen = (u == g);
+              for (int o = 0; o < no; ++o) seen = seen || outer[(size_t)g * 3 + o] == u;
+              if (!seen && no < 3) outer[(size_t)g * 3 + no++] = u;
+            }
+        }
+        std::vector<int> coarse(fe.nv, -1);
+        int nc = 0;
+        for (int v = 0; v < fe.nv; ++v)
+          if (!is_bary[v]) coarse[v] = nc++;
+        HostCsr P;
+        P.nrows = n;
+        P.ncols = nc;
+        P.rowptr.assign(n + 1, 0);
+        for (int v = 0; v < n; ++v) {
+          if (v != 0) {
+            if (!is_bary[v]) {
+              P.col.push_back(coarse[v]);
+              P.val.push_back(1.0);
+            } else {
+              int cs[3] = {coarse[outer[(size_t)v * 3]], coarse[outer[(size_t)v * 3 + 1]],
+                           coarse[outer[(size_t)v * 3 + 2]]};
+              std::sort(cs, cs + 3);
+              for (int k = 0; k < 3; ++k) {
+                P.col.push_back(cs[k]);
+                P.val.push_back(1.0 / 3.0);
+              }
+            }
+          }
+          P.rowptr[v + 1] = (int)P.col.size();
+        }
+        HostCsr R, RA, Ac;
+        csr_transpose(P, R);
+        csr_matmul(R, L.A, RA);
+        csr_matmul(RA, P, Ac);
+        L.P = P;
+        L.R = R;
+        AmgLevelHost next;
+        next.A = Ac;
+        amg.levels.push_back(next);
+        continue;
+      }
+    }
     if (lev == 0 && fe.element == 1) {
       // discontinuous pressure: the first coarse space is the continuous P1
       // space on the mesh vertices, injected into P1disc (P: dof 3t + i takes

@@ -245,6 +245,8 @@ def _vcycle(levels, cinv, l, b, nsw):
     (barycentric_refine(unit_square(24)), dict(element="SV"), 20),     # 13 measured
     (barycentric_refine(unit_square(48)), dict(element="SV"), 20),     # 13
     (unit_square(64), dict(), 20),                                     # 14 (Taylor-Hood P1 stiffness)
+    (barycentric_refine(unit_square(48)), dict(), 20),                 # 12 (40 with aggregation alone)
+    (barycentric_refine(channel_step(cells_per_unit=2)), dict(schur=2), 20),
 ])
 def test_pressure_hierarchy_preconditions_its_laplacian(mesh, kw, max_its):
     """The host-built hierarchy (probed level by level), cycled as the device
@@ -253,7 +255,9 @@ def test_pressure_hierarchy_preconditions_its_laplacian(mesh, kw, max_its):
     For the discontinuous pressure the first coarse space is the continuous
     P1 space on the vertices (P injects vertex values into the three dofs of
     every triangle, R = P^T), and the finest smoother works on 9-dof macro
-    triangles."""
+    triangles.  For the continuous pressure on a barycenter refinement the
+    first coarse space is P1 on the parent mesh (a barycenter takes the mean
+    of its triangle's vertices)."""
     import scipy.sparse.linalg as sla
     s = P.EnsembleSolver(mesh.xy, mesh.tri, [0.01, 0.02], [0.01, 0.03], 0.5, 0.01, bind=False, **kw)
     levels = [s.probe_amg_level(l) for l in range(s.sizes.amg_levels)]
@@ -265,6 +269,14 @@ def test_pressure_hierarchy_preconditions_its_laplacian(mesh, kw, max_its):
                              shape=P0.shape)
         assert abs(P0 - want).max() == 0.0
         assert abs(levels[0]["R"] - P0.T).max() == 0.0
+    elif mesh.nt % 3 == 0 and levels[0]["A"].shape[0] == mesh.nv and mesh.nv > 4000:
+        # barycenter refinement: the parent's vertices are the coarse dofs
+        nparent = mesh.nv - mesh.nt // 3
+        P0 = levels[0]["P"]
+        assert P0.shape == (mesh.nv, nparent)
+        rows = np.diff(P0.indptr)
+        assert rows[0] == 0 and set(rows[1:].tolist()) <= {1, 3}
+        assert np.allclose(np.asarray(P0.sum(axis=1)).ravel()[1:], 1.0)
     cinv = np.linalg.inv(levels[-1]["A"].toarray())
     A = levels[0]["A"]
     b = np.random.default_rng(1).standard_normal(A.shape[0])
