@@ -307,7 +307,8 @@ int mhde_probe_laplacian(const mhde_ctx* ctx, int* rowptr, int* col, double* val
 /* Level `level` (0 = finest) of the pressure-Laplacian hierarchy, host data
  * (callable before bind).  counts[6] receives: rows n, nnz(A), nnz(P),
  * nnz(R), the smoother's block size bs (0: damped point Jacobi) and the
- * number of levels; scal[2] the Jacobi damping and the block damping.  Each
+ * number of levels; scal[2] the Jacobi damping (0 on a level smoothed by
+ * blocks, where it is not used) and the block damping.  Each
  * non-NULL array receives a copy: A in CSR (a_rowptr [n+1], a_col, a_val),
  * the prolongation from the next level P (n x n_next) and the restriction
  * R = P^T in CSR, the blocks (blk_idx [n], blk_inv [n/bs][bs][bs]).  The

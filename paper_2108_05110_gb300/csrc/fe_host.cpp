@@ -549,9 +549,11 @@ std::string build_amg(FeHost& fe, int coarse_max) {
   for (int lev = 0; lev < 25; ++lev) {
     AmgLevelHost& L = amg.levels.back();
     L.dinv = diag_inv(L.A);
-    double rho = spectral_radius_DinvA(L.A, L.dinv);
-    L.omega = 4.0 / (3.0 * rho);
     int n = L.A.nrows;
+    // the finest level of the discontinuous pressure is smoothed by blocks
+    // (below), so its point-Jacobi damping is never used and not estimated
+    const bool blocks = lev == 0 && fe.element == 1 && n > coarse_max;
+    L.omega = blocks ? 0.0 : 4.0 / (3.0 * spectral_radius_DinvA(L.A, L.dinv));
     if (n <= coarse_max) break;
     if (lev == 0 && fe.element == 0) {
       // continuous pressure on a barycenter refinement: the first coarse space
