@@ -184,3 +184,49 @@ def test_temporal_errors_match_table4_sample1():
     assert np.allclose(ev, g["e_v"][:3], rtol=0.02)
     assert np.allclose(ew, g["e_w"][:3], rtol=0.02)
     assert np.all((_rates(ev) > 0.9) & (_rates(ev) < 1.1))
+
+
+def _inf_sup_values(mesh):
+    """Square roots of the generalised eigenvalues of B K^-1 B^T against the
+    pressure mass M_p (K the vector P2 stiffness on interior nodes): the
+    smallest nonzero one is the discrete inf-sup constant beta_h of the pair
+    (Section 2, eq. infsup)."""
+    import scipy.linalg as sl
+    from oracle.fe import P2Space
+    S = P2Space(mesh, pressure="P1disc")
+    keep = ~S.is_boundary
+    K = S.stiffness().toarray()[np.ix_(keep, keep)]
+    Bx, By = S.divergence()
+    B = np.hstack([Bx.toarray()[:, keep], By.toarray()[:, keep]])
+    Sch = B @ np.linalg.solve(sl.block_diag(K, K), B.T)
+    w = sl.eigh(Sch, S.pressure_mass().toarray(), eigvals_only=True)
+    return np.sqrt(np.maximum(w, 0.0))
+
+
+def test_inf_sup_stable_on_barycenter_refinements_only():
+    """P2/P1disc on barycenter-refined meshes: one zero mode (the constant
+    pressure, all boundary data Dirichlet) and beta_h bounded away from zero
+    independently of h (Section 2 cites this stability result); on the
+    unrefined meshes the pair has spurious pressure modes."""
+    betas = []
+    for N in (2, 4, 6):
+        s = _inf_sup_values(barycentric_refine(unit_square(N)))
+        assert s[0] < 1e-6 and s[1] > 0.2
+        betas.append(s[1])
+    assert max(betas) / min(betas) < 1.05
+    plain = _inf_sup_values(unit_square(4))
+    assert np.sum(plain < 1e-6) >= 3
+
+
+def test_sv_channel_velocity_is_pointwise_divergence_free():
+    """The divergence pin on the channel's geometry (re-entrant corners of
+    the step, inflow and outflow data), barycenter-refined."""
+    from workloads.ensembles import channel
+    ens = channel(J=2, nsteps=2, dt=0.05, mesh=barycentric_refine(channel_step(cells_per_unit=1)))
+    run = OracleRun(ens, element="SV")
+    for _ in range(2):
+        run.step()
+    S = run.S
+    for Z in (run.V, run.W):
+        for j in range(2):
+            assert S.divergence_sq(Z[j]) < 1e-24 * S.h1semi_sq(run.K, Z[j])
